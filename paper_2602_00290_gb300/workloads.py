@@ -1,0 +1,188 @@
+"""Seeded synthetic workloads for the multigroup S_N tensor-train transport step.
+
+This module produces raw problem inputs only: grid sizes, frequency-group edges,
+fixed material temperature per cell, absorption and scattering opacities per
+merged (cell, group) row, boundary temperatures, time step, rounding tolerance
+and rank cap, plus random TT cores for the rounding tests.  It holds none of the
+method's arithmetic (no quadrature, no Planck integrals, no transport or source
+update); both the CUDA path and the CPU oracle consume these arrays and derive
+everything else on their own.
+
+Conventions shared by every consumer:
+
+* merged spatio-spectral row index ``k = g + G * (ix + Nx * (iy + Ny * iz))``
+  (group fastest, then x, y, z), the row order of the merged core Z of Eq.
+  (tensor_decomp_mer) in Sec. 3.1;
+* frequency groups ``[nu_{f-1}, nu_f)`` with ``nu_0 = 0`` and ``nu_G = inf`` and
+  log-spaced interior edges (Sec. 2 and Sec. 4 preamble);
+* units ``h = k_B = c = a = 1`` so that ``x = nu / T`` (the a = c = 1 unit
+  system of the thermal-relaxation test in Sec. 4.2);
+* face order ``(x-, x+, y-, y+, z-, z+)``; a face temperature of ``None`` means
+  vacuum, otherwise isotropic Planck inflow at that temperature.
+
+Opacity recipe (synthetic stand-in for the paper's tabulated opacities, which
+are not available): ``rho*kappa_a[cell, f] = rho(cell) * kappa0 * (nu_f/nu0)^-3
+* L_f`` with ``L_f = exp(z_f)``, ``z_f ~ N(0, 1)`` seeded, ``nu_f`` the
+geometric mean of the group edges (end groups use the log grid extended by one
+step), ``kappa0 = 10``, ``nu0 = 1``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Optional, Sequence, Tuple
+
+import numpy as np
+
+FACES = ("x-", "x+", "y-", "y+", "z-", "z+")
+
+
+@dataclass
+class Workload:
+    name: str
+    ndim: int                      # number of spatial axes d_X (1, 2 or 3)
+    nx: int
+    ny: int
+    nz: int
+    ngroup: int                    # G
+    quad: str                      # "gauss_legendre_mu" (slab) or "latlong_midpoint"
+    ntheta: int                    # polar nodes (mu nodes for the slab)
+    nphi: int                      # azimuthal nodes (1 for the slab)
+    extent: Tuple[float, float, float]
+    c: float
+    dt: float
+    group_edges: np.ndarray        # (G+1,), [0, ..., inf]
+    temperature: np.ndarray        # (N_X,) material temperature per cell (fixed)
+    rho_kappa_a: np.ndarray        # (N_X*G,) per merged row
+    rho_kappa_s: np.ndarray        # (N_X*G,) per merged row
+    inflow_temperature: Tuple[Optional[float], ...] = (None,) * 6
+    initial_temperature: Optional[np.ndarray] = None  # radiation temperature per cell for I^0
+    tol: float = 1e-6
+    rmax: int = 32
+    steps: int = 20
+    a_rad: float = 1.0
+    seed: int = 0
+    notes: str = ""
+
+    @property
+    def ncell(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def nrow(self) -> int:
+        """Rows of the merged spatio-spectral core (N_X * N_nu)."""
+        return self.ncell * self.ngroup
+
+    @property
+    def spacing(self) -> Tuple[float, float, float]:
+        n = (self.nx, self.ny, self.nz)
+        return tuple(self.extent[a] / n[a] for a in range(3))
+
+    @property
+    def nangle(self) -> int:
+        return self.ntheta * self.nphi
+
+    def full_unknowns(self) -> int:
+        return self.nrow * self.nangle
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+def group_edges(G: int, lo: float = 0.01, hi: float = 100.0) -> np.ndarray:
+    """G groups: nu_0 = 0, G-1 log-spaced interior edges on [lo, hi], nu_G = inf."""
+    e = np.empty(G + 1)
+    e[0] = 0.0
+    e[G] = np.inf
+    if G >= 2:
+        e[1:G] = np.logspace(np.log10(lo), np.log10(hi), G - 1)
+    return e
+
+
+def representative_nu(edges: np.ndarray) -> np.ndarray:
+    """Geometric-mean group frequency used only by the synthetic opacity law."""
+    G = len(edges) - 1
+    inner = np.array(edges[1:G], dtype=float)
+    if G == 1:
+        return np.array([1.0])
+    if G == 2:
+        return np.array([inner[0] / 2.0, inner[0] * 2.0])
+    step = inner[1] / inner[0]
+    ext = np.concatenate([[inner[0] / step], inner, [inner[-1] * step]])
+    return np.sqrt(ext[:-1] * ext[1:])
+
+
+def line_factors(G: int, seed: int, sd: float = 1.0) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    return np.exp(sd * rng.standard_normal(G))
+
+
+def blob_density(nx: int, ny: int, seed: int, nblob: int = 8, contrast: float = 100.0) -> np.ndarray:
+    """rho = 1 + (contrast-1) * min(1, sum_b exp(-|x-c_b|^2 / (2 w_b^2))) on [0,1]^2 cell centres.
+
+    Returned with x fastest: rho[ix + nx*iy]."""
+    rng = np.random.default_rng(seed)
+    cb = rng.uniform(0.1, 0.9, size=(nblob, 2))
+    wb = rng.uniform(0.03, 0.1, size=nblob)
+    xc = (np.arange(nx) + 0.5) / nx
+    yc = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(xc, yc, indexing="xy")  # shape (ny, nx)
+    s = np.zeros_like(X)
+    for b in range(nblob):
+        s += np.exp(-((X - cb[b, 0]) ** 2 + (Y - cb[b, 1]) ** 2) / (2.0 * wb[b] ** 2))
+    rho = 1.0 + (contrast - 1.0) * np.minimum(1.0, s)
+    return rho.reshape(-1)
+
+
+def linear_temperature(nx: int, ny: int = 1, nz: int = 1, t0: float = 1.0, t1: float = 0.1) -> np.ndarray:
+    """T linear in x over cell centres from t0 to t1, constant in y and z."""
+    xc = (np.arange(nx) + 0.5) / nx
+    tx = t0 + (t1 - t0) * xc
+    return np.tile(tx, ny * nz)
+
+
+def opacity_rows(rho_cell: np.ndarray, edges: np.ndarray, lf: np.ndarray,
+                 kappa0: float = 10.0, nu0: float = 1.0) -> np.ndarray:
+    """rho*kappa_a per merged row k = g + G*cell."""
+    nu = representative_nu(edges)
+    kg = kappa0 * (nu / nu0) ** -3.0 * lf
+    return (rho_cell[:, None] * kg[None, :]).reshape(-1)
+
+
+def slab_config0() -> Workload:
+    """1-D planar slab: Nx=64 on [0,1], G=16, 8 Gauss-Legendre mu, rho=1, kappa_s=0,
+    T linear 1 -> 0.1, vacuum, dt=0.01, 10 steps, exact rank (tol 0, rank cap 8)."""
+    nx, G = 64, 16
+    edges = group_edges(G)
+    lf = line_factors(G, seed=0)
+    rho = np.ones(nx)
+    ka = opacity_rows(rho, edges, lf)
+    return Workload(
+        name="slab1d_nx64_g16_mu8", ndim=1, nx=nx, ny=1, nz=1, ngroup=G,
+        quad="gauss_legendre_mu", ntheta=8, nphi=1, extent=(1.0, 1.0, 1.0),
+        c=1.0, dt=0.01, group_edges=edges, temperature=linear_temperature(nx),
+        rho_kappa_a=ka, rho_kappa_s=np.zeros_like(ka), tol=0.0, rmax=8, steps=10, seed=0)
+
+
+def plane_config1(nx: int = 128, ny: int = 128, G: int = 64, ntheta: int = 16, nphi: int = 32,
+                  rmax: int = 32, tol: float = 1e-6, steps: int = 20, seed: int = 1,
+                  cfl: float = 0.5) -> Workload:
+    """2-D (x,y) on [0,1]^2, Gaussian-blob density (8 blobs, contrast 100), kappa_s = 0.1 kappa_a,
+    T linear in x 1 -> 0.1, vacuum, CFL 0.5, lat/long ordinates."""
+    edges = group_edges(G)
+    lf = line_factors(G, seed=seed + 1000)
+    rho = blob_density(nx, ny, seed=seed)
+    ka = opacity_rows(rho, edges, lf)
+    dx = 1.0 / nx
+    return Workload(
+        name=f"plane2d_{nx}x{ny}_g{G}_{ntheta}x{nphi}_r{rmax}", ndim=2, nx=nx, ny=ny, nz=1,
+        ngroup=G, quad="latlong_midpoint", ntheta=ntheta, nphi=nphi, extent=(1.0, 1.0, 1.0),
+        c=1.0, dt=cfl * dx, group_edges=edges, temperature=linear_temperature(nx, ny),
+        rho_kappa_a=ka, rho_kappa_s=0.1 * ka, tol=tol, rmax=rmax, steps=steps, seed=seed)
+
+
+def random_tt(n: Sequence[int], ranks: Sequence[int], seed: int, scale: float = 1.0):
+    """Cores with iid N(0,1) entries, core k of shape (r_{k-1}, n_k, r_k)."""
+    rng = np.random.default_rng(seed)
+    r = [1] + list(ranks) + [1]
+    assert len(r) == len(n) + 1
+    return [scale * rng.standard_normal((r[k], n[k], r[k + 1])) for k in range(len(n))]

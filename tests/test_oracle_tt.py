@@ -1,0 +1,177 @@
+"""Pins of the naive TT oracle: brute force, closed forms and the dense stepper."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dense, naive_tt as nt, problem
+from paper_2602_00290_gb300.workloads import Workload, plane_config1, random_tt, slab_config0
+
+
+def test_full_and_dot_brute_force():
+    x = random_tt([5, 3, 4], [2, 3], seed=1)
+    y = random_tt([5, 3, 4], [3, 2], seed=2)
+    Fx, Fy = nt.full(x), nt.full(y)
+    # brute-force element loop for the full tensor
+    ref = np.zeros((5, 3, 4))
+    for i in range(5):
+        for j in range(3):
+            for k in range(4):
+                ref[i, j, k] = (x[0][0, i, :] @ x[1][:, j, :] @ x[2][:, k, 0])
+    assert np.allclose(Fx, ref, rtol=0, atol=1e-13)
+    assert abs(nt.dot(x, y) - float(np.sum(Fx * Fy))) < 1e-12 * abs(np.sum(Fx * Fy)) + 1e-14
+    assert abs(nt.norm(x) - np.linalg.norm(Fx)) < 1e-12 * np.linalg.norm(Fx)
+
+
+def test_add_is_elementwise_sum_and_ranks_add():
+    x = random_tt([6, 3, 4], [2, 3], seed=3)
+    y = random_tt([6, 3, 4], [3, 2], seed=4)
+    s = nt.add(x, y)
+    assert nt.ranks(s) == [1, 5, 5, 1]
+    assert np.allclose(nt.full(s), nt.full(x) + nt.full(y), atol=1e-13)
+
+
+@pytest.mark.parametrize("d,n,r", [(3, [40, 6, 7], [5, 4]), (2, [30, 9], [6]), (4, [12, 3, 4, 5], [4, 5, 3])])
+def test_round_exact_reconstruction(d, n, r):
+    x = random_tt(n, r, seed=7)
+    info = {}
+    y = nt.round_tt(x, 1e-12, info=info)
+    assert nt.ranks(y)[1:-1] == list(r)
+    err = np.linalg.norm(nt.full(y) - nt.full(x))
+    assert err <= 1e-12 * np.linalg.norm(nt.full(x))
+
+
+def test_round_x_plus_x_and_x_minus_x():
+    x = random_tt([20, 5, 6], [3, 4], seed=9)
+    y = nt.round_tt(nt.add(x, x), 1e-10)
+    assert nt.ranks(y) == nt.ranks(x)
+    assert np.allclose(nt.full(y), 2 * nt.full(x), atol=1e-10 * np.abs(nt.full(x)).max())
+    # X - X is zero up to round-off; a relative tolerance then resolves the round-off itself,
+    # so only the size of the result is fixed, not its ranks
+    z = nt.round_tt(nt.add(x, nt.scale(x, -1.0)), 1e-8)
+    assert np.max(np.abs(nt.full(z))) < 1e-14 * np.abs(nt.full(x)).max()
+    # an exactly zero tensor rounds to ranks 1 with zero cores
+    zero = [np.zeros_like(c) for c in nt.add(x, x)]
+    z = nt.round_tt(zero, 1e-8)
+    assert nt.ranks(z) == [1, 1, 1, 1] and all(not np.any(c) for c in z[:1])
+    assert not np.any(nt.full(z))
+
+
+def test_round_matrix_known_spectrum():
+    """d = 2 with prescribed singular values: the kept rank and the error follow the tail rule
+    exactly (Eckart-Young): error = sqrt(sum of discarded sigma^2) <= tol * ||X||."""
+    rng = np.random.default_rng(0)
+    m, n = 30, 12
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    s = 10.0 ** -np.arange(n, dtype=float)          # 1, 0.1, ..., 1e-11
+    A = (U * s) @ V.T
+    x = [A.reshape(1, m, n) @ np.eye(n)[None], np.eye(n).reshape(n, n, 1)]
+    x = [A.reshape(1, m, n), np.eye(n).reshape(n, n, 1)]
+    nrm = math.sqrt(np.sum(s ** 2))
+    for tol, kexp in ((3e-3, 3), (3e-6, 6), (3e-9, 9)):
+        y = nt.round_tt(x, tol)
+        k = nt.ranks(y)[1]
+        assert k == kexp
+        err = np.linalg.norm(nt.full(y) - A)
+        assert abs(err - math.sqrt(np.sum(s[k:] ** 2))) < 1e-14 * nrm
+        assert err <= tol * nrm
+    y = nt.round_tt(x, 1e-3, rmax=2)
+    assert nt.ranks(y)[1] == 2
+
+
+def test_round_error_bound_d4():
+    """Oseledets' guarantee: ||X - round(X)|| <= tol ||X|| with delta = tol ||X|| / sqrt(d-1)."""
+    x = random_tt([10, 4, 5, 6], [6, 8, 5], seed=11)
+    nx = np.linalg.norm(nt.full(x))
+    for tol in (0.3, 0.1, 0.01):
+        y = nt.round_tt(x, tol)
+        assert np.linalg.norm(nt.full(y) - nt.full(x)) <= tol * nx * (1 + 1e-12)
+
+
+def _small_plane(inflow=False, ks=True):
+    wl = plane_config1(nx=6, ny=5, G=3, ntheta=4, nphi=8, rmax=64, tol=0.0)
+    if inflow:
+        wl = wl.with_(inflow_temperature=(0.8, None, None, 0.6, None, None))
+    if not ks:
+        wl = wl.with_(rho_kappa_s=np.zeros_like(wl.rho_kappa_s))
+    return wl
+
+
+@pytest.mark.parametrize("inflow", [False, True])
+def test_transport_sum_matches_dense_operator(inflow):
+    """Brute force: full(TT transport sum) equals the dense upwind update of full(TT).
+    The dense stepper's source stage is switched off (a = s = eps = 0)."""
+    wl = _small_plane(inflow)
+    coef = problem.build(wl)
+    coef0 = problem.build(wl)
+    coef0.acoef[:] = 0.0
+    coef0.scoef[:] = 0.0
+    coef0.eps[:] = 0.0
+    x = random_tt([wl.nrow, wl.ntheta, wl.nphi], [3, 2], seed=13)
+    S = dense.DenseSolver(wl, coef0)
+    ref = S.step(nt.to_dense_rows(x))
+    t = nt.transport_sum(x, coef)
+    n = 2 * wl.ndim
+    nb = 2 if inflow else 0
+    assert nt.ranks(t)[1] == (n + 1) * 3 + nb and nt.ranks(t)[2] == (n + 1) * 2 + nb
+    assert np.max(np.abs(nt.to_dense_rows(t) - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+def test_source_sum_adds_one_rank_per_bond():
+    wl = _small_plane()
+    coef = problem.build(wl)
+    x = random_tt([wl.nrow, wl.ntheta, wl.nphi], [3, 2], seed=14)
+    s = nt.source_sum(x, coef)
+    assert nt.ranks(s) == [1, 4, 3, 1]
+
+
+@pytest.mark.parametrize("inflow", [False, True])
+def test_exact_rank_tt_step_equals_dense_plane(inflow):
+    """tol = 0 (no truncation): the TT step reproduces the dense step (transport + source)."""
+    wl = _small_plane(inflow)
+    coef = problem.build(wl)
+    S = dense.DenseSolver(wl, coef)
+    I = S.initial()
+    x = nt.initial_tt(problem.initial_rows(wl, coef), coef)
+    for _ in range(4):
+        I = S.step(I)
+        x = nt.step(x, coef, 0.0, 10 ** 6)
+        D = nt.to_dense_rows(x)
+        assert np.max(np.abs(D - I)) <= 1e-12 * np.max(np.abs(I))
+
+
+def test_exact_rank_slab_config_equals_dense():
+    """The 1-D slab workload (exact rank, 10 steps) matches the dense stepper to 1e-12."""
+    wl = slab_config0()
+    coef = problem.build(wl)
+    S = dense.DenseSolver(wl, coef)
+    I = S.initial()
+    x = nt.initial_tt(problem.initial_rows(wl, coef), coef)
+    for _ in range(wl.steps):
+        I = S.step(I)
+        x = nt.step(x, coef, wl.tol, wl.rmax)
+    D = nt.to_dense_rows(x)
+    assert nt.ranks(x)[1] <= wl.rmax
+    assert np.max(np.abs(D - I)) <= 1e-12 * np.max(np.abs(I))
+    E = nt.energy_density_rows(x, coef)
+    assert np.max(np.abs(E - S.energy_density(I))) <= 1e-12 * np.max(np.abs(E))
+
+
+def test_planck_equilibrium_stays_rank_one():
+    wl = _small_plane()
+    wl = wl.with_(temperature=np.full(wl.ncell, 0.7), inflow_temperature=(0.7,) * 4 + (None, None), tol=1e-10)
+    coef = problem.build(wl)
+    x = nt.initial_tt(problem.initial_rows(wl, coef), coef)
+    F0 = nt.full(x)
+    y = nt.step(x, coef, 1e-10, 32)
+    assert nt.ranks(y) == [1, 1, 1, 1]
+    assert np.max(np.abs(nt.full(y) - F0)) <= 1e-13 * np.max(np.abs(F0))
+
+
+def test_compression_counts_parameters():
+    """Eq. (compression): dense size over the parameter count of the cores."""
+    n = [7 * 3, 4, 8]
+    x = random_tt(n, [5, 3], seed=1)
+    params = sum(c.size for c in x)
+    assert nt.compression(7, 3, 4, 8, 5, 3) == pytest.approx(np.prod(n) / params, rel=1e-15)
