@@ -1,0 +1,167 @@
+/*
+ * tt.h -- C ABI of the GB300 (sm_103a) tensor-train multigroup S_N transport step.
+ *
+ * The method is the tensor-train (TT) multigroup discrete-ordinates solver of
+ * "Multigroup Thermal Radiation Transport with Tensor Trains" (arXiv 2602.00290):
+ * the solution I_{k l p} = Z_k Theta_l Phi_p with a merged spatio-spectral core Z
+ * (Sec. 3.1, Eq. tensor_decomp_mer), advanced by step-then-truncate (end of Sec. 3.1):
+ * forward-Euler upwind transport as a sum of n = 2 d_X rank-1 TT operators
+ * (Appendix A, 'Value of n'), SVD-based rounding (Sec. 3.1 footnote), the
+ * backward-Euler operator-split source of Eq. (discRTsource) at fixed material
+ * temperature, and rounding again.
+ *
+ * Conventions for every call
+ * --------------------------
+ * - Every pointer inside tt_tensor / tt_problem is DEVICE memory owned by the caller
+ *   unless stated otherwise.  The library never frees caller memory.
+ * - All calls are asynchronous on the context's CUDA stream and return after enqueueing.
+ *   Argument errors that the host can see are returned immediately.  Errors detected on
+ *   the device (rank capacity exceeded, non-finite values) are latched in a device status
+ *   word and returned by the next tt_sync().  No kernel traps; every device-side wait is
+ *   bounded.
+ * - TT layout: core j has shape (r_{j-1}, n_j, r_j) and is stored row-major as
+ *   [rcap_{j-1} * n_j][rcap_j] in the tensor's dtype, i.e. element (a, i, b) lives at
+ *   (a * n_j + i) * rcap_j + b.  r_0 = r_d = 1.  Live ranks are in device memory
+ *   (rank[0..d], int32) and are read and written by the library, so a sequence of calls
+ *   never needs the host to know them.  Entries outside the live ranks must be zero on
+ *   input; the library keeps them zero on output.
+ * - Core 0 is the merged spatio-spectral core Z with rows k = g + G*(ix + Nx*(iy + Ny*iz)).
+ *   Supported topologies: d = 2 (planar slab: Z, mu core) and d = 3 (Z, polar core Theta,
+ *   azimuthal core Phi).
+ */
+#ifndef TT_H
+#define TT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TT_MAX_CORES 8
+
+typedef enum {
+  TT_OK = 0,
+  TT_ERR_ARG = 1,          /* null pointer, bad enum, negative tolerance, ...            */
+  TT_ERR_SHAPE = 2,        /* incompatible mode sizes or topology                         */
+  TT_ERR_CAPACITY = 3,     /* a result rank would exceed the output rank capacity         */
+  TT_ERR_CUDA = 4,         /* a CUDA runtime call failed                                  */
+  TT_ERR_NONFINITE = 5,    /* NaN/Inf met in a norm or a singular value on the device     */
+  TT_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up                          */
+  TT_ERR_UNSUPPORTED = 7,  /* valid request outside what this build implements            */
+  TT_ERR_WORKSPACE = 8     /* the context workspace is too small for the request          */
+} tt_status;
+
+typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
+
+/* Arithmetic of the rounding and contraction kernels.
+ * TT_PREC_FP64  : every step in FP64.
+ * TT_PREC_MIXED : bulk passes over the merged core in FP32 (FP32 storage of Z allowed),
+ *                 R-factor merges, small-core SVDs, norms and the energy check in FP64. */
+typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_precision;
+
+typedef enum { TT_QUAD_GAUSS_LEGENDRE_MU = 0, TT_QUAD_LATLONG_MIDPOINT = 1 } tt_quadrature;
+
+typedef struct {
+  int32_t d;                       /* number of cores, 2 or 3                               */
+  int32_t n[TT_MAX_CORES];         /* mode sizes n_0..n_{d-1}                               */
+  int32_t rcap[TT_MAX_CORES + 1];  /* rank capacities, rcap[0] = rcap[d] = 1                */
+  int32_t *rank;                   /* device int32[d+1], live ranks                         */
+  void *core[TT_MAX_CORES];        /* device, core j: [rcap_{j-1} * n_j][rcap_j]            */
+  tt_dtype dtype;                  /* element type of every core                            */
+} tt_tensor;
+
+/* Raw physical problem (Sec. 2, Sec. 2.1, Sec. 4 preamble).  Units h = k_B = c = a = 1
+ * unless c and a_rad say otherwise; x = nu / T in the Planck integrals. */
+typedef struct {
+  int32_t ndim_x;                  /* spatial axes d_X: 1 (slab, needs d = 2) or 2, 3 (d = 3) */
+  int32_t nx, ny, nz;              /* cells per axis (1 for unused axes)                    */
+  int32_t ngroup;                  /* G frequency groups                                    */
+  int32_t quadrature;              /* tt_quadrature                                         */
+  int32_t ntheta, nphi;            /* polar (or mu) nodes, azimuthal nodes (1 for the slab) */
+  double dx, dy, dz;               /* cell sizes                                            */
+  double c, dt, a_rad;             /* speed of light, time step, radiation constant         */
+  const double *group_edges;       /* device double[G+1]: 0, log-spaced interior, +inf      */
+  const double *temperature;       /* device double[N_X]: fixed material temperature        */
+  const double *rho_kappa_a;       /* device double[N_X*G] per merged row                   */
+  const double *rho_kappa_s;       /* device double[N_X*G] per merged row                   */
+  double inflow_temperature[6];    /* faces x-,x+,y-,y+,z-,z+; < 0 means vacuum             */
+} tt_problem;
+
+typedef struct tt_context tt_context;
+typedef struct tt_plan tt_plan;
+
+/* Status text for a tt_status value (static storage, never NULL). */
+const char *tt_status_string(tt_status s);
+
+/* Create a context bound to CUDA device `device` and stream `cuda_stream` (a cudaStream_t,
+ * NULL = legacy default stream).  `workspace_bytes` > 0 pre-allocates that much device
+ * workspace; 0 lets the library size it on first use (outside any stream capture).
+ * The context owns its workspace and its device status word. */
+tt_status tt_context_create(tt_context **ctx, int device, void *cuda_stream, size_t workspace_bytes);
+tt_status tt_context_destroy(tt_context *ctx);
+
+/* Synchronise the context stream, then return and clear the latched device status. */
+tt_status tt_sync(tt_context *ctx);
+
+/* Workspace the context needs for tt_step / tt_round on tensors of capacity `x` with
+ * problem `plan` (NULL for tt_round only). */
+tt_status tt_workspace_query(tt_context *ctx, const tt_plan *plan, const tt_tensor *x,
+                             tt_precision prec, size_t *bytes);
+
+/* Build the per-step coefficients of a problem on the device: angular quadrature (Sec. 4
+ * preamble: Gauss-Legendre mu for the slab, lat/long midpoint rule otherwise), group
+ * emission epsilon_f(T) per merged row by Planck integrals (Eqs. Ttoeps1-2, evaluated with
+ * polylogarithm-type series as at the end of Sec. 2.1), the backward-Euler coefficients
+ * c*dt*rho*kappa of Eq. (discRTsource), inflow spectra and the angular factors of the 2 d_X
+ * rank-1 transport operators (Appendix A).  The plan copies what it needs; the problem's
+ * device arrays may be freed after the call returns and the stream has run. */
+tt_status tt_plan_create(tt_context *ctx, const tt_problem *prob, tt_plan **plan);
+tt_status tt_plan_destroy(tt_plan *plan);
+
+/* Device arrays owned by the plan (valid until tt_plan_destroy), for inspection:
+ * which = 0: emission per row (N_Z), 1: solid-angle weights (N_theta*N_phi),
+ *         2: mu nodes (N_theta), 3: phi nodes (N_phi), 4: c*dt*rho*kappa_a per row,
+ *         5: c*dt*rho*kappa_s per row, 6: inflow spectra [6][G] (0 for vacuum faces). */
+tt_status tt_plan_array(const tt_plan *plan, int which, const double **ptr, int64_t *len);
+
+/* y <- alpha * x + y by rank concatenation (TT addition, Sec. 3.1): ranks add.
+ * x and y must have equal d and mode sizes.  If a summed rank exceeds y's capacity the
+ * call leaves y unchanged and latches TT_ERR_CAPACITY. */
+tt_status tt_axpy(tt_context *ctx, double alpha, const tt_tensor *x, tt_tensor *y);
+
+/* *out_dev <- <x, y> (Frobenius inner product), FP64 accumulation, deterministic order.
+ * out_dev is a device double. */
+tt_status tt_dot(tt_context *ctx, const tt_tensor *x, const tt_tensor *y, double *out_dev);
+
+/* In-place SVD-based rounding (Sec. 3.1 footnote; Oseledets 2011): left-to-right QR
+ * orthogonalisation, then right-to-left truncated SVD with delta = rel_tol*||x||/sqrt(d-1);
+ * each bond keeps the smallest rank whose discarded tail is <= delta, capped at rmax
+ * (rel_tol = 0 keeps the full rank of every unfolding).  rmax must not exceed x's rank
+ * capacities.  A zero tensor rounds to ranks 1 with zero cores. */
+tt_status tt_round(tt_context *ctx, tt_tensor *x, double rel_tol, int32_t rmax, tt_precision prec);
+
+/* out <- the unrounded forward-Euler upwind transport update of `in` (Appendix A: the sum
+ * of the solution, its n = 2 d_X rank-1 operator images and the Dirichlet inflow tensor),
+ * materialised with ranks (n+1) r + n_b where n_b counts operators whose upwind face has
+ * inflow.  out must have the same d and mode sizes and enough capacity, else
+ * TT_ERR_CAPACITY is latched and out is left unchanged. */
+tt_status tt_apply_transport(tt_context *ctx, const tt_plan *plan, const tt_tensor *in, tt_tensor *out);
+
+/* One time step in place (end of Sec. 3.1): transport, round, source (Eq. discRTsource at
+ * fixed T), round, all on the device without materialising the transport sum.
+ * energy_dev (nullable, device double[4]) receives the radiation energy before and after
+ * the step, the energy of the post-transport tensor, and the absorption-emission exchange
+ * (4 pi / c) sum dV c dt rho kappa_a (eps - J^{m+1}). */
+tt_status tt_step(tt_context *ctx, const tt_plan *plan, tt_tensor *I, double tol, int32_t rmax,
+                  tt_precision prec, double *energy_dev);
+
+/* Radiation energy density per merged row, E_f = (4 pi / c) J_f (Sec. 2), into the
+ * device array out_dev[N_Z]. */
+tt_status tt_energy_density(tt_context *ctx, const tt_plan *plan, const tt_tensor *x, double *out_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TT_H */

@@ -1,0 +1,297 @@
+// C ABI of the library (declared in include/tt.h): argument checks, context and plan
+// lifetime, workspace sizing, dtype dispatch.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "common.cuh"
+#include "small.cuh"
+#include "step.cuh"
+
+namespace {
+
+tt_status check_tensor(const tt_tensor* x) {
+  if (!x || !x->rank) return TT_ERR_ARG;
+  if (x->d != 2 && x->d != 3) return TT_ERR_UNSUPPORTED;
+  if (x->dtype != TT_F64 && x->dtype != TT_F32) return TT_ERR_ARG;
+  if (x->rcap[0] != 1 || x->rcap[x->d] != 1) return TT_ERR_SHAPE;
+  for (int j = 0; j < x->d; ++j) {
+    if (x->n[j] <= 0 || x->rcap[j + 1] <= 0 || !x->core[j]) return TT_ERR_SHAPE;
+  }
+  return TT_OK;
+}
+
+tt_status same_modes(const tt_tensor* a, const tt_tensor* b) {
+  if (a->d != b->d || a->dtype != b->dtype) return TT_ERR_SHAPE;
+  for (int j = 0; j < a->d; ++j)
+    if (a->n[j] != b->n[j]) return TT_ERR_SHAPE;
+  return TT_OK;
+}
+
+tt_status check_plan_tensor(const tt_plan* p, const tt_tensor* x) {
+  if (!p) return TT_ERR_ARG;
+  if (x->d != p->d || x->n[0] != p->nrow || x->n[1] != p->n1) return TT_ERR_SHAPE;
+  if (x->d == 3 && x->n[2] != p->n2) return TT_ERR_SHAPE;
+  return TT_OK;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) return false;
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+tt_status ensure_ws(tt_context* ctx, size_t need) {
+  if (need <= ctx->ws_bytes) return TT_OK;
+  if (capturing(ctx->stream)) return TT_ERR_WORKSPACE;
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  if (cudaMalloc(&ctx->ws, need) != cudaSuccess) return TT_ERR_CUDA;
+  ctx->ws_bytes = need;
+  return TT_OK;
+}
+
+// Run `fn(Bump&)` once as a dry run to size the workspace, then for real.
+template <class F>
+tt_status with_ws(tt_context* ctx, F&& fn) {
+  ttk::Bump dry{nullptr, 0, 0, true};
+  tt_status st = fn(dry);
+  if (st != TT_OK) return st;
+  st = ensure_ws(ctx, dry.off);
+  if (st != TT_OK) return st;
+  ttk::Bump real{static_cast<char*>(ctx->ws), 0, ctx->ws_bytes, false};
+  return fn(real);
+}
+
+int set_device(tt_context* ctx) { return cudaSetDevice(ctx->device) == cudaSuccess; }
+
+}  // namespace
+
+extern "C" {
+
+const char* tt_status_string(tt_status s) {
+  switch (s) {
+    case TT_OK: return "ok";
+    case TT_ERR_ARG: return "invalid argument";
+    case TT_ERR_SHAPE: return "incompatible shapes";
+    case TT_ERR_CAPACITY: return "rank capacity exceeded";
+    case TT_ERR_CUDA: return "CUDA runtime error";
+    case TT_ERR_NONFINITE: return "non-finite value";
+    case TT_ERR_TIMEOUT: return "bounded device wait gave up";
+    case TT_ERR_UNSUPPORTED: return "unsupported request";
+    case TT_ERR_WORKSPACE: return "workspace too small";
+  }
+  return "unknown status";
+}
+
+tt_status tt_context_create(tt_context** out, int device, void* stream, size_t workspace_bytes) {
+  if (!out) return TT_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return TT_ERR_CUDA;
+  tt_context* ctx = new tt_context();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
+    delete ctx;
+    return TT_ERR_CUDA;
+  }
+  cudaMemsetAsync(ctx->ctrl, 0, sizeof(ttk::DevCtrl), ctx->stream);
+  if (workspace_bytes > 0 && ensure_ws(ctx, workspace_bytes) != TT_OK) {
+    cudaFree(ctx->ctrl);
+    delete ctx;
+    return TT_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaFree(ctx->ctrl);
+    delete ctx;
+    return TT_ERR_CUDA;
+  }
+  *out = ctx;
+  return TT_OK;
+}
+
+tt_status tt_context_destroy(tt_context* ctx) {
+  if (!ctx) return TT_ERR_ARG;
+  set_device(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->ws) cudaFree(ctx->ws);
+  cudaFree(ctx->ctrl);
+  delete ctx;
+  return TT_OK;
+}
+
+tt_status tt_sync(tt_context* ctx) {
+  if (!ctx) return TT_ERR_ARG;
+  set_device(ctx);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, &ctx->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TT_ERR_CUDA;
+  if (st != 0) cudaMemset(&ctx->ctrl->status, 0, sizeof(int));
+  if (cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
+  return static_cast<tt_status>(st);
+}
+
+tt_status tt_plan_create(tt_context* ctx, const tt_problem* prob, tt_plan** out) {
+  if (!ctx || !prob || !out) return TT_ERR_ARG;
+  *out = nullptr;
+  if (prob->ndim_x < 1 || prob->ndim_x > 3) return TT_ERR_ARG;
+  if (prob->ngroup < 1 || prob->nx < 1 || prob->ny < 1 || prob->nz < 1 || prob->ntheta < 1 || prob->nphi < 1)
+    return TT_ERR_ARG;
+  if (prob->ndim_x == 1 && (prob->quadrature != TT_QUAD_GAUSS_LEGENDRE_MU || prob->ny != 1 || prob->nz != 1))
+    return TT_ERR_UNSUPPORTED;
+  if (prob->ndim_x >= 2 && prob->quadrature != TT_QUAD_LATLONG_MIDPOINT) return TT_ERR_UNSUPPORTED;
+  if (prob->ndim_x == 2 && prob->nz != 1) return TT_ERR_ARG;
+  if (!prob->group_edges || !prob->temperature || !prob->rho_kappa_a || !prob->rho_kappa_s) return TT_ERR_ARG;
+  if (!(prob->c > 0) || !(prob->dt > 0) || !(prob->dx > 0)) return TT_ERR_ARG;
+  if (prob->ndim_x >= 2 && !(prob->dy > 0)) return TT_ERR_ARG;
+  if (prob->ndim_x >= 3 && !(prob->dz > 0)) return TT_ERR_ARG;
+  set_device(ctx);
+  tt_plan* p = new tt_plan();
+  std::memset(p, 0, sizeof(tt_plan));
+  p->ctx = ctx;
+  tt_status st = ttk::physics_setup(ctx, prob, p);
+  if (st != TT_OK) {
+    tt_plan_destroy(p);
+    return st;
+  }
+  *out = p;
+  return TT_OK;
+}
+
+tt_status tt_plan_destroy(tt_plan* p) {
+  if (!p) return TT_ERR_ARG;
+  double* arrs[] = {p->eps, p->acoef, p->scoef, p->domega, p->mu, p->phi, p->fac1, p->fac2, p->inflow, p->bcval, p->edges};
+  for (double* a : arrs)
+    if (a) cudaFree(a);
+  if (p->bc_term_dev) cudaFree(p->bc_term_dev);
+  delete p;
+  return TT_OK;
+}
+
+tt_status tt_plan_array(const tt_plan* p, int which, const double** ptr, int64_t* len) {
+  if (!p || !ptr || !len) return TT_ERR_ARG;
+  switch (which) {
+    case 0: *ptr = p->eps; *len = p->nrow; break;
+    case 1: *ptr = p->domega; *len = (int64_t)p->n1 * p->n2; break;
+    case 2: *ptr = p->mu; *len = p->ntheta; break;
+    case 3: *ptr = p->phi; *len = p->nphi; break;
+    case 4: *ptr = p->acoef; *len = p->nrow; break;
+    case 5: *ptr = p->scoef; *len = p->nrow; break;
+    case 6: *ptr = p->inflow; *len = 6 * (int64_t)p->G; break;
+    default: return TT_ERR_ARG;
+  }
+  return TT_OK;
+}
+
+tt_status tt_axpy(tt_context* ctx, double alpha, const tt_tensor* x, tt_tensor* y) {
+  if (!ctx) return TT_ERR_ARG;
+  tt_status st = check_tensor(x);
+  if (st == TT_OK) st = check_tensor(y);
+  if (st == TT_OK) st = same_modes(x, y);
+  if (st != TT_OK) return st;
+  if (!std::isfinite(alpha)) return TT_ERR_ARG;
+  set_device(ctx);
+  return (x->dtype == TT_F64) ? ttk::axpy_impl<double>(ctx, alpha, x, y) : ttk::axpy_impl<float>(ctx, alpha, x, y);
+}
+
+tt_status tt_dot(tt_context* ctx, const tt_tensor* x, const tt_tensor* y, double* out_dev) {
+  if (!ctx || !out_dev) return TT_ERR_ARG;
+  tt_status st = check_tensor(x);
+  if (st == TT_OK) st = check_tensor(y);
+  if (st == TT_OK) st = same_modes(x, y);
+  if (st != TT_OK) return st;
+  set_device(ctx);
+  return with_ws(ctx, [&](ttk::Bump& ws) {
+    return (x->dtype == TT_F64) ? ttk::dot_impl<double>(ctx, x, y, out_dev, ws)
+                                : ttk::dot_impl<float>(ctx, x, y, out_dev, ws);
+  });
+}
+
+static tt_status check_round_args(const tt_tensor* x, double tol, int32_t rmax, tt_precision prec) {
+  if (!(tol >= 0.0) || !std::isfinite(tol)) return TT_ERR_ARG;
+  if (rmax < 1) return TT_ERR_ARG;
+  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return TT_ERR_ARG;
+  for (int j = 1; j < x->d; ++j)
+    if (rmax > x->rcap[j]) return TT_ERR_CAPACITY;
+  return TT_OK;
+}
+
+tt_status tt_round(tt_context* ctx, tt_tensor* x, double tol, int32_t rmax, tt_precision prec) {
+  if (!ctx) return TT_ERR_ARG;
+  tt_status st = check_tensor(x);
+  if (st == TT_OK) st = check_round_args(x, tol, rmax, prec);
+  if (st != TT_OK) return st;
+  set_device(ctx);
+  return with_ws(ctx, [&](ttk::Bump& ws) {
+    return (x->dtype == TT_F64) ? ttk::round_impl<double>(ctx, x, tol, rmax, ws)
+                                : ttk::round_impl<float>(ctx, x, tol, rmax, ws);
+  });
+}
+
+tt_status tt_apply_transport(tt_context* ctx, const tt_plan* plan, const tt_tensor* in, tt_tensor* out) {
+  if (!ctx || !plan) return TT_ERR_ARG;
+  tt_status st = check_tensor(in);
+  if (st == TT_OK) st = check_tensor(out);
+  if (st == TT_OK) st = same_modes(in, out);
+  if (st == TT_OK) st = check_plan_tensor(plan, in);
+  if (st != TT_OK) return st;
+  if (in->core[0] == out->core[0]) return TT_ERR_ARG;
+  set_device(ctx);
+  return (in->dtype == TT_F64) ? ttk::apply_transport_impl<double>(ctx, plan, in, out)
+                               : ttk::apply_transport_impl<float>(ctx, plan, in, out);
+}
+
+tt_status tt_step(tt_context* ctx, const tt_plan* plan, tt_tensor* I, double tol, int32_t rmax, tt_precision prec,
+                  double* energy_dev) {
+  if (!ctx || !plan) return TT_ERR_ARG;
+  tt_status st = check_tensor(I);
+  if (st == TT_OK) st = check_plan_tensor(plan, I);
+  if (st == TT_OK) st = check_round_args(I, tol, rmax, prec);
+  if (st != TT_OK) return st;
+  set_device(ctx);
+  return with_ws(ctx, [&](ttk::Bump& ws) {
+    return (I->dtype == TT_F64) ? ttk::step_impl<double>(ctx, plan, I, tol, rmax, energy_dev, ws)
+                                : ttk::step_impl<float>(ctx, plan, I, tol, rmax, energy_dev, ws);
+  });
+}
+
+tt_status tt_energy_density(tt_context* ctx, const tt_plan* plan, const tt_tensor* x, double* out_dev) {
+  if (!ctx || !plan || !out_dev) return TT_ERR_ARG;
+  tt_status st = check_tensor(x);
+  if (st == TT_OK) st = check_plan_tensor(plan, x);
+  if (st != TT_OK) return st;
+  set_device(ctx);
+  return with_ws(ctx, [&](ttk::Bump& ws) {
+    return (x->dtype == TT_F64) ? ttk::energy_density_impl<double>(ctx, plan, x, out_dev, ws)
+                                : ttk::energy_density_impl<float>(ctx, plan, x, out_dev, ws);
+  });
+}
+
+tt_status tt_workspace_query(tt_context* ctx, const tt_plan* plan, const tt_tensor* x, tt_precision prec,
+                             size_t* bytes) {
+  if (!ctx || !x || !bytes) return TT_ERR_ARG;
+  tt_status st = check_tensor(x);
+  if (st != TT_OK) return st;
+  (void)prec;
+  ttk::Bump dry{nullptr, 0, 0, true};
+  tt_tensor tmp = *x;
+  if (plan) {
+    st = check_plan_tensor(plan, x);
+    if (st != TT_OK) return st;
+    st = (x->dtype == TT_F64) ? ttk::step_impl<double>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry)
+                              : ttk::step_impl<float>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry);
+  } else {
+    st = (x->dtype == TT_F64) ? ttk::round_impl<double>(ctx, &tmp, 1e-6, 1, dry)
+                              : ttk::round_impl<float>(ctx, &tmp, 1e-6, 1, dry);
+  }
+  *bytes = dry.off;
+  return st;
+}
+
+}  // extern "C"

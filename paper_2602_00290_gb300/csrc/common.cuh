@@ -1,0 +1,121 @@
+// Shared device/host definitions of the sm_103a tensor-train transport library.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tt.h"
+
+namespace ttk {
+
+constexpr int kMaxTerms = 6;  // 2 d_X transport operators for d_X <= 3 (Appendix A)
+
+// Device control block of a context: latched status plus the per-rounding decisions that
+// later kernels read (no host round trip inside a step).
+struct DevCtrl {
+  int status;          // first tt_status latched on the device (0 = TT_OK)
+  int k[4];            // ranks decided by the last small-core sweep (bond 1, bond 2)
+  int pad;
+  double norm;         // ||X||_F of the last rounded tensor
+  double delta;        // truncation threshold of the last rounding
+  double energy[8];    // scratch for energy reports
+};
+
+__device__ __forceinline__ void latch(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// Column-liveness pattern of a (possibly virtual) tall matrix in capacity layout:
+// columns [t*rcap, t*rcap + rcap) for t < nblk are live iff their offset is < r (r read
+// from device memory); the `nextra` columns after nblk*rcap are always live.
+struct LivePattern {
+  const int* r_ptr;
+  int rcap;
+  int nblk;
+  int nextra;
+  __host__ __device__ int ncap() const { return nblk * rcap + nextra; }
+  __device__ __forceinline__ bool live(int c, int r) const {
+    int t = c / rcap;
+    if (t < nblk) return (c - t * rcap) < r;
+    return c < nblk * rcap + nextra;
+  }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of one double per thread (blockDim multiple of 32, <= 1024).  All threads
+// receive the result.  `red` is shared scratch of >= 33 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double s = (lane < nw) ? red[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  double out = red[32];
+  __syncthreads();
+  return out;
+}
+
+template <typename S>
+__device__ __forceinline__ double to_d(S x) { return (double)x; }
+
+}  // namespace ttk
+
+// Host-side context and plan (defined here so every translation unit sees one layout).
+struct tt_context {
+  int device;
+  cudaStream_t stream;
+  void* ws;
+  size_t ws_bytes;
+  ttk::DevCtrl* ctrl;  // device
+  int num_sms;
+  int smem_optin;
+};
+
+struct tt_plan {
+  tt_context* ctx;
+  int ndim, nx, ny, nz, G, quad, ntheta, nphi;
+  int d;          // TT cores: 2 (slab) or 3
+  int n1, n2;     // angular mode sizes (n2 = 1 when d = 2)
+  long nrow;      // N_Z
+  double lam[3], c, dt, dV;
+  int nterm;                    // 2 d_X
+  int term_axis[ttk::kMaxTerms], term_w[ttk::kMaxTerms];
+  int nbc;                      // operators whose upwind face has inflow
+  int bc_term[ttk::kMaxTerms];  // operator index of each inflow column
+  long stride[3];
+  int ext[3];
+  // device arrays owned by the plan
+  double* eps;     // [N_Z]
+  double* acoef;   // [N_Z] c dt rho kappa_a
+  double* scoef;   // [N_Z] c dt rho kappa_s
+  double* domega;  // [n1*n2]
+  double* mu;      // [ntheta]
+  double* phi;     // [nphi]
+  double* fac1;    // [nterm][n1] angular factor on core 1
+  double* fac2;    // [nterm][n2] angular factor on core 2 (ones when d = 2)
+  double* inflow;  // [6][G] inflow spectra (0 for vacuum)
+  double* bcval;   // [nbc][G] signed lambda * inflow spectrum of each inflow column
+  double* edges;   // [G+1]
+  int* bc_term_dev;  // [kMaxTerms] operator index of each inflow column
+};
+
+// Internal entry points shared between translation units.
+namespace ttk {
+tt_status physics_setup(tt_context* ctx, const tt_problem* prob, tt_plan* plan);
+}

@@ -1,0 +1,354 @@
+// Host orchestration of the time step and of the TT primitives on the device.  No host
+// synchronisation happens inside any of these calls: ranks and truncation decisions stay in
+// device memory (tensor rank arrays and the context control block).
+#include <cstdio>
+#include <cstring>
+
+#include "bigpass.cuh"
+#include "small.cuh"
+#include "step.cuh"
+
+namespace ttk {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kTM = 32;   // rows per update tile
+constexpr int kBR = 16;   // rows per TSQR block (FP64)
+
+// B0 of the transport sum: block t = 0 is the right part of the state, block t = 1..nterm is
+// the same right part scaled by the operator's angular factors f1_t(l) f2_t(p), and each
+// inflow column carries the factors alone (Appendix A: rank-1 operators and the rank-1
+// Dirichlet tensor).
+__global__ void k_b0_transport(int rcap, int nterm, int nbc, int n1, int n2, const double* __restrict__ Bbase,
+                               const double* __restrict__ fac1, const double* __restrict__ fac2,
+                               const int* __restrict__ bc_term_dev, double* __restrict__ B0) {
+  const int nang = n1 * n2;
+  const int R = (nterm + 1) * rcap + nbc;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)R * nang;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx / nang);
+    const int i = (int)(idx - (long)c * nang);
+    const int l = i / n2, p = i - (i / n2) * n2;
+    const int t = c / rcap;
+    double v;
+    if (t == 0) {
+      v = Bbase[(size_t)c * nang + i];
+    } else if (t <= nterm) {
+      const int q = c - t * rcap;
+      v = fac1[(t - 1) * n1 + l] * fac2[(t - 1) * n2 + p] * Bbase[(size_t)q * nang + i];
+    } else {
+      const int tt = bc_term_dev[c - (nterm + 1) * rcap];
+      v = fac1[tt * n1 + l] * fac2[tt * n2 + p];
+    }
+    B0[idx] = v;
+  }
+}
+
+// B0 of the source sum [diag(1/(1+a+s)) Z_new, g]: the new right part, then a row of ones
+// (the isotropic rank-1 term).
+__global__ void k_b0_source(int rcap, int nang, const double* __restrict__ Bnew, double* __restrict__ B0) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)(rcap + 1) * nang;
+       idx += (long)gridDim.x * blockDim.x)
+    B0[idx] = (idx < (long)rcap * nang) ? Bnew[idx] : 1.0;
+}
+
+template <typename S>
+__global__ void k_commit(int d, int n1, int n2, int K1, int K2, const double* __restrict__ c1,
+                         const double* __restrict__ c2, S* __restrict__ core1, S* __restrict__ core2,
+                         const DevCtrl* ctrl, int* rank) {
+  const long tot1 = (long)K1 * n1 * (d == 3 ? K2 : 1);
+  const long tot2 = (d == 3) ? (long)K2 * n2 : 0;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < tot1 + tot2;
+       idx += (long)gridDim.x * blockDim.x) {
+    if (idx < tot1)
+      core1[idx] = (S)c1[idx];
+    else
+      core2[idx - tot1] = (S)c2[idx - tot1];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    rank[1] = ctrl->k[0];
+    if (d == 3) rank[2] = ctrl->k[1];
+  }
+}
+
+__global__ void k_save_ranks(DevCtrl* ctrl) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctrl->k[2] = ctrl->k[0];
+    ctrl->k[3] = ctrl->k[1];
+  }
+}
+
+// per-CTA partial sums of Z[k,:] . v (mean intensity J per row summed)
+template <typename S>
+__global__ void k_rowdot_partials(long nrows, int ld, int ncol, const S* __restrict__ Z, const double* __restrict__ v,
+                                  double* __restrict__ partials, double* __restrict__ per_row, double row_scale) {
+  __shared__ double red[33];
+  double s = 0.0;
+  const long k = blockIdx.x * (long)blockDim.x + threadIdx.x;
+  if (k < nrows) {
+    double j = 0.0;
+    for (int q = 0; q < ncol; ++q) j += (double)Z[k * ld + q] * v[q];
+    s = j;
+    if (per_row) per_row[k] = row_scale * j;
+  }
+  s = block_sum(s, red);
+  if (threadIdx.x == 0 && partials) partials[blockIdx.x] = s;
+}
+
+__global__ void k_energy_pack(const double* __restrict__ e_before, const double* __restrict__ e1,
+                              const double* __restrict__ e2, double scale, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    out[0] = e_before ? scale * e_before[0] : 0.0;
+    out[1] = scale * e2[0];
+    out[2] = scale * e1[0];
+    out[3] = scale * e1[1];
+  }
+}
+
+}  // namespace
+
+template <typename S>
+static void fill_stencil(SrcStencil<S>& src, const tt_plan* p, const S* Z, int rcap1) {
+  src.Z = Z;
+  src.ldz = rcap1;
+  src.rcap = rcap1;
+  src.nterm = p->nterm;
+  src.G = p->G;
+  for (int a = 0; a < 3; ++a) {
+    src.ext[a] = p->ext[a];
+    src.stride[a] = p->stride[a];
+  }
+  for (int t = 0; t < kMaxTerms; ++t) {
+    src.lam[t] = (t < p->nterm) ? p->lam[p->term_axis[t]] : 0.0;
+    src.axis[t] = (t < p->nterm) ? p->term_axis[t] : 0;
+    src.w[t] = (t < p->nterm) ? p->term_w[t] : 1;
+    src.bc_term[t] = (t < p->nbc) ? p->bc_term[t] : 0;
+  }
+  src.bcval = p->bcval;
+}
+
+template <typename T, class Src, class Epi>
+static tt_status launch_update(cudaStream_t s, const Src& src, LivePattern lp, long nrows, const double* W,
+                               int kcap, const Epi& epi, double* partials) {
+  const size_t smem = update_smem_bytes<T, kTM>(lp.ncap(), kcap);
+  if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(k_update<T, kTM, Src, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long grid = (nrows + kTM - 1) / kTM;
+  k_update<T, kTM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+// Workspace carving shared by dry runs (size queries) and real runs.
+struct RoundBufs {
+  double* tsqr_a;
+  double* tsqr_b;
+  double* Bbase;
+  double* B0;
+  double* W;
+  double* core1;
+  double* core2;
+  double* Bnew;
+  double* vJ;
+};
+
+static RoundBufs take_round_bufs(Bump& ws, int num_sms, int d, int R, long nrows, int n1, int n2, int K1, int K2,
+                                 int rcapin1) {
+  RoundBufs b;
+  const long L = tsqr_max_leaves<double, kBR>(num_sms, R, nrows, 0);
+  b.tsqr_a = ws.take<double>((size_t)L * R * R);
+  b.tsqr_b = ws.take<double>((size_t)((L + 1) / 2) * R * R);
+  b.Bbase = ws.take<double>((size_t)rcapin1 * n1 * n2);
+  b.B0 = ws.take<double>((size_t)R * n1 * n2);
+  b.W = ws.take<double>((size_t)R * K1);
+  b.core1 = ws.take<double>((size_t)K1 * n1 * (d == 3 ? K2 : 1));
+  b.core2 = ws.take<double>((size_t)(d == 3 ? K2 * n2 : 1));
+  b.Bnew = ws.take<double>((size_t)K1 * n1 * n2);
+  b.vJ = ws.take<double>(K1);
+  return b;
+}
+
+template <typename S>
+tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& ws) {
+  cudaStream_t s = ctx->stream;
+  const int d = x->d;
+  const long N = x->n[0];
+  const int n1 = x->n[1], n2 = (d == 3) ? x->n[2] : 1;
+  const int K1 = x->rcap[1], K2 = (d == 3) ? x->rcap[2] : 1;
+  LivePattern lp{x->rank + 1, K1, 1, 0};
+  const int R = lp.ncap();
+  RoundBufs b = take_round_bufs(ws, ctx->num_sms, d, R, N, n1, n2, K1, K2, K1);
+  SmallJob job{};
+  job.d = d;
+  job.n1 = n1;
+  job.n2 = n2;
+  job.nrowsZ = N;
+  job.lp = lp;
+  job.r2_ptr = (d == 3) ? x->rank + 2 : nullptr;
+  job.r2_nblk = 1;
+  job.r2_nextra = 0;
+  job.tol = tol;
+  job.rmax = rmax;
+  job.K1cap = K1;
+  job.K2cap = K2;
+  job.B0 = b.Bbase;
+  job.domega = nullptr;
+  job.W = b.W;
+  job.core1 = b.core1;
+  job.core2 = b.core2;
+  job.Bnew = b.Bnew;
+  job.vJ = b.vJ;
+  job.ctrl = ctx->ctrl;
+  double* domega_ones = ws.take<double>((size_t)n1 * n2);
+  job.domega = domega_ones;
+  double* RZ = nullptr;
+  if (!ws.dry) {
+    tt_status st = run_tsqr<double, kBR>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, 0, b.tsqr_a,
+                                         b.tsqr_b, &RZ);
+    if (st != TT_OK) return st;
+    right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, b.Bbase);
+    cudaMemsetAsync(domega_ones, 0, sizeof(double) * (size_t)n1 * n2, s);
+  }
+  job.RZ = RZ;
+  tt_status st = small_round(s, ctx->num_sms, job, ws);
+  if (st != TT_OK || ws.dry) return st;
+  st = launch_update<double>(s, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
+                             EpiPlain<S>{(S*)x->core[0], K1}, nullptr);
+  if (st != TT_OK) return st;
+  const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
+  k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b.core1, b.core2,
+                                                            (S*)x->core[1], d == 3 ? (S*)x->core[2] : nullptr,
+                                                            ctx->ctrl, x->rank);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+template <typename S>
+tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol, int rmax, double* energy,
+                    Bump& ws) {
+  cudaStream_t s = ctx->stream;
+  const int d = I->d;
+  const long N = I->n[0];
+  const int n1 = p->n1, n2 = p->n2, nang = n1 * n2;
+  const int K1 = I->rcap[1], K2 = (d == 3) ? I->rcap[2] : 1;
+  // ---- round 1: the transport sum, never materialised
+  LivePattern lp1{I->rank + 1, K1, p->nterm + 1, p->nbc};
+  const int R1 = lp1.ncap();
+  RoundBufs b1 = take_round_bufs(ws, ctx->num_sms, d, R1, N, n1, n2, K1, K2, K1);
+  S* Zsrc = ws.take<S>((size_t)N * (K1 + 1));
+  const long ngrid = (N + kTM - 1) / kTM;
+  double* part1 = ws.take<double>((size_t)2 * ngrid);
+  double* part2 = ws.take<double>((size_t)2 * ngrid);
+  double* part0 = ws.take<double>((size_t)((N + 255) / 256));
+  double* sums = ws.take<double>(8);
+  double* vJ0 = ws.take<double>(K1);
+  SrcStencil<S> src1{};
+  fill_stencil<S>(src1, p, (const S*)I->core[0], K1);
+  SmallJob j1{};
+  j1.d = d;
+  j1.n1 = n1;
+  j1.n2 = n2;
+  j1.nrowsZ = N;
+  j1.lp = lp1;
+  j1.r2_ptr = (d == 3) ? I->rank + 2 : nullptr;
+  j1.r2_nblk = p->nterm + 1;
+  j1.r2_nextra = p->nbc;
+  j1.tol = tol;
+  j1.rmax = rmax;
+  j1.K1cap = K1;
+  j1.K2cap = K2;
+  j1.B0 = b1.B0;
+  j1.domega = p->domega;
+  j1.W = b1.W;
+  j1.core1 = b1.core1;
+  j1.core2 = b1.core2;
+  j1.Bnew = b1.Bnew;
+  j1.vJ = b1.vJ;
+  j1.ctrl = ctx->ctrl;
+  double* RZ1 = nullptr;
+  if (!ws.dry) {
+    right_part<S>(s, d, K1, n1, K2, n2, (const S*)I->core[1], d == 3 ? (const S*)I->core[2] : nullptr, b1.Bbase);
+    if (energy) {
+      k_vj_host_launch(s, K1, nang, b1.Bbase, p->domega, vJ0);
+      k_rowdot_partials<S><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, K1, K1, (const S*)I->core[0], vJ0, part0,
+                                                                      nullptr, 0.0);
+      reduce_partials(s, part0, (N + 255) / 256, 1, sums, 1.0);
+    }
+    k_b0_transport<<<256, 256, 0, s>>>(K1, p->nterm, p->nbc, n1, n2, b1.Bbase, p->fac1, p->fac2, p->bc_term_dev,
+                                       b1.B0);
+    tt_status st = run_tsqr<double, kBR>(s, ctx->num_sms, src1, lp1, N, 0, b1.tsqr_a, b1.tsqr_b, &RZ1);
+    if (st != TT_OK) return st;
+  }
+  j1.RZ = RZ1;
+  tt_status st = small_round(s, ctx->num_sms, j1, ws);
+  if (st != TT_OK) return st;
+  // ---- source step fused into the write of the rounded transport update
+  LivePattern lp2{nullptr, K1, 1, 1};
+  RoundBufs b2 = take_round_bufs(ws, ctx->num_sms, d, lp2.ncap(), N, n1, n2, K1, K2, K1);
+  if (ws.dry) {
+    SmallJob j2 = j1;
+    j2.lp = lp2;
+    return small_round(s, ctx->num_sms, j2, ws);
+  }
+  st = launch_update<double>(s, src1, lp1, N, b1.W, K1,
+                             EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps}, part1);
+  if (st != TT_OK) return st;
+  k_save_ranks<<<1, 32, 0, s>>>(ctx->ctrl);
+  lp2.r_ptr = &ctx->ctrl->k[2];
+  // ---- round 2: [D^-1 Z_new, g]
+  k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0);
+  double* RZ2 = nullptr;
+  st = run_tsqr<double, kBR>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, 0, b2.tsqr_a, b2.tsqr_b, &RZ2);
+  if (st != TT_OK) return st;
+  SmallJob j2 = j1;
+  j2.lp = lp2;
+  j2.r2_ptr = (d == 3) ? &ctx->ctrl->k[3] : nullptr;
+  j2.r2_nblk = 1;
+  j2.r2_nextra = 1;
+  j2.B0 = b2.B0;
+  j2.RZ = RZ2;
+  j2.W = b2.W;
+  j2.core1 = b2.core1;
+  j2.core2 = b2.core2;
+  j2.Bnew = b2.Bnew;
+  j2.vJ = b2.vJ;
+  st = small_round(s, ctx->num_sms, j2, ws);
+  if (st != TT_OK) return st;
+  st = launch_update<double>(s, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
+                             EpiFinal<S>{(S*)I->core[0], K1, b2.vJ}, part2);
+  if (st != TT_OK) return st;
+  const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
+  k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b2.core1, b2.core2,
+                                                            (S*)I->core[1], d == 3 ? (S*)I->core[2] : nullptr,
+                                                            ctx->ctrl, I->rank);
+  if (energy) {
+    reduce_partials(s, part1, ngrid, 2, sums + 2, 1.0);
+    reduce_partials(s, part2, ngrid, 2, sums + 4, 1.0);
+    k_energy_pack<<<1, 32, 0, s>>>(sums, sums + 2, sums + 4, 4.0 * kPi / p->c * p->dV, energy);
+  }
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+template tt_status round_impl<double>(tt_context*, tt_tensor*, double, int, Bump&);
+template tt_status round_impl<float>(tt_context*, tt_tensor*, double, int, Bump&);
+template tt_status step_impl<double>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
+template tt_status step_impl<float>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
+
+template <typename S>
+tt_status energy_density_impl(tt_context* ctx, const tt_plan* p, const tt_tensor* x, double* out, Bump& ws) {
+  cudaStream_t s = ctx->stream;
+  const int d = x->d;
+  const long N = x->n[0];
+  const int n1 = x->n[1], n2 = (d == 3) ? x->n[2] : 1;
+  const int K1 = x->rcap[1], K2 = (d == 3) ? x->rcap[2] : 1;
+  double* Bb = ws.take<double>((size_t)K1 * n1 * n2);
+  double* v = ws.take<double>(K1);
+  if (ws.dry) return TT_OK;
+  right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, Bb);
+  k_vj_host_launch(s, K1, n1 * n2, Bb, p->domega, v);
+  k_rowdot_partials<S><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, K1, K1, (const S*)x->core[0], v, nullptr, out,
+                                                                  4.0 * kPi / p->c);
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+template tt_status energy_density_impl<double>(tt_context*, const tt_plan*, const tt_tensor*, double*, Bump&);
+template tt_status energy_density_impl<float>(tt_context*, const tt_plan*, const tt_tensor*, double*, Bump&);
+
+}  // namespace ttk

@@ -1,0 +1,20 @@
+// Internal entry points of the step/rounding orchestration (see step.cu, prim.cu).
+#pragma once
+#include "common.cuh"
+#include "small.cuh"
+
+namespace ttk {
+template <typename S>
+tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& ws);
+template <typename S>
+tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol, int rmax, double* energy,
+                    Bump& ws);
+template <typename S>
+tt_status energy_density_impl(tt_context* ctx, const tt_plan* p, const tt_tensor* x, double* out, Bump& ws);
+template <typename S>
+tt_status apply_transport_impl(tt_context* ctx, const tt_plan* p, const tt_tensor* in, tt_tensor* out);
+template <typename S>
+tt_status axpy_impl(tt_context* ctx, double alpha, const tt_tensor* x, tt_tensor* y);
+template <typename S>
+tt_status dot_impl(tt_context* ctx, const tt_tensor* x, const tt_tensor* y, double* out, Bump& ws);
+}  // namespace ttk

@@ -1,0 +1,259 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (FP64 path): 1e-13 relative for exact operations (plan arrays, transport sum,
+axpy, dot), 1e-10 relative for anything that goes through rounding (TSQR + Jacobi vs
+LAPACK Householder QR + SVD), and identical ranks whenever the oracle's singular-value tail
+is not within a relative 1e-9 of the truncation threshold.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import dense, naive_tt as nt, planck, problem, quadrature  # noqa: E402
+from paper_2602_00290_gb300.workloads import plane_config1, random_tt, slab_config0  # noqa: E402
+
+TIE = 1e-9
+
+
+@pytest.fixture(scope="module")
+def tt():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2602_00290_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(tt):
+    return tt.Context(0)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b)))) / max(float(np.max(np.abs(np.asarray(b)))), 1e-300)
+
+
+def small_plane(**kw):
+    args = dict(nx=12, ny=10, G=5, ntheta=4, nphi=8, rmax=8, tol=1e-6, steps=4)
+    args.update(kw)
+    return plane_config1(**args)
+
+
+# ---------------------------------------------------------------------------------------- plan
+
+@pytest.mark.parametrize("wl", [slab_config0(), small_plane(), small_plane().with_(
+    inflow_temperature=(0.8, None, 0.5, None, None, None))])
+def test_plan_arrays_match_oracle(tt, ctx, wl):
+    plan = tt.Plan(ctx, wl)
+    coef = problem.build(wl)
+    eps = plan.array(0)
+    big = coef.eps > 1e-290
+    assert np.all((eps == 0) == (coef.eps == 0)) or np.max(np.abs(eps - coef.eps)) < 1e-299
+    assert np.max(np.abs(eps[big] / coef.eps[big] - 1.0)) < 1e-13
+    assert rel(plan.array(1), coef.dirs["domega"]) < 1e-14
+    assert rel(plan.array(2), coef.dirs["mu"]) < 1e-14
+    assert rel(plan.array(4), coef.acoef) < 1e-15
+    assert rel(plan.array(5), coef.scoef + 0.0) < 1e-15 or np.all(coef.scoef == 0)
+    inflow = plan.array(6).reshape(6, wl.ngroup)
+    for f in range(6):
+        want = coef.inflow[f] if coef.inflow[f] is not None else np.zeros(wl.ngroup)
+        assert np.max(np.abs(inflow[f] - want)) <= 1e-13 * max(np.max(np.abs(want)), 1e-300)
+
+
+# --------------------------------------------------------------------------- primitives (exact)
+
+@pytest.mark.parametrize("n,ra,rb", [([50, 6, 7], [3, 4], [2, 5]), ([37, 9], [4], [3])])
+def test_dot_matches_brute_force(tt, ctx, n, ra, rb):
+    a = random_tt(n, ra, seed=1)
+    b = random_tt(n, rb, seed=2)
+    x = tt.TT.from_cores(a, rcap=[r + 2 for r in ra])
+    y = tt.TT.from_cores(b, rcap=[r + 1 for r in rb])
+    got = tt.tt_dot(ctx, x, y).item()
+    want = float(np.sum(nt.full(a) * nt.full(b)))
+    assert abs(got - want) <= 1e-12 * max(abs(want), nt.norm(a) * nt.norm(b))
+
+
+@pytest.mark.parametrize("n,ra,rb", [([40, 5, 6], [3, 2], [2, 3]), ([33, 8], [3], [2])])
+def test_axpy_concatenates(tt, ctx, n, ra, rb):
+    a = random_tt(n, ra, seed=3)
+    b = random_tt(n, rb, seed=4)
+    x = tt.TT.from_cores(a)
+    y = tt.TT.from_cores(b, rcap=[p + q for p, q in zip(ra, rb)])
+    tt.tt_axpy(ctx, -0.75, x, y)
+    ctx.sync()
+    assert y.ranks()[1:-1] == [p + q for p, q in zip(ra, rb)]
+    assert rel(nt.full(y.to_cores()), -0.75 * nt.full(a) + nt.full(b)) < 1e-14
+
+
+def test_axpy_capacity_overflow_is_latched(tt, ctx):
+    a = random_tt([20, 4, 5], [3, 2], seed=5)
+    x = tt.TT.from_cores(a)
+    y = tt.TT.from_cores(a)  # capacities equal to the live ranks: no room
+    before = nt.full(y.to_cores())
+    tt.tt_axpy(ctx, 1.0, x, y)
+    with pytest.raises(tt.TTError) as e:
+        ctx.sync()
+    assert e.value.status == tt.TT_ERR_CAPACITY
+    assert y.ranks() == [1, 3, 2, 1]
+    assert rel(nt.full(y.to_cores()), before) == 0.0
+    ctx.sync()  # status was cleared
+
+
+@pytest.mark.parametrize("wl", [slab_config0().with_(inflow_temperature=(0.9, 0.3, None, None, None, None)),
+                                small_plane(), small_plane().with_(inflow_temperature=(0.8, None, None, 0.4, None, None))])
+def test_apply_transport_matches_explicit_sum(tt, ctx, wl):
+    coef = problem.build(wl)
+    plan = tt.Plan(ctx, wl)
+    n = plan.n
+    r = [3] if len(n) == 2 else [3, 2]
+    a = random_tt(n, r, seed=6)
+    x = tt.TT.from_cores(a, rcap=[q + 1 for q in r])
+    want = nt.transport_sum(a, coef)
+    R = nt.ranks(want)[1:-1]
+    out = tt.TT(n, [q + 2 for q in R])
+    tt.tt_apply_transport(ctx, plan, x, out)
+    ctx.sync()
+    assert out.ranks()[1:-1] == R
+    assert rel(nt.full(out.to_cores()), nt.full(want)) < 1e-13
+
+
+def test_apply_transport_capacity_overflow(tt, ctx):
+    wl = small_plane()
+    plan = tt.Plan(ctx, wl)
+    a = random_tt(plan.n, [3, 2], seed=7)
+    x = tt.TT.from_cores(a)
+    out = tt.TT(plan.n, [10, 10])  # needs 15 x 10
+    tt.tt_apply_transport(ctx, plan, x, out)
+    with pytest.raises(tt.TTError) as e:
+        ctx.sync()
+    assert e.value.status == tt.TT_ERR_CAPACITY
+    assert out.ranks() == [1, 1, 1, 1]
+
+
+# ------------------------------------------------------------------------------------ rounding
+
+def _tie_free(info):
+    return all(b["gap"] > TIE for b in info["bonds"])
+
+
+@pytest.mark.parametrize("n,r", [([300, 6, 7], [5, 4]), ([75, 9], [6]), ([1000, 16, 32], [12, 9])])
+def test_round_exact_reconstruction(tt, ctx, n, r):
+    a = random_tt(n, r, seed=8)
+    x = tt.TT.from_cores(a, rcap=[q + 3 for q in r])
+    tt.tt_round(ctx, x, 1e-12, min(r) + 3)
+    ctx.sync()
+    assert x.ranks()[1:-1] == r
+    assert rel(nt.full(x.to_cores()), nt.full(a)) < 1e-11
+
+
+@pytest.mark.parametrize("tol,rmax", [(1e-2, 20), (1e-4, 20), (1e-6, 20), (0.0, 20), (1e-3, 4)])
+def test_round_sum_matches_oracle(tt, ctx, tol, rmax):
+    """Round a sum of random TTs with decaying weights (a spread of singular values)."""
+    n = [233, 5, 9]
+    terms = [nt.scale(random_tt(n, [3, 2], seed=20 + i), 10.0 ** -i) for i in range(6)]
+    a = nt.add_many(terms)
+    info = {}
+    want = nt.round_tt(a, tol, rmax, info)
+    x = tt.TT.from_cores(a, rcap=[20, 20])
+    tt.tt_round(ctx, x, tol, rmax)
+    ctx.sync()
+    if _tie_free(info):
+        assert x.ranks() == nt.ranks(want)
+        assert rel(nt.full(x.to_cores()), nt.full(want)) < 1e-10
+
+
+def test_round_x_plus_x_and_zero(tt, ctx):
+    a = random_tt([120, 6, 7], [4, 3], seed=30)
+    x = tt.TT.from_cores(nt.add(a, a), rcap=[8, 6])
+    tt.tt_round(ctx, x, 1e-10, 6)
+    ctx.sync()
+    assert x.ranks() == [1, 4, 3, 1]
+    assert rel(nt.full(x.to_cores()), 2 * nt.full(a)) < 1e-12
+    z = tt.TT([120, 6, 7], [8, 6])  # all-zero cores, ranks 1
+    tt.tt_round(ctx, z, 1e-6, 6)
+    ctx.sync()
+    assert z.ranks() == [1, 1, 1, 1]
+    assert not np.any(nt.full(z.to_cores()))
+
+
+def test_round_rejects_rmax_above_capacity(tt, ctx):
+    x = tt.TT.from_cores(random_tt([30, 4, 5], [2, 2], seed=1), rcap=[4, 4])
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_round(ctx, x, 1e-6, 5)
+    assert e.value.status == tt.TT_ERR_CAPACITY
+
+
+# ---------------------------------------------------------------------------------- time steps
+
+def _run_steps(tt, ctx, wl, nsteps, rcap, dtype="f64"):
+    coef = problem.build(wl)
+    plan = tt.Plan(ctx, wl)
+    x = tt.initial_state(plan, rcap, dtype)
+    ref = nt.initial_tt(problem.initial_rows(wl, coef), coef)
+    energy = torch.zeros(4, dtype=torch.float64, device="cuda")
+    for s in range(nsteps):
+        info = {}
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64", energy)
+        ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
+        ctx.sync()
+        tie_free = _tie_free(info["transport_round"]) and _tie_free(info["source_round"])
+        yield s, x, ref, coef, plan, energy.cpu().numpy(), tie_free
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(tol=1e-8, rmax=12), dict(tol=1e-4, rmax=6),
+                                dict(inflow_temperature=(0.9, None, 0.6, None, None, None)),
+                                dict(nx=7, ny=9, G=3, ntheta=6, nphi=12, rmax=10)])
+def test_step_plane_matches_naive_tt(tt, ctx, kw):
+    infl = kw.pop("inflow_temperature", None)
+    wl = small_plane(**kw)
+    if infl is not None:
+        wl = wl.with_(inflow_temperature=infl)
+    rcap = [wl.rmax, wl.rmax]
+    for s, x, ref, coef, plan, energy, tie_free in _run_steps(tt, ctx, wl, 4, rcap):
+        if not tie_free:
+            pytest.skip("rank decision within 1e-9 of the threshold")
+        assert x.ranks() == nt.ranks(ref), (s, x.ranks(), nt.ranks(ref))
+        assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10
+        E = tt.tt_energy_density(ctx, plan, x).cpu().numpy()
+        assert rel(E, nt.energy_density_rows(ref, coef)) < 1e-10
+        Etot = coef.dV * float(np.sum(nt.energy_density_rows(ref, coef)))
+        assert abs(energy[1] - Etot) <= 1e-10 * Etot
+
+
+def test_step_slab_exact_rank_matches_dense(tt, ctx):
+    """1-D slab workload (Nx=64, G=16, 8 GL mu, dt=0.01, 10 steps, exact rank) vs the dense
+    FP64 stepper: 1e-10 relative."""
+    wl = slab_config0()
+    S = dense.DenseSolver(wl)
+    I = S.initial()
+    last = None
+    for s, x, ref, coef, plan, energy, _ in _run_steps(tt, ctx, wl, wl.steps, [wl.rmax]):
+        I = S.step(I)
+        last = x
+        assert rel(nt.to_dense_rows(x.to_cores()), I) < 1e-10
+    assert last.ranks()[1] <= wl.rmax
+
+
+def test_step_energy_report_balances(tt, ctx):
+    """E* - E before = -dt * net outflow is checked by the oracle; here the report's terms are
+    consistent with the state: E_after from the final rows and the exchange term."""
+    wl = small_plane(tol=1e-10, rmax=8)
+    coef = problem.build(wl)
+    for s, x, ref, coef, plan, energy, _ in _run_steps(tt, ctx, wl, 2, [8, 8]):
+        E_after = coef.dV * float(np.sum(nt.energy_density_rows(ref, coef)))
+        assert abs(energy[1] - E_after) <= 1e-9 * E_after
+        assert energy[0] > 0 and energy[2] > 0
+
+
+def test_step_rejects_mismatched_plan(tt, ctx):
+    wl = small_plane()
+    plan = tt.Plan(ctx, wl)
+    x = tt.TT([wl.nrow + 1, wl.ntheta, wl.nphi], [4, 4])
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_step(ctx, plan, x, 1e-6, 4)
+    assert e.value.status == tt.TT_ERR_SHAPE
