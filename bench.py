@@ -1,0 +1,295 @@
+"""Benchmark of the tensor-train multigroup S_N transport step on GB300.
+
+Workload: the 2-D plane problem -- 128 x 128 cells on [0,1]^2, G = 64 log-spaced groups,
+16 polar x 32 azimuthal ordinates (536,870,912 full-grid unknowns), Gaussian-blob density
+(8 blobs, contrast 100), kappa_s = 0.1 kappa_a, T linear in x, vacuum boundaries, CFL 0.5,
+TT ranks capped at 32, rounding tolerance 1e-6.  One step = transport, round, source,
+round (tt_step).  W warm-up steps start from I^0 = epsilon(T); K steps are then timed.
+
+Our arm: CUDA events around each tt_step on the library's stream, L2 flushed (256 MB
+write) between timed steps, max over ranks; N > 1 runs independent replicas.
+Reference arm (--impl reference): the CPU oracle (naive explicit-sum TT, LAPACK QR+SVD)
+on the same workload, on the host cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TT transport steps/s and core-contraction TFLOP/s at fixed tol, FP64 vs mixed"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64"])
+    ap.add_argument("--size", default="full", choices=["full", "small"])
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(size):
+    from paper_2602_00290_gb300.workloads import plane_config1
+    if size == "small":
+        return plane_config1(nx=32, ny=32, G=16, ntheta=8, nphi=16, rmax=16)
+    return plane_config1()
+
+
+def counted_flops(N, r_before, r_mid, r_after, nterm=4, nbc=0):
+    """Counted core-contraction flops of one step: 2 N (R1^2 + R1 r' + R2^2 + R2 r'') with
+    R1 = (n+1) r + n_b (transport sum) and R2 = r' + 1 (source sum)."""
+    R1 = (nterm + 1) * r_before + nbc
+    R2 = r_mid + 1
+    return 2.0 * N * (R1 * R1 + R1 * r_mid + R2 * R2 + R2 * r_after)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.rows = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        time.sleep(0.1)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_steps_per_s(wl, x_cores, nsteps_max=3, budget_s=20.0):
+    """Time the CPU oracle (naive TT step) on the given state; returns (steps/s, steps, seconds)."""
+    from oracle import naive_tt, problem
+    coef = problem.build(wl)
+    x = x_cores
+    t0 = time.perf_counter()
+    n = 0
+    while n < nsteps_max:
+        x = naive_tt.step(x, coef, wl.tol, wl.rmax)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import naive_tt, problem
+    wl = workload(args.size)
+    coef = problem.build(wl)
+    x = naive_tt.initial_tt(problem.initial_rows(wl, coef), coef)
+    for _ in range(args.warmup):
+        x = naive_tt.step(x, coef, wl.tol, wl.rmax)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x = naive_tt.step(x, coef, wl.tol, wl.rmax)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "tol": wl.tol, "rmax": wl.rmax, "steps_from": "I0 = epsilon(T)"},
+            "cpu_baseline": {"kind": "oracle", "value": v, "unit": "steps/s", "cores": host_cores(),
+                             "sample": f"{args.steps} naive explicit-sum TT steps (LAPACK QR + SVD) after "
+                                       f"{args.warmup} warm-up steps from I0"},
+            "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "ranks": naive_tt.ranks(x)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    from paper_2602_00290_gb300 import _build
+    _build.build()
+    import paper_2602_00290_gb300 as tt
+
+    wl = workload(args.size)
+    ctx = tt.Context()
+    plan = tt.Plan(ctx, wl)
+    rcap = [wl.rmax, wl.rmax]
+    x = tt.initial_state(plan, rcap)
+    stream = ctx.stream
+    energy = torch.zeros(4, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, args.precision, energy)
+    ctx.sync()
+    ranks = [x.ranks()]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    clocks = Clocks(vis)
+    ctx.counters(reset=True)
+    ctx.set_timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    rank_hist = torch.zeros(args.steps, 4, dtype=torch.int32, device="cuda")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, args.precision, energy)
+        evs[i][1].record(stream)
+        rank_hist[i].copy_(x.rank)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.sync()
+    ctx.set_timing(False)
+    kms, klaunch = ctx.counters(reset=True)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    hist = rank_hist.cpu().numpy()
+    r_seq = [ranks[0]] + [list(map(int, h)) for h in hist]
+    N = wl.nrow
+    flops = 0.0
+    leaf_flops = 0.0
+    for i in range(args.steps):
+        rb, ra = r_seq[i][1], r_seq[i + 1][1]
+        flops += counted_flops(N, rb, ra, ra)
+        R1, R2 = 5 * rb, ra + 1
+        leaf_flops += 2.0 * N * (R1 * R1 + R2 * R2)
+    value = ws * args.steps / (total_ms / 1e3)
+    tflops = flops / (total_ms / 1e3) / 1e12
+    # roofline of the dominant pass over the merged core (TSQR leaves here)
+    leaf_tf = leaf_flops / (kms["tsqr_leaf"] / 1e3) / 1e12 if kms["tsqr_leaf"] > 0 else None
+    roof = {"kernel": "k_tsqr_leaf (Householder TSQR over the transport and source sums)",
+            "bound": "alu", "achieved": leaf_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": (leaf_tf / FP64_PEAK_TFLOPS) if leaf_tf else None, "traffic": None,
+            "peak_source": "FP64 FMA units: 152 SMs x 2/clk x 2 flop x 2070 MHz (no FP64 entry in MEASURED_PEAKS.json)",
+            "share": kms["tsqr_leaf"] / total_ms if total_ms else None}
+    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "groups": wl.ngroup,
+                       "ordinates": [wl.ntheta, wl.nphi], "tol": wl.tol, "rmax": wl.rmax,
+                       "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "tflops": tflops, "roofline": roof,
+            "breakdown_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+            "gpu_launches": int(sum(klaunch.values())), "clocks": clk, "ranks": r_seq[-1],
+            "rank_history": [r[1:-1] for r in r_seq]}
+    # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
+    if args.e2e_steps > 0:
+        host = [c.cpu().pin_memory() for c in x.cores]
+        host_rank = x.rank.cpu().pin_memory()
+        host_energy = torch.zeros(4, dtype=torch.float64).pin_memory()
+        h2d = sum(c.numel() * c.element_size() for c in host) + host_rank.numel() * 4
+        d2h = h2d + host_energy.numel() * 8
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            with torch.cuda.stream(stream):
+                for c, h in zip(x.cores, host):
+                    c.copy_(h, non_blocking=True)
+                x.rank.copy_(host_rank, non_blocking=True)
+            tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, args.precision, energy)
+            with torch.cuda.stream(stream):
+                for c, h in zip(x.cores, host):
+                    h.copy_(c, non_blocking=True)
+                host_rank.copy_(x.rank, non_blocking=True)
+                host_energy.copy_(energy, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1)
+        line["e2e"] = {"value": ws * args.e2e_steps / (e2e_ms / 1e3), "unit": "steps/s",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "steps": args.e2e_steps}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = x.to_cores()
+        v, n, dt = oracle_steps_per_s(wl, cores)
+        line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
+                                "sample": f"{n} naive explicit-sum TT step(s) (numpy, LAPACK QR + SVD) of the "
+                                          f"same workload from the GPU state after the timed steps ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -102,6 +102,24 @@ const char *tt_status_string(tt_status s);
 tt_status tt_context_create(tt_context **ctx, int device, void *cuda_stream, size_t workspace_bytes);
 tt_status tt_context_destroy(tt_context *ctx);
 
+/* Opt-in instrumentation of a context (off by default).  While timing is enabled, every
+ * later call records CUDA events on the context stream around its hot kernels, grouped as
+ * TT_TIMER_* categories.  Launch counts are always collected. */
+typedef enum {
+  TT_TIMER_TSQR_LEAF = 0,   /* leaf pass of the tall-skinny QR over the merged core        */
+  TT_TIMER_TSQR_MERGE = 1,  /* merge tree of the R factors                                 */
+  TT_TIMER_SMALL = 2,       /* small-core sweep (QRs, Jacobi SVDs, rank decisions)         */
+  TT_TIMER_UPDATE = 3,      /* update pass Z_new = Z_sum W (and the fused source step)     */
+  TT_TIMER_OTHER = 4        /* everything else (counted only)                              */
+} tt_timer;
+#define TT_TIMER_COUNT 5
+tt_status tt_context_set_timing(tt_context *ctx, int enable);
+
+/* Synchronise the context stream and report, per tt_timer category, the summed kernel time
+ * in milliseconds (ms[TT_TIMER_COUNT], nullable) and the number of kernel launches
+ * (launches[TT_TIMER_COUNT], nullable) since the last reset; reset != 0 clears both. */
+tt_status tt_context_counters(tt_context *ctx, double *ms, int64_t *launches, int reset);
+
 /* Synchronise the context stream, then return and clear the latched device status. */
 tt_status tt_sync(tt_context *ctx);
 

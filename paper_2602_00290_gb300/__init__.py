@@ -29,7 +29,9 @@ PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED}
 
 EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sync", "tt_workspace_query",
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
-           "tt_apply_transport", "tt_step", "tt_energy_density")
+           "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
+           "tt_context_counters")
+TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other")
 
 
 class TTError(RuntimeError):
@@ -86,6 +88,8 @@ def lib():
             "tt_apply_transport": [vp, vp, ctypes.POINTER(_Tensor), ctypes.POINTER(_Tensor)],
             "tt_step": [vp, vp, ctypes.POINTER(_Tensor), dbl, i32, ctypes.c_int, vp],
             "tt_energy_density": [vp, vp, ctypes.POINTER(_Tensor), vp],
+            "tt_context_set_timing": [vp, ctypes.c_int],
+            "tt_context_counters": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -130,6 +134,16 @@ class Context:
 
     def sync(self):
         _check(lib().tt_sync(self.handle), "tt_sync")
+
+    def set_timing(self, enable: bool):
+        _check(lib().tt_context_set_timing(self.handle, 1 if enable else 0), "tt_context_set_timing")
+
+    def counters(self, reset: bool = False):
+        """(ms per category, launches per category) since the last reset (tt_context_counters)."""
+        ms = (ctypes.c_double * len(TIMER_NAMES))()
+        n = (ctypes.c_int64 * len(TIMER_NAMES))()
+        _check(lib().tt_context_counters(self.handle, ms, n, 1 if reset else 0), "tt_context_counters")
+        return dict(zip(TIMER_NAMES, list(ms))), dict(zip(TIMER_NAMES, list(n)))
 
     def close(self):
         if getattr(self, "handle", None):

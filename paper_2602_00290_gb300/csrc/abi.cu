@@ -5,10 +5,21 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "instr.cuh"
 #include "small.cuh"
 #include "step.cuh"
 
+namespace ttk {
+thread_local Instr* g_instr = nullptr;
+}
+
 namespace {
+
+struct InstrGuard {
+  ttk::Instr* prev;
+  explicit InstrGuard(tt_context* ctx) : prev(ttk::g_instr) { ttk::g_instr = static_cast<ttk::Instr*>(ctx->instr); }
+  ~InstrGuard() { ttk::g_instr = prev; }
+};
 
 tt_status check_tensor(const tt_tensor* x) {
   if (!x || !x->rank) return TT_ERR_ARG;
@@ -56,6 +67,7 @@ tt_status ensure_ws(tt_context* ctx, size_t need) {
 // Run `fn(Bump&)` once as a dry run to size the workspace, then for real.
 template <class F>
 tt_status with_ws(tt_context* ctx, F&& fn) {
+  InstrGuard guard(ctx);
   ttk::Bump dry{nullptr, 0, 0, true};
   tt_status st = fn(dry);
   if (st != TT_OK) return st;
@@ -95,6 +107,7 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->stream = static_cast<cudaStream_t>(stream);
   ctx->ws = nullptr;
   ctx->ws_bytes = 0;
+  ctx->instr = new ttk::Instr();
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
@@ -122,7 +135,39 @@ tt_status tt_context_destroy(tt_context* ctx) {
   cudaStreamSynchronize(ctx->stream);
   if (ctx->ws) cudaFree(ctx->ws);
   cudaFree(ctx->ctrl);
+  ttk::Instr* in = static_cast<ttk::Instr*>(ctx->instr);
+  for (cudaEvent_t e : in->pool) cudaEventDestroy(e);
+  delete in;
   delete ctx;
+  return TT_OK;
+}
+
+tt_status tt_context_set_timing(tt_context* ctx, int enable) {
+  if (!ctx) return TT_ERR_ARG;
+  static_cast<ttk::Instr*>(ctx->instr)->timing = (enable != 0);
+  return TT_OK;
+}
+
+tt_status tt_context_counters(tt_context* ctx, double* ms, int64_t* launches, int reset) {
+  if (!ctx) return TT_ERR_ARG;
+  ttk::Instr* in = static_cast<ttk::Instr*>(ctx->instr);
+  set_device(ctx);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
+  double acc[ttk::kNumCat] = {0, 0, 0, 0, 0};
+  for (const auto& r : in->recs) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return TT_ERR_CUDA;
+    acc[r.cat] += t;
+  }
+  for (int c = 0; c < ttk::kNumCat; ++c) {
+    if (ms) ms[c] = acc[c];
+    if (launches) launches[c] = in->launches[c];
+  }
+  if (reset) {
+    in->recs.clear();
+    in->pool_used = 0;
+    for (int c = 0; c < ttk::kNumCat; ++c) in->launches[c] = 0;
+  }
   return TT_OK;
 }
 
@@ -197,6 +242,7 @@ tt_status tt_axpy(tt_context* ctx, double alpha, const tt_tensor* x, tt_tensor* 
   if (st != TT_OK) return st;
   if (!std::isfinite(alpha)) return TT_ERR_ARG;
   set_device(ctx);
+  InstrGuard guard(ctx);
   return (x->dtype == TT_F64) ? ttk::axpy_impl<double>(ctx, alpha, x, y) : ttk::axpy_impl<float>(ctx, alpha, x, y);
 }
 
@@ -217,6 +263,7 @@ static tt_status check_round_args(const tt_tensor* x, double tol, int32_t rmax, 
   if (!(tol >= 0.0) || !std::isfinite(tol)) return TT_ERR_ARG;
   if (rmax < 1) return TT_ERR_ARG;
   if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return TT_ERR_ARG;
+  if (prec == TT_PREC_MIXED) return TT_ERR_UNSUPPORTED;
   for (int j = 1; j < x->d; ++j)
     if (rmax > x->rcap[j]) return TT_ERR_CAPACITY;
   return TT_OK;
@@ -243,6 +290,7 @@ tt_status tt_apply_transport(tt_context* ctx, const tt_plan* plan, const tt_tens
   if (st != TT_OK) return st;
   if (in->core[0] == out->core[0]) return TT_ERR_ARG;
   set_device(ctx);
+  InstrGuard guard(ctx);
   return (in->dtype == TT_F64) ? ttk::apply_transport_impl<double>(ctx, plan, in, out)
                                : ttk::apply_transport_impl<float>(ctx, plan, in, out);
 }

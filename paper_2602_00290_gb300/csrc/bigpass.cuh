@@ -3,6 +3,7 @@
 // source-step epilogue.  These are the kernels that touch every row of the TT state.
 #pragma once
 #include "common.cuh"
+#include "instr.cuh"
 
 namespace ttk {
 
@@ -256,13 +257,17 @@ tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, 
   if (L < 1) L = 1;
   cudaFuncSetAttribute(k_tsqr_leaf<T, BR, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_tsqr_merge<T, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_tsqr_leaf<T, BR, Src><<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a);
+  {
+    TimerScope scope(kTsqrLeaf, s);
+    k_tsqr_leaf<T, BR, Src><<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
+  }
+  TimerScope scope(kTsqrMerge, s);
   double* in = ws_a;
   double* out = ws_b;
   int n = (int)L;
   while (n > 1) {
     const int m = (n + 1) / 2;
-    k_tsqr_merge<T, BR><<<m, threads, smem, s>>>(lp, n, in, out);
+    k_tsqr_merge<T, BR><<<m, threads, smem, s>>>(lp, n, in, out); count_launch();
     double* t = in;
     in = out;
     out = t;

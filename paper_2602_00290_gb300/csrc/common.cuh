@@ -85,6 +85,7 @@ struct tt_context {
   ttk::DevCtrl* ctrl;  // device
   int num_sms;
   int smem_optin;
+  void* instr;  // ttk::Instr, opt-in counters and kernel timers
 };
 
 struct tt_plan {

@@ -226,13 +226,13 @@ tt_status apply_transport_impl(tt_context* ctx, const tt_plan* p, const tt_tenso
   const long N = in->n[0];
   const int rcapo2 = (d == 3) ? out->rcap[2] : 1;
   k_transport_Z<S><<<1024, 256, 0, s>>>(N, src, in->rank, (S*)out->core[0], out->rcap[1], p->nbc,
-                                        d == 3 ? in->rank + 2 : nullptr, rcapo2, &ctx->ctrl->status);
+                                        d == 3 ? in->rank + 2 : nullptr, rcapo2, &ctx->ctrl->status); count_launch();
   k_transport_small<S><<<64, 256, 0, s>>>(d, p->nterm, p->nbc, p->n1, p->n2, (const S*)in->core[1],
                                           d == 3 ? (const S*)in->core[2] : nullptr, in->rcap[1],
                                           d == 3 ? in->rcap[2] : 1, in->rank, (S*)out->core[1],
                                           d == 3 ? (S*)out->core[2] : nullptr, out->rcap[1], rcapo2, p->fac1, p->fac2,
-                                          p->bc_term_dev);
-  k_transport_ranks<<<1, 32, 0, s>>>(d, p->nterm, p->nbc, in->rank, out->rank, out->rcap[1], rcapo2);
+                                          p->bc_term_dev); count_launch();
+  k_transport_ranks<<<1, 32, 0, s>>>(d, p->nterm, p->nbc, in->rank, out->rank, out->rcap[1], rcapo2); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -243,12 +243,12 @@ tt_status axpy_impl(tt_context* ctx, double alpha, const tt_tensor* x, tt_tensor
   const long N = x->n[0];
   const int rcapy2 = (d == 3) ? y->rcap[2] : 1;
   k_axpy_Z<S><<<1024, 256, 0, s>>>(N, alpha, (const S*)x->core[0], x->rcap[1], x->rank, (S*)y->core[0], y->rcap[1],
-                                   y->rank, d, rcapy2, &ctx->ctrl->status);
+                                   y->rank, d, rcapy2, &ctx->ctrl->status); count_launch();
   k_axpy_small<S><<<64, 256, 0, s>>>(d, x->n[1], d == 3 ? x->n[2] : 1, (const S*)x->core[1],
                                      d == 3 ? (const S*)x->core[2] : nullptr, x->rcap[1], d == 3 ? x->rcap[2] : 1,
                                      x->rank, (S*)y->core[1], d == 3 ? (S*)y->core[2] : nullptr, y->rcap[1], rcapy2,
-                                     y->rank);
-  k_axpy_ranks<<<1, 32, 0, s>>>(d, x->rank, y->rank, y->rcap[1], rcapy2);
+                                     y->rank); count_launch();
+  k_axpy_ranks<<<1, 32, 0, s>>>(d, x->rank, y->rank, y->rcap[1], rcapy2); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -272,14 +272,14 @@ tt_status dot_impl(tt_context* ctx, const tt_tensor* x, const tt_tensor* y, doub
   if (ws.dry) return TT_OK;
   dim3 grid((unsigned)nchunks, (unsigned)((ne + 255) / 256));
   k_gram_partials<S><<<grid, 256, 0, s>>>(N, rows_per, (const S*)x->core[0], rx, rx, (const S*)y->core[0], ry, ry,
-                                          part);
-  k_sum_chunks<<<(ne + 255) / 256, 256, 0, s>>>(part, nchunks, ne, W1);
+                                          part); count_launch();
+  k_sum_chunks<<<(ne + 255) / 256, 256, 0, s>>>(part, nchunks, ne, W1); count_launch();
   right_part<S>(s, d, rx, n1, d == 3 ? x->rcap[2] : 1, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr,
                 Bx);
   right_part<S>(s, d, ry, n1, d == 3 ? y->rcap[2] : 1, n2, (const S*)y->core[1], d == 3 ? (const S*)y->core[2] : nullptr,
                 By);
   small_gemm<double, double>(s, rx, ry, nang, Bx, nang, 1, By, 1, nang, G, ry, nullptr, nullptr);
-  k_dot_final<<<1, 1024, 0, s>>>(ne, W1, G, out);
+  k_dot_final<<<1, 1024, 0, s>>>(ne, W1, G, out); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 

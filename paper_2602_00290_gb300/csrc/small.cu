@@ -331,7 +331,7 @@ template <typename TA, typename TB>
 void small_gemm(cudaStream_t s, int M, int N, int K, const TA* A, long sa0, long sa1, const TB* B, long sb0,
                 long sb1, double* C, long ldc, const int* nlive, const double* inv_colscale) {
   dim3 grid((N + 15) / 16, (M + 15) / 16);
-  k_small_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sa0, sa1, B, sb0, sb1, C, ldc, nlive, inv_colscale);
+  k_small_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sa0, sa1, B, sb0, sb1, C, ldc, nlive, inv_colscale); count_launch();
 }
 
 template void small_gemm<double, double>(cudaStream_t, int, int, int, const double*, long, long, const double*,
@@ -345,18 +345,18 @@ void right_part(cudaStream_t s, int d, int rcap1, int n1, int rcap2, int n2, con
   if (d == 3) {
     small_gemm<S, S>(s, rcap1 * n1, n2, rcap2, core1, rcap2, 1, core2, n2, 1, Bbase, n2, nullptr, nullptr);
   } else {
-    k_right_part2<S><<<(rcap1 * n1 + 255) / 256, 256, 0, s>>>(rcap1, n1, core1, Bbase);
+    k_right_part2<S><<<(rcap1 * n1 + 255) / 256, 256, 0, s>>>(rcap1, n1, core1, Bbase); count_launch();
   }
 }
 template void right_part<double>(cudaStream_t, int, int, int, int, int, const double*, const double*, double*);
 template void right_part<float>(cudaStream_t, int, int, int, int, int, const float*, const float*, double*);
 
 void k_vj_host_launch(cudaStream_t s, int K1, int nang, const double* B, const double* domega, double* vJ) {
-  k_vj<<<K1, 128, 0, s>>>(K1, nang, B, domega, vJ);
+  k_vj<<<K1, 128, 0, s>>>(K1, nang, B, domega, vJ); count_launch();
 }
 
 void reduce_partials(cudaStream_t s, const double* partials, long nblocks, int stride, double* out, double scale) {
-  k_reduce_partials<<<1, 1024, 0, s>>>(partials, nblocks, stride, out, scale);
+  k_reduce_partials<<<1, 1024, 0, s>>>(partials, nblocks, stride, out, scale); count_launch();
 }
 
 static tt_status jacobi(cudaStream_t s, int n, const double* R, Bump& ws, double* sigma, double* V,
@@ -366,7 +366,7 @@ static tt_status jacobi(cudaStream_t s, int n, const double* R, Bump& ws, double
   int* perm = ws.take<int>(n);
   if (ws.dry) return TT_OK;
   if (n > 1024) return TT_ERR_UNSUPPORTED;
-  k_jacobi<<<1, 1024, 0, s>>>(n, R, Aw, Vw, sigma, V, perm, 60, &ctrl->status);
+  k_jacobi<<<1, 1024, 0, s>>>(n, R, Aw, Vw, sigma, V, perm, 60, &ctrl->status); count_launch();
   return TT_OK;
 }
 
@@ -386,6 +386,7 @@ static tt_status small_qr(cudaStream_t s, int num_sms, const Src& src, long rows
 }
 
 tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) {
+  TimerScope scope(kSmall, s);
   const int R = j.lp.ncap();
   const int n1 = j.n1, n2 = j.n2, nang = n1 * n2;
   tt_status st;
@@ -401,11 +402,11 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
     if (st != TT_OK) return st;
     if (ws.dry) return TT_OK;
     k_decide<<<1, 32, 0, s>>>(sig, n1, 1, 2, j.tol, j.rmax, j.K1cap, j.nrowsZ, j.lp.r_ptr, j.lp.nblk,
-                              j.lp.nextra, 1, nullptr, 0, 0, nullptr, 0, n1, j.ctrl, 0);
+                              j.lp.nextra, 1, nullptr, 0, 0, nullptr, 0, n1, j.ctrl, 0); count_launch();
     small_gemm<double, double>(s, R, j.K1cap, n1, j.B0, n1, 1, V, n1, 1, j.W, j.K1cap, &j.ctrl->k[0], nullptr);
-    k_write_cores2<<<(j.K1cap * n1 + 255) / 256, 256, 0, s>>>(n1, j.K1cap, V, j.ctrl, j.core1);
+    k_write_cores2<<<(j.K1cap * n1 + 255) / 256, 256, 0, s>>>(n1, j.K1cap, V, j.ctrl, j.core1); count_launch();
     cudaMemcpyAsync(j.Bnew, j.core1, sizeof(double) * (size_t)j.K1cap * n1, cudaMemcpyDeviceToDevice, s);
-    k_vj<<<j.K1cap, 128, 0, s>>>(j.K1cap, nang, j.Bnew, j.domega, j.vJ);
+    k_vj<<<j.K1cap, 128, 0, s>>>(j.K1cap, nang, j.Bnew, j.domega, j.vJ); count_launch();
     return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
   // ---- d = 3 ----
@@ -423,7 +424,7 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
   double* B0p = ws.take<double>((size_t)R * nv);
   if (!ws.dry) {
     k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
-                              j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1);
+                              j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1); count_launch();
     small_gemm<double, double>(s, R * n1, K2, n2, Y, n2, 1, V2, n2, 1, Y2, K2, &j.ctrl->k[1], nullptr);
     small_gemm<double, double>(s, R * n1, K2, n2, j.B0, n2, 1, V2, n2, 1, B0p, K2, &j.ctrl->k[1], nullptr);
   }
@@ -438,16 +439,16 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
   double* V1 = ws.take<double>((size_t)nv * K1);
   if (ws.dry) return TT_OK;
   k_decide<<<1, 32, 0, s>>>(sig1, R, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
-                            nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0);
+                            nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0); count_launch();
   // V1 = Y2^T U1(:, :k1) diag(1/sigma1)
   small_gemm<double, double>(s, nv, K1, R, Y2, 1, nv, U1, R, 1, V1, K1, &j.ctrl->k[0], sig1);
-  k_reorth<<<1, 1024, 0, s>>>(nv, K1, V1, &j.ctrl->k[0], K2, &j.ctrl->k[1]);
-  k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2);
+  k_reorth<<<1, 1024, 0, s>>>(nv, K1, V1, &j.ctrl->k[0], K2, &j.ctrl->k[1]); count_launch();
+  k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2); count_launch();
   // W = B0p (R x nv) V1 (nv x K1)
   small_gemm<double, double>(s, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], nullptr);
   // Bnew = core1 (K1 n1 x K2) core2 (K2 x n2); vJ
   small_gemm<double, double>(s, K1 * n1, n2, K2, j.core1, K2, 1, j.core2, n2, 1, j.Bnew, n2, nullptr, nullptr);
-  k_vj<<<K1, 128, 0, s>>>(K1, nang, j.Bnew, j.domega, j.vJ);
+  k_vj<<<K1, 128, 0, s>>>(K1, nang, j.Bnew, j.domega, j.vJ); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 

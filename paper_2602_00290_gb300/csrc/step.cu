@@ -134,7 +134,8 @@ static tt_status launch_update(cudaStream_t s, const Src& src, LivePattern lp, l
   if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
   cudaFuncSetAttribute(k_update<T, kTM, Src, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long grid = (nrows + kTM - 1) / kTM;
-  k_update<T, kTM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials);
+  TimerScope scope(kUpdate, s);
+  k_update<T, kTM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -217,7 +218,7 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
   k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b.core1, b.core2,
                                                             (S*)x->core[1], d == 3 ? (S*)x->core[2] : nullptr,
-                                                            ctx->ctrl, x->rank);
+                                                            ctx->ctrl, x->rank); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -269,11 +270,11 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     if (energy) {
       k_vj_host_launch(s, K1, nang, b1.Bbase, p->domega, vJ0);
       k_rowdot_partials<S><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, K1, K1, (const S*)I->core[0], vJ0, part0,
-                                                                      nullptr, 0.0);
+                                                                      nullptr, 0.0); count_launch();
       reduce_partials(s, part0, (N + 255) / 256, 1, sums, 1.0);
     }
     k_b0_transport<<<256, 256, 0, s>>>(K1, p->nterm, p->nbc, n1, n2, b1.Bbase, p->fac1, p->fac2, p->bc_term_dev,
-                                       b1.B0);
+                                       b1.B0); count_launch();
     tt_status st = run_tsqr<double, kBR>(s, ctx->num_sms, src1, lp1, N, 0, b1.tsqr_a, b1.tsqr_b, &RZ1);
     if (st != TT_OK) return st;
   }
@@ -291,10 +292,10 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   st = launch_update<double>(s, src1, lp1, N, b1.W, K1,
                              EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps}, part1);
   if (st != TT_OK) return st;
-  k_save_ranks<<<1, 32, 0, s>>>(ctx->ctrl);
+  k_save_ranks<<<1, 32, 0, s>>>(ctx->ctrl); count_launch();
   lp2.r_ptr = &ctx->ctrl->k[2];
   // ---- round 2: [D^-1 Z_new, g]
-  k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0);
+  k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0); count_launch();
   double* RZ2 = nullptr;
   st = run_tsqr<double, kBR>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, 0, b2.tsqr_a, b2.tsqr_b, &RZ2);
   if (st != TT_OK) return st;
@@ -318,11 +319,11 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
   k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b2.core1, b2.core2,
                                                             (S*)I->core[1], d == 3 ? (S*)I->core[2] : nullptr,
-                                                            ctx->ctrl, I->rank);
+                                                            ctx->ctrl, I->rank); count_launch();
   if (energy) {
     reduce_partials(s, part1, ngrid, 2, sums + 2, 1.0);
     reduce_partials(s, part2, ngrid, 2, sums + 4, 1.0);
-    k_energy_pack<<<1, 32, 0, s>>>(sums, sums + 2, sums + 4, 4.0 * kPi / p->c * p->dV, energy);
+    k_energy_pack<<<1, 32, 0, s>>>(sums, sums + 2, sums + 4, 4.0 * kPi / p->c * p->dV, energy); count_launch();
   }
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
@@ -345,7 +346,7 @@ tt_status energy_density_impl(tt_context* ctx, const tt_plan* p, const tt_tensor
   right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, Bb);
   k_vj_host_launch(s, K1, n1 * n2, Bb, p->domega, v);
   k_rowdot_partials<S><<<(unsigned)((N + 255) / 256), 256, 0, s>>>(N, K1, K1, (const S*)x->core[0], v, nullptr, out,
-                                                                  4.0 * kPi / p->c);
+                                                                  4.0 * kPi / p->c); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 template tt_status energy_density_impl<double>(tt_context*, const tt_plan*, const tt_tensor*, double*, Bump&);
