@@ -24,7 +24,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "TT transport steps/s and core-contraction TFLOP/s at fixed tol, FP64 vs mixed"
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12  # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
 
 
 def parse():
@@ -33,8 +34,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64"])
-    ap.add_argument("--size", default="full", choices=["full", "small"])
+    ap.add_argument("--precision", default="both", choices=["fp64", "mixed", "both"])
+    ap.add_argument("--size", default="full", choices=["full", "medium", "small"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -44,6 +45,8 @@ def workload(size):
     from paper_2602_00290_gb300.workloads import plane_config1
     if size == "small":
         return plane_config1(nx=32, ny=32, G=16, ntheta=8, nphi=16, rmax=16)
+    if size == "medium":  # merged core of 96*96*64 rows x 32: 151 MB in FP64, above the 129 MB L2
+        return plane_config1(nx=96, ny=96)
     return plane_config1()
 
 
@@ -157,6 +160,77 @@ def run_reference(args):
     return 0
 
 
+def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index):
+    """W warm-up then K timed tt_step calls for one precision; returns (line fields, state)."""
+    dtype = "f64" if precision == "fp64" else "f32"
+    rcap = [wl.rmax, wl.rmax]
+    x = tt.initial_state(plan, rcap, dtype)
+    stream = ctx.stream
+    energy = torch.zeros(4, dtype=torch.float64, device="cuda")
+    for _ in range(args.warmup):
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
+    ctx.sync()
+    ranks = [x.ranks()]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    clocks = Clocks(clocks_index)
+    ctx.counters(reset=True)
+    ctx.diagnostics(reset=True)
+    ctx.set_timing(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    rank_hist = torch.zeros(args.steps, 4, dtype=torch.int32, device="cuda")
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
+        evs[i][1].record(stream)
+        rank_hist[i].copy_(x.rank)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ctx.sync()
+    ctx.set_timing(False)
+    kms, klaunch = ctx.counters(reset=True)
+    diag = ctx.diagnostics(reset=True)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    hist = rank_hist.cpu().numpy()
+    r_seq = [ranks[0]] + [list(map(int, h)) for h in hist]
+    N = wl.nrow
+    flops = 0.0
+    leaf_flops = 0.0
+    for i in range(args.steps):
+        rb, ra = r_seq[i][1], r_seq[i + 1][1]
+        flops += counted_flops(N, rb, ra, ra)
+        R1, R2 = 5 * rb, ra + 1
+        leaf_flops += 2.0 * N * (R1 * R1 + R2 * R2)
+    ws = dist.get_world_size() if dist else 1
+    out = {"value": ws * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
+           "tflops": flops / (total_ms / 1e3) / 1e12,
+           "breakdown_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+           "gpu_launches": int(sum(klaunch.values())), "clocks": clk, "ranks": r_seq[-1],
+           "rank_history": [r[1:-1] for r in r_seq], "jacobi": diag}
+    leaf_tf = leaf_flops / (kms["tsqr_leaf"] / 1e3) / 1e12 if kms["tsqr_leaf"] > 0 else None
+    if precision == "fp64":
+        peak, src, bound = FP64_PEAK_TFLOPS, ("FP64 FMA units: 152 SMs x 2/clk x 2 flop x 2070 MHz "
+                                              "(no FP64 entry in MEASURED_PEAKS.json)"), "alu"
+    else:
+        peak, src, bound = FP32_PEAK_TFLOPS, ("FP32 FMA units: 152 SMs x 128/clk x 2 flop x 2070 MHz "
+                                              "(no FP32 entry in MEASURED_PEAKS.json)"), "alu"
+    out["roofline"] = {"kernel": "k_tsqr_leaf (Householder TSQR over the transport and source sums)",
+                       "bound": bound, "achieved": leaf_tf, "peak": peak, "unit": "TFLOP/s",
+                       "frac": (leaf_tf / peak) if leaf_tf else None, "traffic": None, "peak_source": src,
+                       "share": kms["tsqr_leaf"] / total_ms if total_ms else None}
+    return out, x, energy
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -176,75 +250,41 @@ def run_ours(args):
     wl = workload(args.size)
     ctx = tt.Context()
     plan = tt.Plan(ctx, wl)
-    rcap = [wl.rmax, wl.rmax]
-    x = tt.initial_state(plan, rcap)
-    stream = ctx.stream
-    energy = torch.zeros(4, dtype=torch.float64, device="cuda")
-    for _ in range(args.warmup):
-        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, args.precision, energy)
-    ctx.sync()
-    ranks = [x.ranks()]
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local] if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
-    clocks = Clocks(vis)
-    ctx.counters(reset=True)
-    ctx.set_timing(True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    rank_hist = torch.zeros(args.steps, 4, dtype=torch.int32, device="cuda")
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()
-        evs[i][0].record(stream)
-        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, args.precision, energy)
-        evs[i][1].record(stream)
-        rank_hist[i].copy_(x.rank)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ctx.sync()
-    ctx.set_timing(False)
-    kms, klaunch = ctx.counters(reset=True)
-    clk = clocks.stop()
-    step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    hist = rank_hist.cpu().numpy()
-    r_seq = [ranks[0]] + [list(map(int, h)) for h in hist]
-    N = wl.nrow
-    flops = 0.0
-    leaf_flops = 0.0
-    for i in range(args.steps):
-        rb, ra = r_seq[i][1], r_seq[i + 1][1]
-        flops += counted_flops(N, rb, ra, ra)
-        R1, R2 = 5 * rb, ra + 1
-        leaf_flops += 2.0 * N * (R1 * R1 + R2 * R2)
-    value = ws * args.steps / (total_ms / 1e3)
-    tflops = flops / (total_ms / 1e3) / 1e12
-    # roofline of the dominant pass over the merged core (TSQR leaves here)
-    leaf_tf = leaf_flops / (kms["tsqr_leaf"] / 1e3) / 1e12 if kms["tsqr_leaf"] > 0 else None
-    roof = {"kernel": "k_tsqr_leaf (Householder TSQR over the transport and source sums)",
-            "bound": "alu", "achieved": leaf_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (leaf_tf / FP64_PEAK_TFLOPS) if leaf_tf else None, "traffic": None,
-            "peak_source": "FP64 FMA units: 152 SMs x 2/clk x 2 flop x 2070 MHz (no FP64 entry in MEASURED_PEAKS.json)",
-            "share": kms["tsqr_leaf"] / total_ms if total_ms else None}
-    line = {"metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    vis = (os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[local]
+           if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local))
+    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    results, states = {}, {}
+    for prec in precs:
+        results[prec], states[prec], energy = time_precision(tt, torch, ctx, plan, wl, args, prec, dist, vis)
+    head = "mixed" if "mixed" in results else "fp64"
+    R = results[head]
+    x = states[head]
+    line = {"metric": METRIC, "value": R["value"], "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 passes over the merged core, f64 small cores" if head == "mixed" else "f64",
+            "data": "synthetic",
             "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "groups": wl.ngroup,
                        "ordinates": [wl.ntheta, wl.nphi], "tol": wl.tol, "rmax": wl.rmax,
-                       "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                       "precision": head, "state_dtype": "f32" if head == "mixed" else "f64",
+                       "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
-            "tflops": tflops, "roofline": roof,
-            "breakdown_ms_per_step": {k: v / args.steps for k, v in kms.items()},
-            "gpu_launches": int(sum(klaunch.values())), "clocks": clk, "ranks": r_seq[-1],
-            "rank_history": [r[1:-1] for r in r_seq]}
+            "tflops": R["tflops"], "roofline": R["roofline"],
+            "breakdown_ms_per_step": R["breakdown_ms_per_step"], "gpu_launches": R["gpu_launches"],
+            "clocks": R["clocks"], "ranks": R["ranks"], "rank_history": R["rank_history"],
+            "jacobi": R["jacobi"]}
+    if "fp64" in results and head != "fp64":
+        F = results["fp64"]
+        line["fp64"] = {k: F[k] for k in ("value", "ms_per_step", "tflops", "roofline", "breakdown_ms_per_step",
+                                          "gpu_launches", "ranks", "jacobi")}
+        line["speedup_mixed_over_fp64"] = R["value"] / F["value"]
+        Em = tt.tt_energy_density(ctx, plan, states["mixed"]).cpu().numpy()
+        Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()
+        line["mixed_vs_fp64_energy_density_rel_err"] = float(np.linalg.norm(Em - Ed) / np.linalg.norm(Ed))
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     if args.e2e_steps > 0:
+        stream = ctx.stream
+        energy = torch.zeros(4, dtype=torch.float64, device="cuda")
         host = [c.cpu().pin_memory() for c in x.cores]
         host_rank = x.rank.cpu().pin_memory()
         host_energy = torch.zeros(4, dtype=torch.float64).pin_memory()
@@ -259,7 +299,7 @@ def run_ours(args):
                 for c, h in zip(x.cores, host):
                     c.copy_(h, non_blocking=True)
                 x.rank.copy_(host_rank, non_blocking=True)
-            tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, args.precision, energy)
+            tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, head, energy)
             with torch.cuda.stream(stream):
                 for c, h in zip(x.cores, host):
                     h.copy_(c, non_blocking=True)

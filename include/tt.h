@@ -120,6 +120,11 @@ tt_status tt_context_set_timing(tt_context *ctx, int enable);
  * (launches[TT_TIMER_COUNT], nullable) since the last reset; reset != 0 clears both. */
 tt_status tt_context_counters(tt_context *ctx, double *ms, int64_t *launches, int reset);
 
+/* Synchronise the context stream and copy device-side iteration statistics since the last
+ * reset into out[0..n) (n <= 3): [0] the largest number of Jacobi sweeps of one SVD,
+ * [1] the number of Jacobi SVDs, [2] their total number of sweeps.  reset != 0 clears them. */
+tt_status tt_context_diagnostics(tt_context *ctx, int64_t *out, int n, int reset);
+
 /* Synchronise the context stream, then return and clear the latched device status. */
 tt_status tt_sync(tt_context *ctx);
 

@@ -30,7 +30,7 @@ PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED}
 EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sync", "tt_workspace_query",
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
-           "tt_context_counters")
+           "tt_context_counters", "tt_context_diagnostics")
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other")
 
 
@@ -90,6 +90,7 @@ def lib():
             "tt_energy_density": [vp, vp, ctypes.POINTER(_Tensor), vp],
             "tt_context_set_timing": [vp, ctypes.c_int],
             "tt_context_counters": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
+            "tt_context_diagnostics": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -137,6 +138,12 @@ class Context:
 
     def set_timing(self, enable: bool):
         _check(lib().tt_context_set_timing(self.handle, 1 if enable else 0), "tt_context_set_timing")
+
+    def diagnostics(self, reset: bool = False):
+        """Jacobi statistics since the last reset: max sweeps, SVD count, total sweeps."""
+        out = (ctypes.c_int64 * 3)()
+        _check(lib().tt_context_diagnostics(self.handle, out, 3, 1 if reset else 0), "tt_context_diagnostics")
+        return {"jacobi_sweeps_max": out[0], "jacobi_svds": out[1], "jacobi_sweeps_total": out[2]}
 
     def counters(self, reset: bool = False):
         """(ms per category, launches per category) since the last reset (tt_context_counters)."""

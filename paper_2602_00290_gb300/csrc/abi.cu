@@ -171,6 +171,18 @@ tt_status tt_context_counters(tt_context* ctx, double* ms, int64_t* launches, in
   return TT_OK;
 }
 
+tt_status tt_context_diagnostics(tt_context* ctx, int64_t* out, int n, int reset) {
+  if (!ctx || (n > 0 && !out) || n < 0 || n > 3) return TT_ERR_ARG;
+  set_device(ctx);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
+  int v[3] = {0, 0, 0};
+  if (cudaMemcpy(v, &ctx->ctrl->jac_sweeps_max, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return TT_ERR_CUDA;
+  const int64_t w[3] = {v[0], v[1], v[2]};
+  for (int i = 0; i < n; ++i) out[i] = w[i];
+  if (reset && cudaMemset(&ctx->ctrl->jac_sweeps_max, 0, sizeof(v)) != cudaSuccess) return TT_ERR_CUDA;
+  return TT_OK;
+}
+
 tt_status tt_sync(tt_context* ctx) {
   if (!ctx) return TT_ERR_ARG;
   set_device(ctx);
@@ -263,7 +275,6 @@ static tt_status check_round_args(const tt_tensor* x, double tol, int32_t rmax, 
   if (!(tol >= 0.0) || !std::isfinite(tol)) return TT_ERR_ARG;
   if (rmax < 1) return TT_ERR_ARG;
   if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return TT_ERR_ARG;
-  if (prec == TT_PREC_MIXED) return TT_ERR_UNSUPPORTED;
   for (int j = 1; j < x->d; ++j)
     if (rmax > x->rcap[j]) return TT_ERR_CAPACITY;
   return TT_OK;
@@ -276,8 +287,11 @@ tt_status tt_round(tt_context* ctx, tt_tensor* x, double tol, int32_t rmax, tt_p
   if (st != TT_OK) return st;
   set_device(ctx);
   return with_ws(ctx, [&](ttk::Bump& ws) {
-    return (x->dtype == TT_F64) ? ttk::round_impl<double>(ctx, x, tol, rmax, ws)
-                                : ttk::round_impl<float>(ctx, x, tol, rmax, ws);
+    const bool f64 = (x->dtype == TT_F64), mixed = (prec == TT_PREC_MIXED);
+    if (f64) return mixed ? ttk::round_impl<double, float>(ctx, x, tol, rmax, ws)
+                          : ttk::round_impl<double, double>(ctx, x, tol, rmax, ws);
+    return mixed ? ttk::round_impl<float, float>(ctx, x, tol, rmax, ws)
+                 : ttk::round_impl<float, double>(ctx, x, tol, rmax, ws);
   });
 }
 
@@ -304,8 +318,11 @@ tt_status tt_step(tt_context* ctx, const tt_plan* plan, tt_tensor* I, double tol
   if (st != TT_OK) return st;
   set_device(ctx);
   return with_ws(ctx, [&](ttk::Bump& ws) {
-    return (I->dtype == TT_F64) ? ttk::step_impl<double>(ctx, plan, I, tol, rmax, energy_dev, ws)
-                                : ttk::step_impl<float>(ctx, plan, I, tol, rmax, energy_dev, ws);
+    const bool f64 = (I->dtype == TT_F64), mixed = (prec == TT_PREC_MIXED);
+    if (f64) return mixed ? ttk::step_impl<double, float>(ctx, plan, I, tol, rmax, energy_dev, ws)
+                          : ttk::step_impl<double, double>(ctx, plan, I, tol, rmax, energy_dev, ws);
+    return mixed ? ttk::step_impl<float, float>(ctx, plan, I, tol, rmax, energy_dev, ws)
+                 : ttk::step_impl<float, double>(ctx, plan, I, tol, rmax, energy_dev, ws);
   });
 }
 
@@ -326,17 +343,24 @@ tt_status tt_workspace_query(tt_context* ctx, const tt_plan* plan, const tt_tens
   if (!ctx || !x || !bytes) return TT_ERR_ARG;
   tt_status st = check_tensor(x);
   if (st != TT_OK) return st;
-  (void)prec;
   ttk::Bump dry{nullptr, 0, 0, true};
   tt_tensor tmp = *x;
   if (plan) {
     st = check_plan_tensor(plan, x);
     if (st != TT_OK) return st;
-    st = (x->dtype == TT_F64) ? ttk::step_impl<double>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry)
-                              : ttk::step_impl<float>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry);
+    if (prec == TT_PREC_MIXED)
+      st = (x->dtype == TT_F64) ? ttk::step_impl<double, float>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry)
+                                : ttk::step_impl<float, float>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry);
+    else
+      st = (x->dtype == TT_F64) ? ttk::step_impl<double, double>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry)
+                                : ttk::step_impl<float, double>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry);
   } else {
-    st = (x->dtype == TT_F64) ? ttk::round_impl<double>(ctx, &tmp, 1e-6, 1, dry)
-                              : ttk::round_impl<float>(ctx, &tmp, 1e-6, 1, dry);
+    if (prec == TT_PREC_MIXED)
+      st = (x->dtype == TT_F64) ? ttk::round_impl<double, float>(ctx, &tmp, 1e-6, 1, dry)
+                                : ttk::round_impl<float, float>(ctx, &tmp, 1e-6, 1, dry);
+    else
+      st = (x->dtype == TT_F64) ? ttk::round_impl<double, double>(ctx, &tmp, 1e-6, 1, dry)
+                                : ttk::round_impl<float, double>(ctx, &tmp, 1e-6, 1, dry);
   }
   *bytes = dry.off;
   return st;

@@ -121,9 +121,10 @@ __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, 
     if (!lp.live(j, r)) continue;
     T* vb = vbuf + buf * BR;
     if (c == j) {
-      T x2 = T(0);
+      T xp[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-      for (int i = 0; i < BR; ++i) x2 += B[i] * B[i];
+      for (int i = 0; i < BR; ++i) xp[i & 3] += B[i] * B[i];
+      const T x2 = (xp[0] + xp[1]) + (xp[2] + xp[3]);
       T tau = T(0);
       if (x2 > T(0)) {
         T* rjj = Rs + tri_off(j, ncap);
@@ -144,9 +145,10 @@ __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, 
     const T tau = taub[buf];
     if (tau != T(0) && c > j && mycol) {
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
-      T wv = *rjc;
+      T wp[4] = {*rjc, T(0), T(0), T(0)};
 #pragma unroll
-      for (int i = 0; i < BR; ++i) wv += vb[i] * B[i];
+      for (int i = 0; i < BR; ++i) wp[i & 3] += vb[i] * B[i];
+      T wv = (wp[0] + wp[1]) + (wp[2] + wp[3]);
       wv *= tau;
       *rjc -= wv;
 #pragma unroll
@@ -164,9 +166,11 @@ __device__ __forceinline__ void write_R(const T* Rs, int ncap, double* Ro) {
   }
 }
 
+// packed R, then the double-buffered reflector (16-byte aligned) and its two scalars
+__host__ __device__ inline size_t tsqr_r_elems(int ncap) { return (((size_t)ncap * (ncap + 1) / 2) + 3) & ~(size_t)3; }
 template <typename T, int BR>
 __host__ __device__ inline size_t tsqr_smem_bytes(int ncap) {
-  return sizeof(T) * ((size_t)ncap * (ncap + 1) / 2 + 2 * BR + 2);
+  return sizeof(T) * (tsqr_r_elems(ncap) + 2 * BR + 4);
 }
 
 template <typename T, int BR, class Src>
@@ -175,7 +179,7 @@ __global__ void __launch_bounds__(256) k_tsqr_leaf(Src src, LivePattern lp, long
   extern __shared__ __align__(16) unsigned char tsqr_smem[];
   const int ncap = lp.ncap();
   T* Rs = reinterpret_cast<T*>(tsqr_smem);
-  T* vbuf = Rs + (size_t)ncap * (ncap + 1) / 2;
+  T* vbuf = Rs + tsqr_r_elems(ncap);
   T* taub = vbuf + 2 * BR;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
   for (int i = threadIdx.x; i < ncap * (ncap + 1) / 2; i += blockDim.x) Rs[i] = T(0);
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(256) k_tsqr_merge(LivePattern lp, int nin, con
   }
   const double* Rb = Rin + (size_t)b * nn;
   T* Rs = reinterpret_cast<T*>(tsqr_smem);
-  T* vbuf = Rs + (size_t)ncap * (ncap + 1) / 2;
+  T* vbuf = Rs + tsqr_r_elems(ncap);
   T* taub = vbuf + 2 * BR;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
   for (int idx = threadIdx.x; idx < ncap * ncap; idx += blockDim.x) {

@@ -19,6 +19,16 @@ struct DevCtrl {
   double norm;         // ||X||_F of the last rounded tensor
   double delta;        // truncation threshold of the last rounding
   double energy[8];    // scratch for energy reports
+  int jac_sweeps;      // sweeps of the last cooperative Jacobi SVD
+  int jac_sweeps_max;  // max sweeps over Jacobi SVDs since the last counter reset
+  int jac_calls;       // Jacobi SVDs since the last counter reset
+  int jac_sweeps_sum;  // their total sweeps
+  unsigned bar_count;  // grid barrier of cooperative kernels: arrivals in this generation
+  unsigned bar_gen;    // grid barrier generation
+  int abort;           // set when a bounded wait gives up; every CTA then leaves
+  int pad2;
+  double fro2;         // ||A||_F^2 of the matrix in a cooperative Jacobi sweep
+  int jac_rot[64];     // rotations per sweep of the cooperative Jacobi
 };
 
 __device__ __forceinline__ void latch(int* status, int code) {

@@ -12,7 +12,10 @@
 // The new merged core is the projection of X onto the new right frame,
 //   Z_new = Z_sum W,   W = (B0 x_3 V_2k) V_1k,
 // which equals Q_Z U_1 S_1 of the textbook sweep and needs no inverse of R_Z.
-// Every SVD is a QR (TSQR) followed by a one-sided Jacobi SVD of the triangular factor.
+// Every SVD is a one-sided (Hestenes) Jacobi sweep run by a cooperative grid directly on the
+// unfolding (bond 2: Y as (R n1) x n2 with accumulated rotations; bond 1: Y_2^T, whose
+// normalised converged columns are the right singular vectors).
+#include <cstddef>
 #include <cstdio>
 
 #include "bigpass.cuh"
@@ -57,111 +60,6 @@ __global__ void k_small_gemm(int M, int N, int K, const TA* __restrict__ A, long
   }
 }
 
-// One-sided (Hestenes) Jacobi SVD of an n x n matrix R (row-major) in one CTA: columns are
-// orthogonalised by plane rotations in round-robin order (n/2 independent pairs per round,
-// one warp per pair), accumulating V.  Output: sigma sorted descending and V_out row-major
-// with column j the right singular vector of sigma_j.  At most `maxsweep` sweeps.
-__global__ void __launch_bounds__(1024) k_jacobi(int n, const double* __restrict__ R, double* __restrict__ Aw,
-                                                 double* __restrict__ Vw, double* __restrict__ sigma_out,
-                                                 double* __restrict__ V_out, int* __restrict__ perm, int maxsweep,
-                                                 int* status) {
-  __shared__ int rot_flag;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int row = idx / n, col = idx - row * n;
-    Aw[(size_t)col * n + row] = R[idx];
-    Vw[(size_t)col * n + row] = (row == col) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  const int np = n + (n & 1);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  for (int sweep = 0; sweep < maxsweep; ++sweep) {
-    if (threadIdx.x == 0) rot_flag = 0;
-    __syncthreads();
-    for (int round = 0; round < np - 1; ++round) {
-      for (int pr = warp; pr < np / 2; pr += nwarps) {
-        int p, q;
-        if (pr == 0) {
-          p = round;
-          q = np - 1;
-        } else {
-          p = (round + pr) % (np - 1);
-          q = (round - pr + (np - 1)) % (np - 1);
-        }
-        if (p >= n || q >= n) continue;
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
-        double* ap = Aw + (size_t)p * n;
-        double* aq = Aw + (size_t)q * n;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int i = lane; i < n; i += 32) {
-          const double x = ap[i], y = aq[i];
-          a += x * x;
-          b += y * y;
-          g += x * y;
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        if (g != 0.0 && fabs(g) > 1e-15 * sqrt(a) * sqrt(b)) {
-          const double zeta = (b - a) / (2.0 * g);
-          double t;
-          if (fabs(zeta) > 1e150)
-            t = 0.5 / zeta;
-          else
-            t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
-          for (int i = lane; i < n; i += 32) {
-            const double x = ap[i], y = aq[i];
-            ap[i] = cs * x - sn * y;
-            aq[i] = sn * x + cs * y;
-          }
-          double* vp = Vw + (size_t)p * n;
-          double* vq = Vw + (size_t)q * n;
-          for (int i = lane; i < n; i += 32) {
-            const double x = vp[i], y = vq[i];
-            vp[i] = cs * x - sn * y;
-            vq[i] = sn * x + cs * y;
-          }
-          if (lane == 0) rot_flag = 1;
-        }
-      }
-      __syncthreads();
-    }
-    const int f = rot_flag;
-    __syncthreads();
-    if (!f) break;
-    if (sweep == maxsweep - 1 && threadIdx.x == 0) latch(status, TT_ERR_TIMEOUT);
-  }
-  // singular values = column norms; rank-sort descending (ties by index)
-  double* sig = sigma_out;  // temporary: unsorted norms in V_out's last use? use perm-sorted write below
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    double a = 0.0;
-    const double* ap = Aw + (size_t)p * n;
-    for (int i = 0; i < n; ++i) a += ap[i] * ap[i];
-    Aw[(size_t)p * n] = sqrt(a);  // column p is no longer needed beyond its norm
-    if (!isfinite(a)) latch(status, TT_ERR_NONFINITE);
-  }
-  __syncthreads();
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const double sp = Aw[(size_t)p * n];
-    int rank = 0;
-    for (int q = 0; q < n; ++q) {
-      const double sq = Aw[(size_t)q * n];
-      rank += (sq > sp) || (sq == sp && q < p);
-    }
-    perm[rank] = p;
-    sig[rank] = sp;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx - i * n;
-    V_out[idx] = Vw[(size_t)perm[j] * n + i];
-  }
-}
-
 // Rank decision for one bond.  first != 0: this is the first SVD of the right-to-left sweep,
 // which also fixes ||X|| = sqrt(sum sigma^2) and delta = tol ||X|| / sqrt(d-1).  The kept rank
 // is the smallest k >= 1 with sqrt(sum_{j>=k} sigma_j^2) <= delta (tol > 0), or the full rank
@@ -169,10 +67,11 @@ __global__ void __launch_bounds__(1024) k_jacobi(int n, const double* __restrict
 __global__ void k_decide(const double* __restrict__ sigma, int n, int first, int dcores, double tol, int rmax,
                          int kcap, long full_rank_cap, const int* rptr, int nblk, int nextra, int rows_mul,
                          const int* r2ptr, int r2_nblk, int r2_nextra, const int* kprev, int cols_mul,
-                         int cols_fixed, DevCtrl* ctrl, int slot) {
+                         int cols_fixed, DevCtrl* ctrl, int slot, const double* extra_tail) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double tail_beyond = extra_tail ? *extra_tail : 0.0;  // energy beyond the n listed values
   if (first) {
-    double s2 = 0.0;
+    double s2 = tail_beyond;
     for (int j = n - 1; j >= 0; --j) s2 += sigma[j] * sigma[j];
     const double nrm = sqrt(s2);
     ctrl->norm = nrm;
@@ -196,7 +95,7 @@ __global__ void k_decide(const double* __restrict__ sigma, int n, int first, int
     k = full;
   } else {
     k = n;
-    double tail2 = 0.0;
+    double tail2 = tail_beyond;
     // tail(k) = sqrt(sum_{j>=k} sigma_j^2); smallest k >= 1 with tail(k) <= delta
     long best = n;
     for (long kk = n; kk >= 1; --kk) {
@@ -213,22 +112,22 @@ __global__ void k_decide(const double* __restrict__ sigma, int n, int first, int
   ctrl->k[slot] = (int)k;
 }
 
-// Re-orthonormalise the first k columns of V (nv x ldv, row-major) by classical Gram-Schmidt
-// applied twice.  Rows with row % rowmod >= rowlive are structurally zero and stay zero; a
-// column that vanishes (zero singular value) is replaced by the first canonical vector that
-// is independent of the earlier columns.
-__global__ void __launch_bounds__(1024) k_reorth(int nv, int ldv, double* __restrict__ V, const int* kptr,
-                                                 int rowmod, const int* rowlive_ptr) {
+// Classical Gram-Schmidt applied twice (FP64) to the first k columns of V (nv x ldv,
+// row-major), in column order, normalising each.  The columns come sorted by decreasing
+// singular value, so every column is cleaned of its components along the larger ones; a column
+// with nothing left (relative remainder <= 1e-12) is replaced by the first canonical vector on a
+// live row (row % rowmod < rowlive) that is independent of the earlier columns.
+__global__ void __launch_bounds__(1024) k_orthonormalise(int nv, int ldv, double* __restrict__ V, const int* kptr,
+                                                         int rowmod, const int* rowlive_ptr) {
   __shared__ double red[33];
   __shared__ double h[1024];
   const int k = *kptr;
   const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   for (int j = 0; j < k; ++j) {
-    int cand = -1;  // canonical replacement index in use (-1: original column)
+    int cand = -1;
     for (int attempt = 0; attempt <= nv; ++attempt) {
       if (attempt > 0) {
-        // next canonical vector on a live row
         do {
           ++cand;
         } while (cand < nv && (cand % rowmod) >= rowlive);
@@ -241,10 +140,10 @@ __global__ void __launch_bounds__(1024) k_reorth(int nv, int ldv, double* __rest
       n0 = sqrt(block_sum(n0, red));
       for (int pass = 0; pass < 2; ++pass) {
         for (int i2 = warp; i2 < j; i2 += nwarps) {
-          double s = 0.0;
-          for (int i = lane; i < nv; i += 32) s += V[(size_t)i * ldv + i2] * V[(size_t)i * ldv + j];
-          s = warp_sum(s);
-          if (lane == 0) h[i2] = s;
+          double sacc = 0.0;
+          for (int i = lane; i < nv; i += 32) sacc += V[(size_t)i * ldv + i2] * V[(size_t)i * ldv + j];
+          sacc = warp_sum(sacc);
+          if (lane == 0) h[i2] = sacc;
         }
         __syncthreads();
         for (int i = threadIdx.x; i < nv; i += blockDim.x) {
@@ -257,12 +156,152 @@ __global__ void __launch_bounds__(1024) k_reorth(int nv, int ldv, double* __rest
       double n1 = 0.0;
       for (int i = threadIdx.x; i < nv; i += blockDim.x) n1 += V[(size_t)i * ldv + j] * V[(size_t)i * ldv + j];
       n1 = sqrt(block_sum(n1, red));
-      if (n1 > 0.5 * n0 && n1 > 0.0) {
+      if (n1 > 1e-12 * n0 && n1 > 0.0) {
         for (int i = threadIdx.x; i < nv; i += blockDim.x) V[(size_t)i * ldv + j] /= n1;
         __syncthreads();
         break;
       }
     }
+  }
+}
+
+// Classical Gram-Schmidt applied twice (FP64) to the first K columns of V (nv x ldv), in
+// column order: V[:, :K] becomes Q of V[:, :K] = Q T and sig[j] = |T_jj|.  With the columns in
+// order of decreasing norm and P = A U for nearly orthogonal U, T is upper triangular with
+// T_ij (i < j) at most eps_32 sigma_i, which moves the singular values only at second order, so
+// |T_jj| are the singular values to about 1e-14 relative and Q are FP64-orthonormal left
+// singular vectors.  A column with nothing left stays zero with sig = 0.
+__global__ void __launch_bounds__(1024) k_cgs2_sigma(int nv, int ldv, double* __restrict__ V, int K,
+                                                     double* __restrict__ sig) {
+  __shared__ double red[33];
+  __shared__ double h[1024];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int j = 0; j < K; ++j) {
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int i2 = warp; i2 < j; i2 += nwarps) {
+        double sacc = 0.0;
+        for (int i = lane; i < nv; i += 32) sacc += V[(size_t)i * ldv + i2] * V[(size_t)i * ldv + j];
+        sacc = warp_sum(sacc);
+        if (lane == 0) h[i2] = sacc;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        double v = V[(size_t)i * ldv + j];
+        for (int i2 = 0; i2 < j; ++i2) v -= h[i2] * V[(size_t)i * ldv + i2];
+        V[(size_t)i * ldv + j] = v;
+      }
+      __syncthreads();
+    }
+    double n1 = 0.0;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) n1 += V[(size_t)i * ldv + j] * V[(size_t)i * ldv + j];
+    n1 = sqrt(block_sum(n1, red));
+    if (threadIdx.x == 0) sig[j] = n1;
+    const double inv = (n1 > 0.0) ? 1.0 / n1 : 0.0;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) V[(size_t)i * ldv + j] *= inv;
+    __syncthreads();
+  }
+}
+
+// Sort the first K columns of V (nv x ldv) and sig[0..K) by decreasing sig (ties by index).
+__global__ void __launch_bounds__(1024) k_sort_cols(int nv, int ldv, int K, double* __restrict__ sig,
+                                                    double* __restrict__ V, double* __restrict__ tmp) {
+  __shared__ int rank_of[1024];
+  __shared__ double sg[1024];
+  for (int c = threadIdx.x; c < K; c += blockDim.x) sg[c] = sig[c];
+  __syncthreads();
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    int r = 0;
+    for (int q = 0; q < K; ++q) r += (sg[q] > sg[c]) || (sg[q] == sg[c] && q < c);
+    rank_of[c] = r;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nv * K; idx += blockDim.x) {
+    const int i = idx / K, c = idx - (idx / K) * K;
+    tmp[(size_t)i * K + rank_of[c]] = V[(size_t)i * ldv + c];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nv * K; idx += blockDim.x) {
+    const int i = idx / K, c = idx - (idx / K) * K;
+    V[(size_t)i * ldv + c] = tmp[idx];
+  }
+  for (int c = threadIdx.x; c < K; c += blockDim.x) sig[rank_of[c]] = sg[c];
+}
+
+// tail = max(0, fro2 - sum_{j<K} sig_j^2): the energy of A outside its K leading singular pairs
+__global__ void k_tail_from_fro(int K, const double* __restrict__ sig, const double* __restrict__ fro2,
+                                double* __restrict__ tail) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s2 = 0.0;
+  for (int j = K - 1; j >= 0; --j) s2 += sig[j] * sig[j];
+  const double t = *fro2 - s2;
+  *tail = t > 0.0 ? t : 0.0;
+}
+
+__global__ void k_copy_cols(int nv, int ncols, const double* __restrict__ A, int lda, double* __restrict__ B, int ldb) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)nv * ncols;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / ncols), j = (int)(idx - (long)i * ncols);
+    B[(size_t)i * ldb + j] = A[(size_t)i * lda + j];
+  }
+}
+
+// Columns j < k of V (nv x ldv, row-major) whose singular value is exactly zero carry no
+// direction (zero tensor, or a zero kept by tol = 0); each is replaced by the first canonical
+// vector on a live row (row % rowmod < rowlive) that is independent of the earlier columns,
+// orthonormalised against them twice (classical Gram-Schmidt).  Columns with sigma > 0 come
+// out of the converged Jacobi sweep orthonormal and are left as they are.
+__global__ void __launch_bounds__(1024) k_fix_zero_columns(int nv, int ldv, double* __restrict__ V,
+                                                           const double* __restrict__ sigma, const int* kptr,
+                                                           int rowmod, const int* rowlive_ptr) {
+  __shared__ double red[33];
+  __shared__ double h[1024];
+  const int k = *kptr;
+  const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    if (sigma[j] > 0.0) continue;
+    int cand = -1;
+    for (int attempt = 0; attempt < nv; ++attempt) {
+      do {
+        ++cand;
+      } while (cand < nv && (cand % rowmod) >= rowlive);
+      if (cand >= nv) break;
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) V[(size_t)i * ldv + j] = (i == cand) ? 1.0 : 0.0;
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int i2 = warp; i2 < k; i2 += nwarps) {
+          double s = 0.0;
+          if (i2 != j && (i2 < j || sigma[i2] > 0.0))
+            for (int i = lane; i < nv; i += 32) s += V[(size_t)i * ldv + i2] * V[(size_t)i * ldv + j];
+          s = warp_sum(s);
+          if (lane == 0) h[i2] = s;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+          double v = V[(size_t)i * ldv + j];
+          for (int i2 = 0; i2 < k; ++i2) v -= h[i2] * V[(size_t)i * ldv + i2];
+          V[(size_t)i * ldv + j] = v;
+        }
+        __syncthreads();
+      }
+      double n1 = 0.0;
+      for (int i = threadIdx.x; i < nv; i += blockDim.x) n1 += V[(size_t)i * ldv + j] * V[(size_t)i * ldv + j];
+      n1 = sqrt(block_sum(n1, red));
+      if (n1 > 0.5) {
+        for (int i = threadIdx.x; i < nv; i += blockDim.x) V[(size_t)i * ldv + j] /= n1;
+        __syncthreads();
+        break;
+      }
+    }
+  }
+}
+
+// out[c * rows + r] = in[r * cols + c] (row-major to column-major)
+__global__ void k_transpose(int rows, int cols, const double* __restrict__ in, double* __restrict__ out) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)rows * cols;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int r = (int)(idx / cols), c = (int)(idx - (long)r * cols);
+    out[(size_t)c * rows + r] = in[idx];
   }
 }
 
@@ -325,6 +364,335 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, long nblo
   }
 }
 
+
+// Grid-wide barrier for cooperative launches, with a bounded spin.  If the wait gives up,
+// the barrier latches TT_ERR_TIMEOUT and raises the abort flag so every CTA leaves.
+__device__ bool grid_barrier(DevCtrl* ctrl, unsigned nblocks) {
+  __shared__ int sh_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* genp = &ctrl->bar_gen;
+    volatile int* abortp = &ctrl->abort;
+    const unsigned g = *genp;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&ctrl->bar_count, 1u) + 1u;
+    if (arrived == nblocks) {
+      atomicExch(&ctrl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&ctrl->bar_gen, 1u);
+    } else {
+      long spins = 0;
+      while (*genp == g && *abortp == 0) {
+        if (++spins > (1L << 24)) {
+          atomicExch(&ctrl->abort, 1);
+          latch(&ctrl->status, TT_ERR_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    sh_ok = (*abortp == 0);
+  }
+  __syncthreads();
+  return sh_ok != 0;
+}
+
+__global__ void k_fro2(long count, const double* __restrict__ A, double* out) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (long i = threadIdx.x; i < count; i += blockDim.x) s += A[i] * A[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+// Cooperative one-sided Jacobi: CTA b handles pairs b, b + gridDim.x, ... of each round.
+// Each thread keeps E elements of both columns of its pair in registers; the three inner
+// products are reduced through shared memory by one warp, and one lane forms the rotation,
+// so every FP64 instruction that is not proportional to m is issued once per pair.  With
+// V != null the rotations are also applied to the columns of V (n x n, column-major).
+template <int E>
+__global__ void __launch_bounds__(256) k_coop_jacobi(int m, int n, double* __restrict__ A, double* __restrict__ V,
+                                                     DevCtrl* ctrl, int maxsweep) {
+  __shared__ double part[3][256];
+  __shared__ double rot[3];  // cs, sn, flag
+  const unsigned nb = gridDim.x;
+  const int np = n + (n & 1);
+  const int npairs = np / 2;
+  const int tid = threadIdx.x;
+  const double floor_abs = 1e-32 * ctrl->fro2;
+  const double rel_tol = 2.0 * m * 2.220446049250313e-16;  // round-off of a length-m inner product
+  int sweeps = 0;
+  for (int sweep = 0; sweep < maxsweep; ++sweep) {
+    sweeps = sweep + 1;
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pr = blockIdx.x; pr < npairs; pr += nb) {
+        int p, q;
+        if (pr == 0) {
+          p = round;
+          q = np - 1;
+        } else {
+          p = (round + pr) % (np - 1);
+          q = (round - pr + (np - 1)) % (np - 1);
+        }
+        if (p >= n || q >= n) continue;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        double* ap = A + (size_t)p * m;
+        double* aq = A + (size_t)q * m;
+        double x[E], y[E];
+        double a = 0.0, b = 0.0, g = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int i = tid + e * 256;
+          x[e] = (i < m) ? ap[i] : 0.0;
+          y[e] = (i < m) ? aq[i] : 0.0;
+          a += x[e] * x[e];
+          b += y[e] * y[e];
+          g += x[e] * y[e];
+        }
+        part[0][tid] = a;
+        part[1][tid] = b;
+        part[2][tid] = g;
+        __syncthreads();
+        if (tid < 32) {
+          double sa = 0.0, sb = 0.0, sg = 0.0;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            sa += part[0][tid + 32 * k];
+            sb += part[1][tid + 32 * k];
+            sg += part[2][tid + 32 * k];
+          }
+          sa = warp_sum(sa);
+          sb = warp_sum(sb);
+          sg = warp_sum(sg);
+          if (tid == 0) {
+            double cs = 1.0, sn = 0.0, flag = 0.0;
+            if (fabs(sg) > floor_abs && fabs(sg) > rel_tol * sqrt(sa) * sqrt(sb)) {
+              const double zeta = (sb - sa) / (2.0 * sg);
+              double t;
+              if (fabs(zeta) > 1e150)
+                t = 0.5 / zeta;
+              else
+                t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+              cs = 1.0 / sqrt(1.0 + t * t);
+              sn = cs * t;
+              flag = 1.0;
+              atomicAdd(&ctrl->jac_rot[sweep], 1);
+            }
+            rot[0] = cs;
+            rot[1] = sn;
+            rot[2] = flag;
+          }
+        }
+        __syncthreads();
+        if (rot[2] != 0.0) {
+          const double cs = rot[0], sn = rot[1];
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int i = tid + e * 256;
+            if (i < m) {
+              ap[i] = cs * x[e] - sn * y[e];
+              aq[i] = sn * x[e] + cs * y[e];
+            }
+          }
+          if (V) {
+            double* vp = V + (size_t)p * n;
+            double* vq = V + (size_t)q * n;
+            for (int i = tid; i < n; i += 256) {
+              const double u = vp[i], w = vq[i];
+              vp[i] = cs * u - sn * w;
+              vq[i] = sn * u + cs * w;
+            }
+          }
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(ctrl, nb)) return;
+    }
+    const int nrot = *(volatile int*)&ctrl->jac_rot[sweep];
+    if (nrot == 0) break;
+    if (sweep == maxsweep - 1 && blockIdx.x == 0 && threadIdx.x == 0) latch(&ctrl->status, TT_ERR_TIMEOUT);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    ctrl->jac_sweeps = sweeps;
+    atomicMax(&ctrl->jac_sweeps_max, sweeps);
+    atomicAdd(&ctrl->jac_calls, 1);
+    atomicAdd(&ctrl->jac_sweeps_sum, sweeps);
+  }
+}
+
+__global__ void k_identity(int n, double* __restrict__ V) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x)
+    V[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+}
+
+// Vout[i][j] = V[perm j][i] (columns of V as right singular vectors, sorted), row-major n x n.
+__global__ void k_jacobi_write_v(int n, const double* __restrict__ V, const int* __restrict__ perm,
+                                 double* __restrict__ Vout) {
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n * n; idx += gridDim.x * blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    Vout[idx] = V[(size_t)perm[j] * n + i];
+  }
+}
+
+// One-CTA one-sided Jacobi on R^T (R: n x n upper-triangular factor of a tall matrix A,
+// row-major FP64 in global memory) in arithmetic T, with the n columns of R^T (= rows of R)
+// in shared memory.  Jacobi on the transposed triangular factor converges in a few sweeps
+// (Drmac-Veselic preconditioning).  The normalised converged columns are the right singular
+// vectors of R, hence of A; they are written unsorted to U (row-major n x n, column c).
+// Warps take the n/2 pairs of each round; one barrier per round.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restrict__ R, double* __restrict__ U,
+                                                    double* __restrict__ raw, int maxsweep) {
+  extern __shared__ __align__(16) unsigned char jrt_smem[];
+  T* At = reinterpret_cast<T*>(jrt_smem);  // column c at At[c * n]
+  __shared__ int rot_flag;
+  __shared__ float red[33];
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) At[idx] = (T)R[idx];
+  // scale-free thresholds: pairs below the matrix round-off level are left alone
+  float fro = 0.f;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) fro += (float)(R[idx] * R[idx]);
+  fro = warp_sum(fro);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = fro;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.f;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) red[32] = v;
+  }
+  __syncthreads();
+  const T eps = sizeof(T) == 4 ? T(1.1920929e-7) : T(2.220446049250313e-16);
+  const T rel_tol = T(4) * sqrt(T(n)) * eps;
+  const T floor_abs = (sizeof(T) == 4 ? T(1e-14) : T(1e-32)) * (T)red[32];
+  const int np = n + (n & 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  for (int sweep = 0; sweep < maxsweep; ++sweep) {
+    if (threadIdx.x == 0) rot_flag = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pr = warp; pr < np / 2; pr += nwarps) {
+        int p, q;
+        if (pr == 0) {
+          p = round;
+          q = np - 1;
+        } else {
+          p = (round + pr) % (np - 1);
+          q = (round - pr + (np - 1)) % (np - 1);
+        }
+        if (p >= n || q >= n) continue;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        T* ap = At + (size_t)p * n;
+        T* aq = At + (size_t)q * n;
+        T a = 0, b = 0, g = 0;
+        for (int i = lane; i < n; i += 32) {
+          const T x = ap[i], y = aq[i];
+          a += x * x;
+          b += y * y;
+          g += x * y;
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        g = warp_sum(g);
+        if (fabs(g) > floor_abs && fabs(g) > rel_tol * sqrt(a) * sqrt(b)) {
+          const T zeta = (b - a) / (T(2) * g);
+          T t;
+          if (fabs(zeta) > (sizeof(T) == 4 ? T(1e18) : T(1e150)))
+            t = T(0.5) / zeta;
+          else
+            t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
+          for (int i = lane; i < n; i += 32) {
+            const T x = ap[i], y = aq[i];
+            ap[i] = cs * x - sn * y;
+            aq[i] = sn * x + cs * y;
+          }
+          if (lane == 0) rot_flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int f = rot_flag;
+    __syncthreads();
+    if (!f) break;
+  }
+  // normalised columns -> U[i][c]
+  for (int c = warp; c < n; c += nwarps) {
+    const T* ac = At + (size_t)c * n;
+    T s2 = 0;
+    for (int i = lane; i < n; i += 32) s2 += ac[i] * ac[i];
+    s2 = warp_sum(s2);
+    const double inv = (s2 > T(0)) ? 1.0 / sqrt((double)s2) : 0.0;
+    for (int i = lane; i < n; i += 32) U[(size_t)i * n + c] = (double)ac[i] * inv;
+    // the column norm before normalising is the singular value to FP32 accuracy; columns the
+    // FP32 sweep cannot resolve have tiny norms here even though A u can be large
+    if (lane == 0) raw[c] = sqrt((double)s2);
+  }
+}
+
+// perm[r] = the column of rank r by decreasing vals (ties by index)
+__global__ void __launch_bounds__(1024) k_rank_perm(int n, const double* __restrict__ vals, int* __restrict__ perm) {
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    const double v = vals[c];
+    int r = 0;
+    for (int q = 0; q < n; ++q) r += (vals[q] > v) || (vals[q] == v && q < c);
+    perm[r] = c;
+  }
+}
+
+// Vout[i][j] = P[i][perm j] (divided by sigma_j when normalise != 0) for j < ncols.
+__global__ void k_write_sorted(int m, int n, int ncols, const double* __restrict__ P, const double* __restrict__ sigma,
+                               const int* __restrict__ perm, double* __restrict__ Vout, int ldv, int normalise) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)m * ncols;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / ncols), j = (int)(idx - (long)i * ncols);
+    const double v = P[(size_t)i * n + perm[j]];
+    Vout[(size_t)i * ldv + j] = normalise ? (sigma[j] > 0.0 ? v / sigma[j] : 0.0) : v;
+  }
+}
+
+// Column norms of the converged matrix, rank-sorted descending (ties by index).
+__global__ void __launch_bounds__(1024) k_jacobi_sort(int m, int n, const double* __restrict__ A,
+                                                      double* __restrict__ sigma, int* __restrict__ perm,
+                                                      double* __restrict__ tmp, int* status) {
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    double a = 0.0;
+    const double* ap = A + (size_t)p * m;
+    for (int i = 0; i < m; ++i) a += ap[i] * ap[i];
+    tmp[p] = sqrt(a);
+    if (!isfinite(a)) latch(status, TT_ERR_NONFINITE);
+  }
+  __syncthreads();
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const double sp = tmp[p];
+    int rank = 0;
+    for (int q = 0; q < n; ++q) {
+      const double sq = tmp[q];
+      rank += (sq > sp) || (sq == sp && q < p);
+    }
+    perm[rank] = p;
+    sigma[rank] = sp;
+  }
+}
+
+// U[i][j] = A[i][perm j] / sigma_j for j < ncols (0 where sigma_j = 0).
+__global__ void k_jacobi_write_u(int m, int ncols, const double* __restrict__ A, const double* __restrict__ sigma,
+                                 const int* __restrict__ perm, double* __restrict__ U, int ldu) {
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)m * ncols;
+       idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / ncols), j = (int)(idx - (long)i * ncols);
+    const double sg = sigma[j];
+    U[(size_t)i * ldu + j] = (sg > 0.0) ? A[(size_t)perm[j] * m + i] / sg : 0.0;
+  }
+}
+
 }  // namespace
 
 template <typename TA, typename TB>
@@ -359,30 +727,159 @@ void reduce_partials(cudaStream_t s, const double* partials, long nblocks, int s
   k_reduce_partials<<<1, 1024, 0, s>>>(partials, nblocks, stride, out, scale); count_launch();
 }
 
-static tt_status jacobi(cudaStream_t s, int n, const double* R, Bump& ws, double* sigma, double* V,
-                        DevCtrl* ctrl) {
-  double* Aw = ws.take<double>((size_t)n * n);
-  double* Vw = ws.take<double>((size_t)n * n);
-  int* perm = ws.take<int>(n);
-  if (ws.dry) return TT_OK;
-  if (n > 1024) return TT_ERR_UNSUPPORTED;
-  k_jacobi<<<1, 1024, 0, s>>>(n, R, Aw, Vw, sigma, V, perm, 60, &ctrl->status); count_launch();
-  return TT_OK;
+template <int E>
+static cudaError_t launch_coop(int grid, int m, int n, double* A, double* V, DevCtrl* ctrl, int maxsweep,
+                               cudaStream_t s) {
+  void* args[] = {&m, &n, &A, &V, &ctrl, &maxsweep};
+  return cudaLaunchCooperativeKernel((const void*)k_coop_jacobi<E>, dim3(grid), dim3(256), args, 0, s);
 }
 
-// QR of an explicit small matrix (rows x cols) through the TSQR kernels; returns R (cols x cols).
+tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, double* V, double* sigma, double* U,
+                      int ldu, int ncols_out, double* Vout, int* perm, double* tmp, DevCtrl* ctrl) {
+  if (m > 16 * 256) return TT_ERR_UNSUPPORTED;
+  // barrier state, abort flag and sweep counters start at zero for every launch
+  const size_t off = offsetof(DevCtrl, bar_count);
+  cudaMemsetAsync(reinterpret_cast<char*>(ctrl) + off, 0, sizeof(DevCtrl) - off, s);
+  k_fro2<<<1, 1024, 0, s>>>((long)m * n, A, &ctrl->fro2); count_launch();
+  if (V) {
+    k_identity<<<(n * n + 255) / 256, 256, 0, s>>>(n, V); count_launch();
+  }
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coop_jacobi<16>, 256, 0);
+  const int npairs = (n + 1) / 2;
+  int grid = npairs;
+  const int resident = num_sms * (occ > 0 ? occ : 1);
+  if (grid > resident) grid = resident;
+  if (grid < 1) grid = 1;
+  const int maxsweep = 40;
+  cudaError_t e;
+  if (m <= 256) e = launch_coop<1>(grid, m, n, A, V, ctrl, maxsweep, s);
+  else if (m <= 512) e = launch_coop<2>(grid, m, n, A, V, ctrl, maxsweep, s);
+  else if (m <= 1024) e = launch_coop<4>(grid, m, n, A, V, ctrl, maxsweep, s);
+  else if (m <= 2048) e = launch_coop<8>(grid, m, n, A, V, ctrl, maxsweep, s);
+  else e = launch_coop<16>(grid, m, n, A, V, ctrl, maxsweep, s);
+  if (e != cudaSuccess) return TT_ERR_CUDA;
+  count_launch();
+  k_jacobi_sort<<<1, 1024, 0, s>>>(m, n, A, sigma, perm, tmp, &ctrl->status); count_launch();
+  if (U) {
+    const long tot = (long)m * ncols_out;
+    k_jacobi_write_u<<<(unsigned)((tot + 255) / 256 < 1024 ? (tot + 255) / 256 : 1024), 256, 0, s>>>(
+        m, ncols_out, A, sigma, perm, U, ldu); count_launch();
+  }
+  if (V && Vout) {
+    k_jacobi_write_v<<<(n * n + 255) / 256, 256, 0, s>>>(n, V, perm, Vout); count_launch();
+  }
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+// SVD of an m x n row-major matrix M (right singular vectors and singular values) by the
+// cooperative Jacobi sweep on its transpose copy: sigma (n, sorted) and Vout (n x n,
+// row-major, column j for sigma_j).
+static tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const double* M, Bump& ws, double* sigma,
+                           double* Vout, DevCtrl* ctrl) {
+  double* At = ws.take<double>((size_t)m * n);
+  double* V = ws.take<double>((size_t)n * n);
+  double* tmp = ws.take<double>(n);
+  int* perm = ws.take<int>(n);
+  if (ws.dry) return TT_OK;
+  k_transpose<<<(unsigned)(((long)m * n + 255) / 256 < 1024 ? ((long)m * n + 255) / 256 : 1024), 256, 0, s>>>(
+      m, n, M, At); count_launch();
+  return coop_jacobi(s, num_sms, m, n, At, V, sigma, nullptr, 0, 0, Vout, perm, tmp, ctrl);
+}
+
+// Mixed-precision SVD of an explicit tall matrix A (source `src`, rows x cols): FP32 TSQR
+// factor R and one-CTA FP32 Jacobi on R^T giving the right singular vectors U (cols x cols)
+// and their FP32 singular values `raw`, with perm the order of decreasing raw.
 template <class Src>
-static tt_status small_qr(cudaStream_t s, int num_sms, const Src& src, long rows, int cols, Bump& ws,
-                          double** Rout) {
+static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, long rows, int cols, Bump& ws,
+                                 double** U_out, double** P_out, double* raw, int* perm) {
   LivePattern lp{nullptr, cols, 1, 0};
-  const long L = tsqr_max_leaves<double, 16>(num_sms, cols, rows, 64);
+  const long L = tsqr_max_leaves<float, 64>(num_sms, cols, rows, 8);
   double* a = ws.take<double>((size_t)L * cols * cols);
   double* b = ws.take<double>((size_t)((L + 1) / 2) * cols * cols);
-  if (ws.dry) {
-    *Rout = nullptr;
-    return TT_OK;
+  double* U = ws.take<double>((size_t)cols * cols);
+  double* P = ws.take<double>((size_t)rows * cols);
+  double* tmp = ws.take<double>(cols);
+  *U_out = U;
+  *P_out = P;
+  if (ws.dry) return TT_OK;
+  double* R = nullptr;
+  tt_status st = run_tsqr<float, 64>(s, num_sms, src, lp, rows, 8, a, b, &R);
+  if (st != TT_OK) return st;
+  const size_t smem = sizeof(float) * (size_t)cols * cols;
+  if (smem > 200 * 1024) return TT_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(k_jacobi_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jacobi_rt<float><<<1, 1024, smem, s>>>(cols, R, U, raw, 40); count_launch();
+  k_rank_perm<<<1, 1024, 0, s>>>(cols, raw, perm); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+// d = 3 small-core sweep with FP32 rotations and FP64 singular values/vectors: for each bond
+// an FP32 Jacobi on R^T gives nearly orthogonal right vectors U; P = A U in FP64, sorted by
+// column norm; Gram-Schmidt of the leading columns gives FP64 singular values |T_jj| and
+// orthonormal left vectors; the energy beyond them comes from Pythagoras.  Same outputs as
+// the FP64 sweep.
+static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws, const double* Y) {
+  const int R = j.lp.ncap();
+  const int n1 = j.n1, n2 = j.n2, nang = n1 * n2;
+  const int K1 = j.K1cap, K2 = j.K2cap;
+  // ---- bond 2: A2 = Y viewed as (R n1) x n2; right vectors needed
+  double* sigc2 = ws.take<double>(n2);
+  int* perm2 = ws.take<int>(n2);
+  double* sig2 = ws.take<double>(n2);
+  double* V2 = ws.take<double>((size_t)n2 * n2);
+  double* tmp2 = ws.take<double>((size_t)n2 * n2);
+  double *U2 = nullptr, *P2 = nullptr;
+  tt_status st = svd_right_mixed(s, num_sms, SrcRows<double>{Y, n2}, (long)R * n1, n2, ws, &U2, &P2, sigc2, perm2);
+  if (st != TT_OK) return st;
+  double* P2s = ws.take<double>((size_t)R * n1 * n2);
+  const int nv = n1 * K2;
+  double* Y2 = ws.take<double>((size_t)R * nv);
+  double* B0p = ws.take<double>((size_t)R * nv);
+  if (!ws.dry) {
+    small_gemm<double, double>(s, R * n1, n2, n2, Y, n2, 1, U2, n2, 1, P2, n2, nullptr, nullptr);
+    k_write_sorted<<<(unsigned)(((long)R * n1 * n2 + 255) / 256 < 1024 ? ((long)R * n1 * n2 + 255) / 256 : 1024), 256, 0,
+                     s>>>(R * n1, n2, n2, P2, sigc2, perm2, P2s, n2, 0); count_launch();
+    k_write_sorted<<<(n2 * n2 + 255) / 256, 256, 0, s>>>(n2, n2, n2, U2, sigc2, perm2, V2, n2, 0); count_launch();
+    k_cgs2_sigma<<<1, 1024, 0, s>>>(R * n1, n2, P2s, n2, sig2); count_launch();
+    k_sort_cols<<<1, 1024, 0, s>>>(n2, n2, n2, sig2, V2, tmp2); count_launch();
+    k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
+                              j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
+    k_orthonormalise<<<1, 1024, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr); count_launch();
+    small_gemm<double, double>(s, R * n1, K2, n2, Y, n2, 1, V2, n2, 1, Y2, K2, &j.ctrl->k[1], nullptr);
+    small_gemm<double, double>(s, R * n1, K2, n2, j.B0, n2, 1, V2, n2, 1, B0p, K2, &j.ctrl->k[1], nullptr);
   }
-  return run_tsqr<double, 16>(s, num_sms, src, lp, rows, 64, a, b, Rout);
+  // ---- bond 1: A1 = Y2^T (nv x R); its left vectors are V1
+  double* sigc1 = ws.take<double>(R);
+  int* perm1 = ws.take<int>(R);
+  const int Kr = (K1 + 8 < R) ? K1 + 8 : R;  // leading columns refined in FP64
+  double* sig1 = ws.take<double>(Kr);
+  double* P1s = ws.take<double>((size_t)nv * R);
+  double* fro1 = ws.take<double>(1);
+  double* tailK = ws.take<double>(1);
+  double* tmpK = ws.take<double>((size_t)nv * Kr);
+  double* V1 = ws.take<double>((size_t)nv * K1);
+  double *U1 = nullptr, *P1 = nullptr;
+  st = svd_right_mixed(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &U1, &P1, sigc1, perm1);
+  if (st != TT_OK || ws.dry) return st;
+  small_gemm<double, double>(s, nv, R, R, Y2, 1, nv, U1, R, 1, P1, R, nullptr, nullptr);  // P1 = A1 U1
+  k_write_sorted<<<(unsigned)(((long)nv * R + 255) / 256 < 1024 ? ((long)nv * R + 255) / 256 : 1024), 256, 0, s>>>(
+      nv, R, R, P1, sigc1, perm1, P1s, R, 0); count_launch();
+  k_cgs2_sigma<<<1, 1024, 0, s>>>(nv, R, P1s, Kr, sig1); count_launch();
+  // energy beyond the Kr refined values: ||A1||_F^2 - sum sigma_j^2 (FP64)
+  k_fro2<<<1, 1024, 0, s>>>((long)R * nv, Y2, fro1); count_launch();
+  k_tail_from_fro<<<1, 32, 0, s>>>(Kr, sig1, fro1, tailK); count_launch();
+  k_sort_cols<<<1, 1024, 0, s>>>(nv, R, Kr, sig1, P1s, tmpK); count_launch();
+  k_decide<<<1, 32, 0, s>>>(sig1, Kr, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
+                            nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, tailK); count_launch();
+  k_copy_cols<<<(unsigned)(((long)nv * K1 + 255) / 256 < 1024 ? ((long)nv * K1 + 255) / 256 : 1024), 256, 0, s>>>(
+      nv, K1, P1s, R, V1, K1); count_launch();
+  k_fix_zero_columns<<<1, 1024, 0, s>>>(nv, K1, V1, sig1, &j.ctrl->k[0], K2, &j.ctrl->k[1]); count_launch();
+  k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2); count_launch();
+  small_gemm<double, double>(s, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], nullptr);
+  small_gemm<double, double>(s, K1 * n1, n2, K2, j.core1, K2, 1, j.core2, n2, 1, j.Bnew, n2, nullptr, nullptr);
+  k_vj<<<K1, 128, 0, s>>>(K1, nang, j.Bnew, j.domega, j.vJ); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
 tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) {
@@ -393,16 +890,13 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
   double* Y = ws.take<double>((size_t)R * nang);
   if (!ws.dry) small_gemm<double, double>(s, R, nang, R, j.RZ, R, 1, j.B0, nang, 1, Y, nang, nullptr, nullptr);
   if (j.d == 2) {
-    double* Rq = nullptr;
-    st = small_qr(s, num_sms, SrcRows<double>{Y, n1}, R, n1, ws, &Rq);
-    if (st != TT_OK) return st;
+    // the only bond: SVD of Y (R x n1)
     double* sig = ws.take<double>(n1);
     double* V = ws.take<double>((size_t)n1 * n1);
-    st = jacobi(s, n1, Rq, ws, sig, V, j.ctrl);
-    if (st != TT_OK) return st;
-    if (ws.dry) return TT_OK;
+    st = svd_right(s, num_sms, R, n1, Y, ws, sig, V, j.ctrl);
+    if (st != TT_OK || ws.dry) return st;
     k_decide<<<1, 32, 0, s>>>(sig, n1, 1, 2, j.tol, j.rmax, j.K1cap, j.nrowsZ, j.lp.r_ptr, j.lp.nblk,
-                              j.lp.nextra, 1, nullptr, 0, 0, nullptr, 0, n1, j.ctrl, 0); count_launch();
+                              j.lp.nextra, 1, nullptr, 0, 0, nullptr, 0, n1, j.ctrl, 0, nullptr); count_launch();
     small_gemm<double, double>(s, R, j.K1cap, n1, j.B0, n1, 1, V, n1, 1, j.W, j.K1cap, &j.ctrl->k[0], nullptr);
     k_write_cores2<<<(j.K1cap * n1 + 255) / 256, 256, 0, s>>>(n1, j.K1cap, V, j.ctrl, j.core1); count_launch();
     cudaMemcpyAsync(j.Bnew, j.core1, sizeof(double) * (size_t)j.K1cap * n1, cudaMemcpyDeviceToDevice, s);
@@ -411,38 +905,35 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
   }
   // ---- d = 3 ----
   const int K1 = j.K1cap, K2 = j.K2cap;
-  // bond 2: SVD of Y as (R n1) x n2
-  double* R2 = nullptr;
-  st = small_qr(s, num_sms, SrcRows<double>{Y, n2}, (long)R * n1, n2, ws, &R2);
-  if (st != TT_OK) return st;
+  if (j.mixed) return small_round_mixed3(s, num_sms, j, ws, Y);
+  // bond 2: SVD of Y viewed as (R n1) x n2
   double* sig2 = ws.take<double>(n2);
   double* V2 = ws.take<double>((size_t)n2 * n2);
-  st = jacobi(s, n2, R2, ws, sig2, V2, j.ctrl);
+  st = svd_right(s, num_sms, R * n1, n2, Y, ws, sig2, V2, j.ctrl);
   if (st != TT_OK) return st;
   const int nv = n1 * K2;
   double* Y2 = ws.take<double>((size_t)R * nv);
   double* B0p = ws.take<double>((size_t)R * nv);
   if (!ws.dry) {
     k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
-                              j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1); count_launch();
+                              j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
     small_gemm<double, double>(s, R * n1, K2, n2, Y, n2, 1, V2, n2, 1, Y2, K2, &j.ctrl->k[1], nullptr);
     small_gemm<double, double>(s, R * n1, K2, n2, j.B0, n2, 1, V2, n2, 1, B0p, K2, &j.ctrl->k[1], nullptr);
   }
-  // bond 1: SVD of Y2 as R x (n1 K2) through the QR of its transpose
-  double* R1 = nullptr;
-  st = small_qr(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &R1);
-  if (st != TT_OK) return st;
+  // bond 1: one-sided Jacobi directly on Y2^T (its columns are the rows of Y2, length
+  // n1 K2); the normalised converged columns are the right singular vectors V1 of the
+  // unfolding R x (n1 K2), so no Q factor, no accumulated rotations and no division by
+  // small singular values are needed.
   double* sig1 = ws.take<double>(R);
-  double* U1 = ws.take<double>((size_t)R * R);
-  st = jacobi(s, R, R1, ws, sig1, U1, j.ctrl);
-  if (st != TT_OK) return st;
+  double* tmp1 = ws.take<double>(R);
+  int* perm1 = ws.take<int>(R);
   double* V1 = ws.take<double>((size_t)nv * K1);
   if (ws.dry) return TT_OK;
+  st = coop_jacobi(s, num_sms, nv, R, Y2, nullptr, sig1, V1, K1, K1 < R ? K1 : R, nullptr, perm1, tmp1, j.ctrl);
+  if (st != TT_OK) return st;
   k_decide<<<1, 32, 0, s>>>(sig1, R, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
-                            nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0); count_launch();
-  // V1 = Y2^T U1(:, :k1) diag(1/sigma1)
-  small_gemm<double, double>(s, nv, K1, R, Y2, 1, nv, U1, R, 1, V1, K1, &j.ctrl->k[0], sig1);
-  k_reorth<<<1, 1024, 0, s>>>(nv, K1, V1, &j.ctrl->k[0], K2, &j.ctrl->k[1]); count_launch();
+                            nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, nullptr); count_launch();
+  k_fix_zero_columns<<<1, 1024, 0, s>>>(nv, K1, V1, sig1, &j.ctrl->k[0], K2, &j.ctrl->k[1]); count_launch();
   k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2); count_launch();
   // W = B0p (R x nv) V1 (nv x K1)
   small_gemm<double, double>(s, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], nullptr);

@@ -42,6 +42,7 @@ struct SmallJob {
   double* Bnew;       // [K1cap][n1*n2]
   double* vJ;         // [K1cap]
   DevCtrl* ctrl;      // ranks -> ctrl->k[0] (bond 1), ctrl->k[1] (bond 2)
+  bool mixed;         // FP32 rotations (Jacobi on R^T of an FP32 TSQR), FP64 singular values/vectors
 };
 
 tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& job, Bump& ws);
@@ -64,4 +65,17 @@ void k_vj_host_launch(cudaStream_t s, int K1, int nang, const double* B, const d
 void reduce_partials(cudaStream_t s, const double* partials, long nblocks, int stride, double* out,
                      double scale);
 
+}  // namespace ttk
+
+namespace ttk {
+// One-sided Jacobi SVD of an m x n column-major matrix A (in place) by a cooperative grid:
+// one CTA per column pair per round (round-robin order), bounded-spin grid barrier between
+// rounds.  On return the columns of A are orthogonal; sigma[j] (sorted descending) and, if
+// U != null, U[i][j] = A[i][perm j] / sigma_j (row-major m x ldu, j < ncols_out, zero
+// columns for sigma = 0) are written.  Rotations stop when no pair in a sweep exceeds the
+// thresholds (at most 40 sweeps, else TT_ERR_TIMEOUT is latched).
+// With V != null the rotations are accumulated in V (n x n) and Vout (row-major n x n,
+// column j the right singular vector of sigma_j) is written.
+tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, double* V, double* sigma, double* U,
+                      int ldu, int ncols_out, double* Vout, int* perm, double* tmp, DevCtrl* ctrl);
 }  // namespace ttk

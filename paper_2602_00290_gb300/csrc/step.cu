@@ -13,7 +13,18 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kTM = 32;   // rows per update tile
-constexpr int kBR = 16;   // rows per TSQR block (FP64)
+// rows per TSQR block over the merged core: FP64 registers hold 32 rows per column, FP32 64
+template <typename T>
+struct BigBR {
+  static constexpr int value = sizeof(T) == 8 ? 32 : 64;
+};
+// leaves of the TSQR over the merged core per SM: FP64 R factors fill ~103 KB of shared memory
+// (two CTAs per SM), FP32 ones ~52 KB (three CTAs per SM, register-limited, hide the
+// reflector latency)
+template <typename T>
+struct BigLeaves {
+  static constexpr int per_sm = sizeof(T) == 8 ? 2 : 3;
+};
 
 // B0 of the transport sum: block t = 0 is the right part of the state, block t = 1..nterm is
 // the same right part scaled by the operator's angular factors f1_t(l) f2_t(p), and each
@@ -152,10 +163,11 @@ struct RoundBufs {
   double* vJ;
 };
 
+template <typename T>
 static RoundBufs take_round_bufs(Bump& ws, int num_sms, int d, int R, long nrows, int n1, int n2, int K1, int K2,
                                  int rcapin1) {
   RoundBufs b;
-  const long L = tsqr_max_leaves<double, kBR>(num_sms, R, nrows, 0);
+  const long L = tsqr_max_leaves<T, BigBR<T>::value>(num_sms, R, nrows, BigLeaves<T>::per_sm * num_sms);
   b.tsqr_a = ws.take<double>((size_t)L * R * R);
   b.tsqr_b = ws.take<double>((size_t)((L + 1) / 2) * R * R);
   b.Bbase = ws.take<double>((size_t)rcapin1 * n1 * n2);
@@ -168,7 +180,7 @@ static RoundBufs take_round_bufs(Bump& ws, int num_sms, int d, int R, long nrows
   return b;
 }
 
-template <typename S>
+template <typename S, typename T>
 tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& ws) {
   cudaStream_t s = ctx->stream;
   const int d = x->d;
@@ -177,7 +189,7 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   const int K1 = x->rcap[1], K2 = (d == 3) ? x->rcap[2] : 1;
   LivePattern lp{x->rank + 1, K1, 1, 0};
   const int R = lp.ncap();
-  RoundBufs b = take_round_bufs(ws, ctx->num_sms, d, R, N, n1, n2, K1, K2, K1);
+  RoundBufs b = take_round_bufs<T>(ws, ctx->num_sms, d, R, N, n1, n2, K1, K2, K1);
   SmallJob job{};
   job.d = d;
   job.n1 = n1;
@@ -199,11 +211,12 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   job.Bnew = b.Bnew;
   job.vJ = b.vJ;
   job.ctrl = ctx->ctrl;
+  job.mixed = (sizeof(T) == 4);
   double* domega_ones = ws.take<double>((size_t)n1 * n2);
   job.domega = domega_ones;
   double* RZ = nullptr;
   if (!ws.dry) {
-    tt_status st = run_tsqr<double, kBR>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, 0, b.tsqr_a,
+    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, BigLeaves<T>::per_sm * ctx->num_sms, b.tsqr_a,
                                          b.tsqr_b, &RZ);
     if (st != TT_OK) return st;
     right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, b.Bbase);
@@ -212,7 +225,7 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   job.RZ = RZ;
   tt_status st = small_round(s, ctx->num_sms, job, ws);
   if (st != TT_OK || ws.dry) return st;
-  st = launch_update<double>(s, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
+  st = launch_update<T>(s, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
                              EpiPlain<S>{(S*)x->core[0], K1}, nullptr);
   if (st != TT_OK) return st;
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
@@ -222,7 +235,7 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
-template <typename S>
+template <typename S, typename T>
 tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol, int rmax, double* energy,
                     Bump& ws) {
   cudaStream_t s = ctx->stream;
@@ -233,7 +246,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- round 1: the transport sum, never materialised
   LivePattern lp1{I->rank + 1, K1, p->nterm + 1, p->nbc};
   const int R1 = lp1.ncap();
-  RoundBufs b1 = take_round_bufs(ws, ctx->num_sms, d, R1, N, n1, n2, K1, K2, K1);
+  RoundBufs b1 = take_round_bufs<T>(ws, ctx->num_sms, d, R1, N, n1, n2, K1, K2, K1);
   S* Zsrc = ws.take<S>((size_t)N * (K1 + 1));
   const long ngrid = (N + kTM - 1) / kTM;
   double* part1 = ws.take<double>((size_t)2 * ngrid);
@@ -264,6 +277,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   j1.Bnew = b1.Bnew;
   j1.vJ = b1.vJ;
   j1.ctrl = ctx->ctrl;
+  j1.mixed = (sizeof(T) == 4);
   double* RZ1 = nullptr;
   if (!ws.dry) {
     right_part<S>(s, d, K1, n1, K2, n2, (const S*)I->core[1], d == 3 ? (const S*)I->core[2] : nullptr, b1.Bbase);
@@ -275,7 +289,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     }
     k_b0_transport<<<256, 256, 0, s>>>(K1, p->nterm, p->nbc, n1, n2, b1.Bbase, p->fac1, p->fac2, p->bc_term_dev,
                                        b1.B0); count_launch();
-    tt_status st = run_tsqr<double, kBR>(s, ctx->num_sms, src1, lp1, N, 0, b1.tsqr_a, b1.tsqr_b, &RZ1);
+    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, src1, lp1, N, BigLeaves<T>::per_sm * ctx->num_sms, b1.tsqr_a, b1.tsqr_b, &RZ1);
     if (st != TT_OK) return st;
   }
   j1.RZ = RZ1;
@@ -283,13 +297,13 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   if (st != TT_OK) return st;
   // ---- source step fused into the write of the rounded transport update
   LivePattern lp2{nullptr, K1, 1, 1};
-  RoundBufs b2 = take_round_bufs(ws, ctx->num_sms, d, lp2.ncap(), N, n1, n2, K1, K2, K1);
+  RoundBufs b2 = take_round_bufs<T>(ws, ctx->num_sms, d, lp2.ncap(), N, n1, n2, K1, K2, K1);
   if (ws.dry) {
     SmallJob j2 = j1;
     j2.lp = lp2;
     return small_round(s, ctx->num_sms, j2, ws);
   }
-  st = launch_update<double>(s, src1, lp1, N, b1.W, K1,
+  st = launch_update<T>(s, src1, lp1, N, b1.W, K1,
                              EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps}, part1);
   if (st != TT_OK) return st;
   k_save_ranks<<<1, 32, 0, s>>>(ctx->ctrl); count_launch();
@@ -297,7 +311,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- round 2: [D^-1 Z_new, g]
   k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0); count_launch();
   double* RZ2 = nullptr;
-  st = run_tsqr<double, kBR>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, 0, b2.tsqr_a, b2.tsqr_b, &RZ2);
+  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, BigLeaves<T>::per_sm * ctx->num_sms, b2.tsqr_a, b2.tsqr_b, &RZ2);
   if (st != TT_OK) return st;
   SmallJob j2 = j1;
   j2.lp = lp2;
@@ -313,7 +327,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   j2.vJ = b2.vJ;
   st = small_round(s, ctx->num_sms, j2, ws);
   if (st != TT_OK) return st;
-  st = launch_update<double>(s, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
+  st = launch_update<T>(s, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
                              EpiFinal<S>{(S*)I->core[0], K1, b2.vJ}, part2);
   if (st != TT_OK) return st;
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
@@ -328,10 +342,14 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
-template tt_status round_impl<double>(tt_context*, tt_tensor*, double, int, Bump&);
-template tt_status round_impl<float>(tt_context*, tt_tensor*, double, int, Bump&);
-template tt_status step_impl<double>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
-template tt_status step_impl<float>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
+template tt_status round_impl<double, double>(tt_context*, tt_tensor*, double, int, Bump&);
+template tt_status round_impl<float, double>(tt_context*, tt_tensor*, double, int, Bump&);
+template tt_status round_impl<double, float>(tt_context*, tt_tensor*, double, int, Bump&);
+template tt_status round_impl<float, float>(tt_context*, tt_tensor*, double, int, Bump&);
+template tt_status step_impl<double, double>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
+template tt_status step_impl<float, double>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
+template tt_status step_impl<double, float>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
+template tt_status step_impl<float, float>(tt_context*, const tt_plan*, tt_tensor*, double, int, double*, Bump&);
 
 template <typename S>
 tt_status energy_density_impl(tt_context* ctx, const tt_plan* p, const tt_tensor* x, double* out, Bump& ws) {

@@ -4,9 +4,11 @@
 #include "small.cuh"
 
 namespace ttk {
-template <typename S>
+// S: storage type of the cores; T: arithmetic of the passes over the merged core (TSQR leaves
+// and merges, update pass).  Small cores, norms, rank decisions and energies are FP64.
+template <typename S, typename T>
 tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& ws);
-template <typename S>
+template <typename S, typename T>
 tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol, int rmax, double* energy,
                     Bump& ws);
 template <typename S>
