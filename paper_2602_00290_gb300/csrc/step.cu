@@ -243,7 +243,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   const long N = I->n[0];
   const int n1 = p->n1, n2 = p->n2, nang = n1 * n2;
   const int K1 = I->rcap[1], K2 = (d == 3) ? I->rcap[2] : 1;
-  // ---- round 1: the transport sum, never materialised
+  // ---- first rounding: the transport sum, never materialised
   LivePattern lp1{I->rank + 1, K1, p->nterm + 1, p->nbc};
   const int R1 = lp1.ncap();
   RoundBufs b1 = take_round_bufs<T>(ws, ctx->num_sms, d, R1, N, n1, n2, K1, K2, K1);
@@ -308,7 +308,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   if (st != TT_OK) return st;
   k_save_ranks<<<1, 32, 0, s>>>(ctx->ctrl); count_launch();
   lp2.r_ptr = &ctx->ctrl->k[2];
-  // ---- round 2: [D^-1 Z_new, g]
+  // ---- second rounding: [D^-1 Z_new, g]
   k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0); count_launch();
   double* RZ2 = nullptr;
   st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, BigLeaves<T>::per_sm * ctx->num_sms, b2.tsqr_a, b2.tsqr_b, &RZ2);
