@@ -180,6 +180,22 @@ tt_status tt_apply_transport(tt_context *ctx, const tt_plan *plan, const tt_tens
 tt_status tt_step(tt_context *ctx, const tt_plan *plan, tt_tensor *I, double tol, int32_t rmax,
                   tt_precision prec, double *energy_dev);
 
+/* *out_dev <- <x, y> like tt_dot, for callers that cannot allocate device memory: programs
+ * that reserve a fixed device-memory budget up front and may not grow it, and code that must
+ * not block while it runs (a real-time loop, a host callback), where cudaMalloc/cudaFree can
+ * synchronise the device.  The paper has no counterpart; this is a deployment variant of
+ * tt_dot.  It takes a stream of the CURRENT device instead of a context and allocates
+ * nothing: its scratch is one file-scope device array of 4 MiB (2^19 doubles) per device,
+ * held from the first call on that device until the process exits.  The first call on a
+ * device looks up the array's device address (make it before any stream capture on that
+ * device).  If the row chunking cannot fit in the 4 MiB (rank capacities with
+ * rcap_1(x)*rcap_1(y)*3 + (rcap_1(x)+rcap_1(y))*n_1*n_2 beyond 2^19 doubles) the call returns
+ * TT_ERR_WORKSPACE and launches nothing.  Every call writes all the scratch it reads, so no
+ * clearing is needed between calls, but all calls on a device share the one array: calls
+ * that overlap on the GPU (several streams, or several host threads) race and give wrong
+ * results.  Same arguments, layout and errors as tt_dot otherwise. */
+tt_status tt_dot_noalloc(void *cuda_stream, const tt_tensor *x, const tt_tensor *y, double *out_dev);
+
 /* Radiation energy density per merged row, E_f = (4 pi / c) J_f (Sec. 2), into the
  * device array out_dev[N_Z]. */
 tt_status tt_energy_density(tt_context *ctx, const tt_plan *plan, const tt_tensor *x, double *out_dev);

@@ -30,7 +30,7 @@ PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED}
 EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sync", "tt_workspace_query",
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
-           "tt_context_counters", "tt_context_diagnostics")
+           "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc")
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other")
 
 
@@ -91,6 +91,7 @@ def lib():
             "tt_context_set_timing": [vp, ctypes.c_int],
             "tt_context_counters": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
             "tt_context_diagnostics": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int],
+            "tt_dot_noalloc": [vp, ctypes.POINTER(_Tensor), ctypes.POINTER(_Tensor), vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -309,6 +310,15 @@ def tt_dot(ctx: Context, x: TT, y: TT, out=None):
         out = torch.zeros(1, dtype=torch.float64, device="cuda")
     _check(lib().tt_dot(ctx.handle, ctypes.byref(x._struct()), ctypes.byref(y._struct()),
                         ctypes.c_void_p(out.data_ptr())), "tt_dot")
+    return out
+
+
+def tt_dot_noalloc(stream, x: TT, y: TT, out):
+    """<x, y> into the device double `out` without any device allocation (see tt.h); `stream`
+    is a torch CUDA stream (or None for the legacy default stream)."""
+    h = ctypes.c_void_p(stream.cuda_stream) if stream is not None else None
+    _check(lib().tt_dot_noalloc(h, ctypes.byref(x._struct()), ctypes.byref(y._struct()),
+                                ctypes.c_void_p(out.data_ptr())), "tt_dot_noalloc")
     return out
 
 

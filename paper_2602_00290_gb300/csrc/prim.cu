@@ -283,6 +283,45 @@ tt_status dot_impl(tt_context* ctx, const tt_tensor* x, const tt_tensor* y, doub
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
+// Inner product with caller-provided scratch (no workspace, no allocation): the same kernels
+// as dot_impl with the number of row chunks reduced until everything fits in `cap` doubles.
+template <typename S>
+tt_status dot_into(cudaStream_t s, const tt_tensor* x, const tt_tensor* y, double* out, double* scratch,
+                   size_t cap) {
+  const int d = x->d;
+  const long N = x->n[0];
+  const int n1 = x->n[1], n2 = (d == 3) ? x->n[2] : 1, nang = n1 * n2;
+  const int rx = x->rcap[1], ry = y->rcap[1];
+  const size_t ne = (size_t)rx * ry;
+  const size_t fixed = ne /*W1*/ + ne /*G*/ + (size_t)(rx + ry) * nang;
+  if (fixed + ne > cap) return TT_ERR_WORKSPACE;
+  long nchunks = (N + 1023) / 1024;
+  if (nchunks > 2048) nchunks = 2048;
+  const long fit = (long)((cap - fixed) / ne);
+  if (nchunks > fit) nchunks = fit;
+  if (nchunks < 1) nchunks = 1;
+  const long rows_per = (N + nchunks - 1) / nchunks;
+  nchunks = (N + rows_per - 1) / rows_per;
+  double* part = scratch;
+  double* W1 = part + (size_t)nchunks * ne;
+  double* Bx = W1 + ne;
+  double* By = Bx + (size_t)rx * nang;
+  double* G = By + (size_t)ry * nang;
+  dim3 grid((unsigned)nchunks, (unsigned)((ne + 255) / 256));
+  k_gram_partials<S><<<grid, 256, 0, s>>>(N, rows_per, (const S*)x->core[0], rx, rx, (const S*)y->core[0], ry, ry,
+                                          part); count_launch();
+  k_sum_chunks<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(part, nchunks, (int)ne, W1); count_launch();
+  right_part<S>(s, d, rx, n1, d == 3 ? x->rcap[2] : 1, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr,
+                Bx);
+  right_part<S>(s, d, ry, n1, d == 3 ? y->rcap[2] : 1, n2, (const S*)y->core[1], d == 3 ? (const S*)y->core[2] : nullptr,
+                By);
+  small_gemm<double, double>(s, rx, ry, nang, Bx, nang, 1, By, 1, nang, G, ry, nullptr, nullptr);
+  k_dot_final<<<1, 1024, 0, s>>>((int)ne, W1, G, out); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+template tt_status dot_into<double>(cudaStream_t, const tt_tensor*, const tt_tensor*, double*, double*, size_t);
+template tt_status dot_into<float>(cudaStream_t, const tt_tensor*, const tt_tensor*, double*, double*, size_t);
+
 template tt_status apply_transport_impl<double>(tt_context*, const tt_plan*, const tt_tensor*, tt_tensor*);
 template tt_status apply_transport_impl<float>(tt_context*, const tt_plan*, const tt_tensor*, tt_tensor*);
 template tt_status axpy_impl<double>(tt_context*, double, const tt_tensor*, tt_tensor*);

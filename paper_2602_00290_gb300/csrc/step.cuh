@@ -18,5 +18,8 @@ tt_status apply_transport_impl(tt_context* ctx, const tt_plan* p, const tt_tenso
 template <typename S>
 tt_status axpy_impl(tt_context* ctx, double alpha, const tt_tensor* x, tt_tensor* y);
 template <typename S>
+tt_status dot_into(cudaStream_t s, const tt_tensor* x, const tt_tensor* y, double* out, double* scratch,
+                   size_t cap);
+template <typename S>
 tt_status dot_impl(tt_context* ctx, const tt_tensor* x, const tt_tensor* y, double* out, Bump& ws);
 }  // namespace ttk
