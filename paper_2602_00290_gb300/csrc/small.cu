@@ -202,6 +202,132 @@ __global__ void __launch_bounds__(1024) k_cgs2_sigma(int nv, int ldv, double* __
   }
 }
 
+// ---- CholeskyQR2 of the first K columns of V (FP64) ----------------------------------------
+// The same factorisation V[:, :K] = Q T as Gram-Schmidt in column order, computed as two passes
+// of: Gram matrix G = V^T V (row chunks spread over many CTAs), upper Cholesky factor
+// G = T^T T (one CTA), V <- V T^{-1} (one thread per row).  Column j of T depends on columns
+// 0..j of V only, so leading columns are unaffected by what follows them.  The columns here are
+// P = A U for nearly orthogonal U, i.e. graded: V = W D with D the column norms and W of
+// condition near 1 on the columns that matter; Cholesky and triangular solves are invariant
+// under that scaling, so two passes give FP64-orthonormal Q and |T_jj| to FP64 relative
+// accuracy.  A column whose Cholesky pivot is at the round-off level of its own diagonal has
+// nothing left beyond the earlier columns: its row of T and its column of Q are set to zero.
+
+constexpr int kGramTileRows = 32;   // rows staged in shared memory per step
+constexpr int kGramChunkRows = 64;  // rows per CTA (one partial Gram matrix each)
+constexpr int kGramEntries = 2048;  // Gram entries per CTA (8 per thread)
+constexpr int kTrsmRows = 64;       // rows per CTA in the triangular solve
+
+__global__ void __launch_bounds__(256) k_gram_chunks(int nv, int ldv, const double* __restrict__ V, int K,
+                                                     double* __restrict__ part) {
+  __shared__ double gs[kGramTileRows * 129];
+  const int KK = K * K;
+  const int beg = blockIdx.x * kGramChunkRows;
+  const int end = min(beg + kGramChunkRows, nv);
+  const int e0 = blockIdx.y * kGramEntries;
+  double acc[kGramEntries / 256];
+#pragma unroll
+  for (int i = 0; i < kGramEntries / 256; ++i) acc[i] = 0.0;
+  for (int r0 = beg; r0 < end; r0 += kGramTileRows) {
+    const int nr = min(kGramTileRows, end - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
+      const int rr = idx / K, c = idx - rr * K;
+      gs[rr * K + c] = V[(size_t)(r0 + rr) * ldv + c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kGramEntries / 256; ++i) {
+      const int e = e0 + threadIdx.x + 256 * i;
+      if (e < KK) {
+        const int a = e / K, b = e - (e / K) * K;
+        double t = acc[i];
+        for (int rr = 0; rr < nr; ++rr) t += gs[rr * K + a] * gs[rr * K + b];
+        acc[i] = t;
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kGramEntries / 256; ++i) {
+    const int e = e0 + threadIdx.x + 256 * i;
+    if (e < KK) part[(size_t)blockIdx.x * KK + e] = acc[i];
+  }
+}
+
+__global__ void k_gram_sum(int nchunks, int KK, const double* __restrict__ part, double* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= KK) return;
+  double t = 0.0;
+  for (int c = 0; c < nchunks; ++c) t += part[(size_t)c * KK + e];
+  G[e] = t;
+}
+
+// Upper Cholesky factor T (K x K, row-major, zero below the diagonal) of the symmetric G.
+__global__ void __launch_bounds__(256) k_chol_upper(int K, const double* __restrict__ G, double* __restrict__ T) {
+  extern __shared__ double chs[];
+  double* A = chs;         // [K][K] working copy (upper triangle used)
+  double* d0 = chs + K * K;  // original diagonal
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) A[idx] = G[idx];
+  for (int j = threadIdx.x; j < K; j += blockDim.x) d0[j] = G[(size_t)j * K + j];
+  __syncthreads();
+  const double thr = 64.0 * K * 2.220446049250313e-16;
+  for (int j = 0; j < K; ++j) {
+    const double piv = A[j * K + j];
+    const bool live = piv > thr * d0[j] && piv > 0.0;
+    const double tjj = live ? sqrt(piv) : 0.0;
+    const double inv = live ? 1.0 / tjj : 0.0;
+    __syncthreads();
+    for (int c = j + threadIdx.x; c < K; c += blockDim.x) A[j * K + c] = (c == j) ? tjj : A[j * K + c] * inv;
+    __syncthreads();
+    const int m = K - j - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int a = j + 1 + idx / m, b = j + 1 + (idx - (idx / m) * m);
+      if (b >= a) A[a * K + b] -= A[j * K + a] * A[j * K + b];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+    const int i = idx / K, c = idx - (idx / K) * K;
+    T[idx] = (c >= i) ? A[idx] : 0.0;
+  }
+}
+
+// V[row][:K] <- V[row][:K] T^{-1} (forward substitution along the row; dead columns give 0).
+__global__ void __launch_bounds__(kTrsmRows) k_trsm_rows(int nv, int ldv, double* __restrict__ V, int K,
+                                                         const double* __restrict__ T) {
+  extern __shared__ double trs[];
+  double* Ts = trs;              // [K][K]
+  double* Rw = trs + K * K;      // [kTrsmRows][K + 1]
+  const int row0 = blockIdx.x * kTrsmRows;
+  const int nr = min(kTrsmRows, nv - row0);
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Ts[idx] = T[idx];
+  for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
+    const int rr = idx / K, c = idx - (idx / K) * K;
+    Rw[rr * (K + 1) + c] = V[(size_t)(row0 + rr) * ldv + c];
+  }
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    double* q = Rw + threadIdx.x * (K + 1);
+    for (int j = 0; j < K; ++j) {
+      const double tjj = Ts[j * K + j];
+      double v = q[j];
+      for (int i = 0; i < j; ++i) v -= q[i] * Ts[i * K + j];
+      q[j] = (tjj > 0.0) ? v / tjj : 0.0;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
+    const int rr = idx / K, c = idx - (idx / K) * K;
+    V[(size_t)(row0 + rr) * ldv + c] = Rw[rr * (K + 1) + c];
+  }
+}
+
+__global__ void k_sig_from_chol(int K, const double* __restrict__ T1, const double* __restrict__ T2,
+                                double* __restrict__ sig) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < K) sig[j] = T1[(size_t)j * K + j] * T2[(size_t)j * K + j];
+}
+
 // Sort the first K columns of V (nv x ldv) and sig[0..K) by decreasing sig (ties by index).
 __global__ void __launch_bounds__(1024) k_sort_cols(int nv, int ldv, int K, double* __restrict__ sig,
                                                     double* __restrict__ V, double* __restrict__ tmp) {
@@ -626,14 +752,16 @@ __global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restr
   // normalised columns -> U[i][c]
   for (int c = warp; c < n; c += nwarps) {
     const T* ac = At + (size_t)c * n;
-    T s2 = 0;
-    for (int i = lane; i < n; i += 32) s2 += ac[i] * ac[i];
+    // FP64 norm of the stored column: U gets unit columns to FP64 accuracy, so that |A u_j|
+    // differs from sigma_j only at second order in the FP32 rotation error
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) s2 += (double)ac[i] * (double)ac[i];
     s2 = warp_sum(s2);
-    const double inv = (s2 > T(0)) ? 1.0 / sqrt((double)s2) : 0.0;
+    const double inv = (s2 > 0.0) ? 1.0 / sqrt(s2) : 0.0;
     for (int i = lane; i < n; i += 32) U[(size_t)i * n + c] = (double)ac[i] * inv;
     // the column norm before normalising is the singular value to FP32 accuracy; columns the
     // FP32 sweep cannot resolve have tiny norms here even though A u can be large
-    if (lane == 0) raw[c] = sqrt((double)s2);
+    if (lane == 0) raw[c] = sqrt(s2);
   }
 }
 
@@ -787,6 +915,36 @@ static tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const doub
   return coop_jacobi(s, num_sms, m, n, At, V, sigma, nullptr, 0, 0, Vout, perm, tmp, ctrl);
 }
 
+// V[:, :K] (nv x ldv, row-major) <- Q and sig[j] = |T_jj| of V[:, :K] = Q T, by CholeskyQR2
+// in FP64 for K <= 128, by one-CTA Gram-Schmidt beyond.
+static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K, double* sig, Bump& ws) {
+  const int KK = K * K;
+  const int nchunks = (nv + kGramChunkRows - 1) / kGramChunkRows;
+  double* part = ws.take<double>((size_t)nchunks * KK);
+  double* G = ws.take<double>(KK);
+  double* T1 = ws.take<double>(KK);
+  double* T2 = ws.take<double>(KK);
+  if (ws.dry) return TT_OK;
+  if (K > 128 || nv < 1) {
+    k_cgs2_sigma<<<1, 1024, 0, s>>>(nv, ldv, V, K, sig); count_launch();
+    return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  }
+  const size_t chol_smem = sizeof(double) * ((size_t)KK + K);
+  const size_t trsm_smem = sizeof(double) * ((size_t)KK + (size_t)kTrsmRows * (K + 1));
+  cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem);
+  cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
+  for (int pass = 0; pass < 2; ++pass) {
+    double* T = pass ? T2 : T1;
+    k_gram_chunks<<<dim3((unsigned)nchunks, (unsigned)((KK + kGramEntries - 1) / kGramEntries)), 256, 0, s>>>(
+        nv, ldv, V, K, part); count_launch();
+    k_gram_sum<<<(KK + 255) / 256, 256, 0, s>>>(nchunks, KK, part, G); count_launch();
+    k_chol_upper<<<1, 256, chol_smem, s>>>(K, G, T); count_launch();
+    k_trsm_rows<<<(nv + kTrsmRows - 1) / kTrsmRows, kTrsmRows, trsm_smem, s>>>(nv, ldv, V, K, T); count_launch();
+  }
+  k_sig_from_chol<<<(K + 127) / 128, 128, 0, s>>>(K, T1, T2, sig); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
 // Mixed-precision SVD of an explicit tall matrix A (source `src`, rows x cols): FP32 TSQR
 // factor R and one-CTA FP32 Jacobi on R^T giving the right singular vectors U (cols x cols)
 // and their FP32 singular values `raw`, with perm the order of decreasing raw.
@@ -841,7 +999,10 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
     k_write_sorted<<<(unsigned)(((long)R * n1 * n2 + 255) / 256 < 1024 ? ((long)R * n1 * n2 + 255) / 256 : 1024), 256, 0,
                      s>>>(R * n1, n2, n2, P2, sigc2, perm2, P2s, n2, 0); count_launch();
     k_write_sorted<<<(n2 * n2 + 255) / 256, 256, 0, s>>>(n2, n2, n2, U2, sigc2, perm2, V2, n2, 0); count_launch();
-    k_cgs2_sigma<<<1, 1024, 0, s>>>(R * n1, n2, P2s, n2, sig2); count_launch();
+  }
+  st = cholqr2_sigma(s, R * n1, n2, P2s, n2, sig2, ws);
+  if (st != TT_OK) return st;
+  if (!ws.dry) {
     k_sort_cols<<<1, 1024, 0, s>>>(n2, n2, n2, sig2, V2, tmp2); count_launch();
     k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
                               j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
@@ -861,11 +1022,14 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   double* V1 = ws.take<double>((size_t)nv * K1);
   double *U1 = nullptr, *P1 = nullptr;
   st = svd_right_mixed(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &U1, &P1, sigc1, perm1);
+  if (st != TT_OK) return st;
+  if (!ws.dry) {
+    small_gemm<double, double>(s, nv, R, R, Y2, 1, nv, U1, R, 1, P1, R, nullptr, nullptr);  // P1 = A1 U1
+    k_write_sorted<<<(unsigned)(((long)nv * R + 255) / 256 < 1024 ? ((long)nv * R + 255) / 256 : 1024), 256, 0,
+                     s>>>(nv, R, R, P1, sigc1, perm1, P1s, R, 0); count_launch();
+  }
+  st = cholqr2_sigma(s, nv, R, P1s, Kr, sig1, ws);
   if (st != TT_OK || ws.dry) return st;
-  small_gemm<double, double>(s, nv, R, R, Y2, 1, nv, U1, R, 1, P1, R, nullptr, nullptr);  // P1 = A1 U1
-  k_write_sorted<<<(unsigned)(((long)nv * R + 255) / 256 < 1024 ? ((long)nv * R + 255) / 256 : 1024), 256, 0, s>>>(
-      nv, R, R, P1, sigc1, perm1, P1s, R, 0); count_launch();
-  k_cgs2_sigma<<<1, 1024, 0, s>>>(nv, R, P1s, Kr, sig1); count_launch();
   // energy beyond the Kr refined values: ||A1||_F^2 - sum sigma_j^2 (FP64)
   k_fro2<<<1, 1024, 0, s>>>((long)R * nv, Y2, fro1); count_launch();
   k_tail_from_fro<<<1, 32, 0, s>>>(Kr, sig1, fro1, tailK); count_launch();

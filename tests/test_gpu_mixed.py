@@ -61,3 +61,23 @@ def test_mixed_round_reconstruction(tt, ctx):
         ctx.sync()
         assert x.ranks() == [1, 5, 4, 1]
         assert fro_rel(nt.full(x.to_cores()), nt.full(a)) < 1e-6
+
+
+@pytest.mark.parametrize("seed0", [20, 40])
+@pytest.mark.parametrize("tol", [1e-2, 1e-4, 3e-6])
+def test_mixed_round_ranks_match_oracle(tt, ctx, seed0, tol):
+    """Mixed rounding keeps the oracle's ranks wherever the oracle's tail is farther from the
+    threshold than the FP32 resolution of the singular values (about 6e-8 |X| each): a relative
+    gap of 0.2 at tol 3e-6, 0.01 above."""
+    n = [233, 5, 9]
+    terms = [nt.scale(random_tt(n, [3, 2], seed=seed0 + i), 10.0 ** -i) for i in range(6)]
+    a = nt.add_many(terms)
+    info = {}
+    want = nt.round_tt(a, tol, 20, info)
+    need = 0.2 if tol < 1e-5 else 0.01
+    assert all(b["gap"] > need for b in info["bonds"])
+    x = tt.TT.from_cores(a, rcap=[20, 20])
+    tt.tt_round(ctx, x, tol, 20, "mixed")
+    ctx.sync()
+    assert x.ranks() == nt.ranks(want)
+    assert fro_rel(nt.full(x.to_cores()), nt.full(want)) < 1e-5
