@@ -21,6 +21,11 @@ struct SrcRows {
   __device__ __forceinline__ double load(const Col& cc, long k) const {
     return (double)A[k * ld + cc.c];
   }
+  __device__ __forceinline__ unsigned row_flags(long) const { return 0u; }
+  template <typename T>
+  __device__ __forceinline__ T loadT(const Col& cc, long k, unsigned) const {
+    return (T)A[k * ld + cc.c];
+  }
 };
 
 // Explicit matrix read transposed: element (row i, column c) = A[c * ld + i].
@@ -32,6 +37,11 @@ struct SrcCols {
   __device__ __forceinline__ Col col(int c) const { return Col{c}; }
   __device__ __forceinline__ double load(const Col& cc, long k) const {
     return (double)A[(long)cc.c * ld + k];
+  }
+  __device__ __forceinline__ unsigned row_flags(long) const { return 0u; }
+  template <typename T>
+  __device__ __forceinline__ T loadT(const Col& cc, long k, unsigned) const {
+    return (T)A[(long)cc.c * ld + k];
   }
 };
 
@@ -58,9 +68,11 @@ struct SrcStencil {
     int kind;  // 0: Z, 1: operator image, 2: inflow column, 3: none
     int q, ax, w, b;
     double lam;
+    float lamf;
+    long s;    // row stride of the operator's axis
   };
   __device__ __forceinline__ Col col(int c) const {
-    Col cc{3, 0, 0, 0, 0, 0.0};
+    Col cc{3, 0, 0, 0, 0, 0.0, 0.0f, 0};
     const int t = c / rcap;
     if (t == 0) {
       cc.kind = 0;
@@ -71,6 +83,8 @@ struct SrcStencil {
       cc.ax = axis[t - 1];
       cc.w = w[t - 1];
       cc.lam = lam[t - 1];
+      cc.lamf = (float)cc.lam;
+      cc.s = stride[cc.ax];
     } else {
       cc.kind = 2;
       cc.b = c - (nterm + 1) * rcap;
@@ -100,6 +114,40 @@ struct SrcStencil {
     const bool at_face = (cc.w > 0) ? (idx == 0) : (idx == ext[cc.ax] - 1);
     return at_face ? bcval[cc.b * G + (int)(k % G)] : 0.0;
   }
+  // Per-row neighbour flags, computed once per row and shared by all columns: bit 2a is set
+  // when row k has a lower neighbour along axis a, bit 2a+1 an upper one; the group index
+  // k mod G sits in bits 8 and up.
+  __device__ __forceinline__ unsigned row_flags(long k) const {
+    unsigned f = 0u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long idx = (k / stride[a]) % ext[a];
+      f |= (idx > 0 ? 1u : 0u) << (2 * a);
+      f |= (idx < ext[a] - 1 ? 1u : 0u) << (2 * a + 1);
+    }
+    return f | ((unsigned)(k % G) << 8);
+  }
+  // The value of load() in arithmetic T, from the row's flags.
+  template <typename T>
+  __device__ __forceinline__ T loadT(const Col& cc, long k, unsigned fl) const {
+    if (cc.kind == 0) return (T)Z[k * ldz + cc.q];
+    if (cc.kind == 3) return T(0);
+    if (cc.kind == 1) {
+      const T lamT = (sizeof(T) == 8) ? (T)cc.lam : (T)cc.lamf;
+      const T zk = (T)Z[k * ldz + cc.q];
+      T diff;
+      if (cc.w > 0) {
+        const T up = ((fl >> (2 * cc.ax)) & 1u) ? (T)Z[(k - cc.s) * ldz + cc.q] : T(0);
+        diff = zk - up;
+      } else {
+        const T dn = ((fl >> (2 * cc.ax + 1)) & 1u) ? (T)Z[(k + cc.s) * ldz + cc.q] : T(0);
+        diff = dn - zk;
+      }
+      return -lamT * diff;
+    }
+    const bool at_face = (cc.w > 0) ? !((fl >> (2 * cc.ax)) & 1u) : !((fl >> (2 * cc.ax + 1)) & 1u);
+    return at_face ? (T)bcval[cc.b * G + (int)(fl >> 8)] : T(0);
+  }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -112,6 +160,16 @@ struct SrcStencil {
 // vector is double-buffered).
 
 __device__ __forceinline__ int tri_off(int j, int n) { return j * n - (j * (j - 1)) / 2; }
+
+__device__ __forceinline__ void ld4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
 
 template <typename T, int BR>
 __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, T* taub, int& buf,
@@ -295,19 +353,21 @@ inline long tsqr_max_leaves(int num_sms, int ncap, long nrows, int max_leaves) {
 
 // ---------------------------------------------------------------------------------------
 // Update pass: out[k][j] = scale_k * sum_c A[k][c] W[c][j] over the live columns c of A,
-// j < kcap, plus an optional extra column out[k][kcap].  A tile of TM rows of A (formed from
-// the source, e.g. the stencil sum) and W sit in shared memory; each thread accumulates a
-// strip of outputs.  Per-row epilogue values (scale, extra column, two energy partials) are
-// computed by thread m < TM from the full output row; partial sums per CTA go to
-// partials[2*cta + {0,1}] in a fixed order.
+// j < kcap, plus an optional extra column out[k][kcap].  Persistent CTAs: W is staged in
+// shared memory once per CTA, which then walks row tiles of TM rows.  A tile of A is formed
+// from the source (e.g. the stencil sum, with per-row neighbour flags) into shared memory;
+// each thread accumulates a TM/32-row x 4-column block of the output over all columns of A.
+// The per-row epilogue (the dot with vJ, scale, extra column, two energy partials) runs one
+// warp per row; per-CTA energy partials go to partials[2*cta + {0,1}] in a fixed order.
 
 template <typename SO>
 struct EpiPlain {
   SO* out;
   long ld;
   static constexpr bool kExtra = false;
-  __device__ __forceinline__ void prep(long, const double*, int, double& scale, double& extra, double& e0,
-                                       double& e1) const {
+  static constexpr bool kDot = false;
+  const double* vj() const { return nullptr; }
+  __device__ __forceinline__ void prep(long, double, double& scale, double& extra, double& e0, double& e1) const {
     scale = 1.0;
     extra = 0.0;
     e0 = 0.0;
@@ -315,8 +375,8 @@ struct EpiPlain {
   }
 };
 
-// Backward-Euler source update of Eq. (discRTsource) at fixed T on a freshly rounded row:
-// J* = Z_new[k,:] . vJ, J^{m+1} = (J* + a eps)/(1 + a), row scale 1/(1 + a + s) and the
+// Backward-Euler source update of Eq. (discRTsource) at fixed T on a freshly rounded row with
+// J* = Z_new[k,:] . vJ: J^{m+1} = (J* + a eps)/(1 + a), row scale 1/(1 + a + s) and the
 // isotropic column g = (a eps + s J^{m+1})/(1 + a + s).
 template <typename SO>
 struct EpiSource {
@@ -327,10 +387,9 @@ struct EpiSource {
   const double* scoef;
   const double* eps;
   static constexpr bool kExtra = true;
-  __device__ __forceinline__ void prep(long k, const double* o, int kcap, double& scale, double& extra,
-                                       double& e0, double& e1) const {
-    double js = 0.0;
-    for (int j = 0; j < kcap; ++j) js += o[j] * vJ[j];
+  static constexpr bool kDot = true;
+  __device__ __forceinline__ void prep(long k, double js, double& scale, double& extra, double& e0,
+                                       double& e1) const {
     const double a = acoef[k], s = scoef[k], e = eps[k];
     const double jn = (js + a * e) / (1.0 + a);
     const double dinv = 1.0 / (1.0 + a + s);
@@ -348,10 +407,9 @@ struct EpiFinal {
   long ld;
   const double* vJ;
   static constexpr bool kExtra = false;
-  __device__ __forceinline__ void prep(long, const double* o, int kcap, double& scale, double& extra,
-                                       double& e0, double& e1) const {
-    double js = 0.0;
-    for (int j = 0; j < kcap; ++j) js += o[j] * vJ[j];
+  static constexpr bool kDot = true;
+  __device__ __forceinline__ void prep(long, double js, double& scale, double& extra, double& e0,
+                                       double& e1) const {
     scale = 1.0;
     extra = 0.0;
     e0 = js;
@@ -359,81 +417,172 @@ struct EpiFinal {
   }
 };
 
-template <typename T, int TM>
+template <class Epi>
+__device__ __forceinline__ const double* epi_vj(const Epi& e) {
+  if constexpr (Epi::kDot) return e.vJ;
+  else return nullptr;
+}
+
+// Output columns of the update GEMM: kcap rounded up to a multiple of 4.
+template <class Epi>
+__host__ __device__ inline int update_kpad(int kcap) { return (kcap + 3) & ~3; }
+template <typename T, int TM, class Src, class Epi>
 __host__ __device__ inline size_t update_smem_bytes(int ncap, int kcap) {
-  return ((sizeof(T) * ((size_t)TM * (ncap + 1) + (size_t)ncap * kcap) + 15) & ~(size_t)15) +
-         sizeof(double) * ((size_t)TM * (kcap + 1) + 4 * TM);
+  const int kpad = update_kpad<Epi>(kcap);
+  size_t b = sizeof(T) * ((size_t)ncap * kpad + (size_t)TM * (ncap + 1) + (size_t)TM * kpad);
+  b = (b + 15) & ~(size_t)15;
+  b += sizeof(typename Src::Col) * (size_t)ncap;
+  b = (b + 15) & ~(size_t)15;
+  return b + sizeof(double) * (3 * TM + 2 * 256) + sizeof(T) * (size_t)kpad + sizeof(unsigned) * TM + (size_t)ncap;
 }
 
 template <typename T, int TM, class Src, class Epi>
 __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nrows, const double* __restrict__ W,
                                                 int kcap, Epi epi, double* __restrict__ partials) {
+  static_assert(TM % 32 == 0, "rows per tile: a multiple of 32");
+  constexpr int RPT = TM / 32;  // output rows per thread
+  using Col = typename Src::Col;
   extern __shared__ __align__(16) unsigned char upd_smem[];
   const int ncap = lp.ncap();
+  const int kpad = update_kpad<Epi>(kcap);
+  const int lda = ncap + 1;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
-  T* As = reinterpret_cast<T*>(upd_smem);                            // [TM][ncap+1]
-  T* Ws = As + (size_t)TM * (ncap + 1);                              // [ncap][kcap]
-  const size_t os_off = ((sizeof(T) * ((size_t)TM * (ncap + 1) + (size_t)ncap * kcap) + 15) & ~(size_t)15);
-  double* Os = reinterpret_cast<double*>(upd_smem + os_off);         // [TM][kcap+1]
-  double* rowv = Os + (size_t)TM * (kcap + 1);                       // [4][TM]
-  const long row0 = (long)blockIdx.x * TM;
-  for (int i = threadIdx.x; i < ncap * kcap; i += blockDim.x) Ws[i] = (T)W[i];
-  for (int c = threadIdx.x; c < ncap; c += blockDim.x) {
-    const bool live = lp.live(c, r);
-    const auto cc = src.col(c);
-    for (int m = 0; m < TM; ++m) {
-      const long k = row0 + m;
-      As[(size_t)m * (ncap + 1) + c] = (live && k < nrows) ? (T)src.load(cc, k) : T(0);
-    }
+  T* Ws = reinterpret_cast<T*>(upd_smem);    // [ncap][kpad]: W, then W vJ
+  T* As = Ws + (size_t)ncap * kpad;          // [TM][ncap + 1]
+  T* Os = As + (size_t)TM * lda;             // [TM][kpad]
+  size_t off = sizeof(T) * ((size_t)ncap * kpad + (size_t)TM * lda + (size_t)TM * kpad);
+  off = (off + 15) & ~(size_t)15;
+  Col* cols = reinterpret_cast<Col*>(upd_smem + off);
+  off += sizeof(Col) * (size_t)ncap;
+  off = (off + 15) & ~(size_t)15;
+  double* rowv = reinterpret_cast<double*>(upd_smem + off);  // [3][TM]: J*, scale, extra
+  double* red = rowv + 3 * TM;                                // [blockDim][2] energy partials
+  T* vJs = reinterpret_cast<T*>(red + 2 * 256);               // [kpad] vJ in arithmetic T
+  unsigned* fl = reinterpret_cast<unsigned*>(vJs + kpad);
+  unsigned char* livec = reinterpret_cast<unsigned char*>(fl + TM);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
+  const double* vJ = epi_vj(epi);
+  for (int c = tid; c < ncap; c += blockDim.x) {
+    cols[c] = src.col(c);
+    livec[c] = lp.live(c, r) ? 1 : 0;
   }
-  __syncthreads();
-  const int m = threadIdx.x % TM;
-  const int strip = threadIdx.x / TM;
-  const int nstrip = blockDim.x / TM;
-  for (int j0 = strip; j0 < kcap; j0 += nstrip * 4) {
-    T acc[4] = {T(0), T(0), T(0), T(0)};
-    for (int c = 0; c < ncap; ++c) {
-      const T a = As[(size_t)m * (ncap + 1) + c];
+  for (int i = tid; i < ncap * kpad; i += blockDim.x) {
+    const int c = i / kpad, j = i - (i / kpad) * kpad;
+    Ws[i] = (j < kcap) ? (T)W[(size_t)c * kcap + j] : T(0);
+  }
+  for (int j = tid; j < kpad; j += blockDim.x) vJs[j] = (vJ && j < kcap) ? (T)vJ[j] : T(0);
+  const long ntiles = (nrows + TM - 1) / TM;
+  double e0t = 0.0, e1t = 0.0;  // this thread's energy partials (rows it prepared)
+  const int jg = tid & 7, mp = tid >> 3;  // 4 columns at 4*jg (+32 per column block), rows mp*RPT..
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long row0 = tile * TM;
+    __syncthreads();  // previous tile's buffers are free (and the staging above is done)
+    for (int m = tid; m < TM; m += blockDim.x) fl[m] = (row0 + m < nrows) ? src.row_flags(row0 + m) : 0u;
+    __syncthreads();
+    // tile of A: one warp per row, lanes over columns (coalesced row reads)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int j = j0 + u * nstrip;
-        if (j < kcap) acc[u] += a * Ws[(size_t)c * kcap + j];
+    for (int q = 0; q < TM / 8; ++q) {
+      const int m = warp + 8 * q;
+      if (m < TM) {
+        const long k = row0 + m;
+        const unsigned f = fl[m];
+        for (int c = lane; c < ncap; c += 32)
+          As[(size_t)m * lda + c] = (k < nrows && livec[c]) ? src.template loadT<T>(cols[c], k, f) : T(0);
       }
     }
+    __syncthreads();
+    for (int jb = 0; jb < kpad; jb += 32) {
+      const int j0 = jb + 4 * jg;
+      if (j0 < kpad) {
+        T acc[RPT][4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = j0 + u * nstrip;
-      if (j < kcap) Os[(size_t)m * (kcap + 1) + j] = (double)acc[u];
+        for (int q = 0; q < RPT; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[q][u] = T(0);
+        const T* arow = As + (size_t)(mp * RPT) * lda;
+#pragma unroll 4
+        for (int c = 0; c < ncap; ++c) {
+          T w[4];
+          ld4(Ws + (size_t)c * kpad + j0, w);
+#pragma unroll
+          for (int q = 0; q < RPT; ++q) {
+            const T a = arow[(size_t)q * lda + c];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[q][u] += a * w[u];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; ++q)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) Os[(size_t)(mp * RPT + q) * kpad + j0 + u] = acc[q][u];
+      }
+    }
+    __syncthreads();
+    // epilogue: (a) one warp per row for J* = o . vJ in arithmetic T, (b) one thread per row
+    // for the row scalars (FP64), (c) coalesced writes of the output rows
+    if (vJ) {
+      for (int mm = warp; mm < TM; mm += nwarps) {
+        const T* o = Os + (size_t)mm * kpad;
+        T js = T(0);
+        for (int j = lane; j < kcap; j += 32) js += o[j] * vJs[j];
+        js = warp_sum(js);
+        if (lane == 0) rowv[2 * TM + mm] = (double)js;
+      }
+      __syncthreads();
+    }
+    for (int m = tid; m < TM; m += blockDim.x) {
+      const long k = row0 + m;
+      double sc = 0.0, ex = 0.0, e0 = 0.0, e1 = 0.0;
+      if (k < nrows) epi.prep(k, vJ ? rowv[2 * TM + m] : 0.0, sc, ex, e0, e1);
+      rowv[m] = sc;
+      rowv[TM + m] = ex;
+      e0t += e0;
+      e1t += e1;
+    }
+    __syncthreads();
+    const int width = kcap + (Epi::kExtra ? 1 : 0);
+    for (int mm = warp; mm < TM; mm += nwarps) {
+      const long k = row0 + mm;
+      if (k >= nrows) break;
+      const T* o = Os + (size_t)mm * kpad;
+      const T sc = (T)rowv[mm];
+      const double ex = rowv[TM + mm];
+      for (int j = lane; j < width; j += 32) {
+        if (j < kcap) epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))(sc * o[j]);
+        else epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))ex;
+      }
     }
   }
-  __syncthreads();
-  if (threadIdx.x < TM) {
-    const long k = row0 + threadIdx.x;
-    double sc = 0.0, ex = 0.0, e0 = 0.0, e1 = 0.0;
-    if (k < nrows) epi.prep(k, Os + (size_t)threadIdx.x * (kcap + 1), kcap, sc, ex, e0, e1);
-    rowv[threadIdx.x] = sc;
-    rowv[TM + threadIdx.x] = ex;
-    rowv[2 * TM + threadIdx.x] = e0;
-    rowv[3 * TM + threadIdx.x] = e1;
-  }
-  __syncthreads();
-  const int width = kcap + (Epi::kExtra ? 1 : 0);
-  for (int idx = threadIdx.x; idx < TM * width; idx += blockDim.x) {
-    const int mm = idx / width, j = idx - mm * width;
-    const long k = row0 + mm;
-    if (k >= nrows) continue;
-    const double v = (j < kcap) ? rowv[mm] * Os[(size_t)mm * (kcap + 1) + j] : rowv[TM + mm];
-    epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))v;
-  }
-  if (partials && threadIdx.x == 0) {
-    double s0 = 0.0, s1 = 0.0;
-    for (int mm = 0; mm < TM; ++mm) {
-      s0 += rowv[2 * TM + mm];
-      s1 += rowv[3 * TM + mm];
+  if (partials) {
+    // fixed-order reduction of the per-thread partials
+    __syncthreads();
+    red[2 * tid] = e0t;
+    red[2 * tid + 1] = e1t;
+    __syncthreads();
+    if (tid == 0) {
+      double s0 = 0.0, s1 = 0.0;
+      for (int t = 0; t < (int)blockDim.x; ++t) {
+        s0 += red[2 * t];
+        s1 += red[2 * t + 1];
+      }
+      partials[2 * (size_t)blockIdx.x] = s0;
+      partials[2 * (size_t)blockIdx.x + 1] = s1;
     }
-    partials[2 * (size_t)blockIdx.x] = s0;
-    partials[2 * (size_t)blockIdx.x + 1] = s1;
   }
+}
+
+// Persistent grid of the update pass (also the number of energy partials it writes).
+template <typename T, int TM, class Src, class Epi>
+inline long update_grid(int num_sms, int ncap, int kcap, long nrows) {
+  const size_t smem = update_smem_bytes<T, TM, Src, Epi>(ncap, kcap);
+  cudaFuncSetAttribute(k_update<T, TM, Src, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update<T, TM, Src, Epi>, 256, smem) != cudaSuccess ||
+      occ < 1)
+    occ = 1;
+  const long ntiles = (nrows + TM - 1) / TM;
+  long g = (long)num_sms * occ;
+  return g < ntiles ? g : (ntiles > 0 ? ntiles : 1);
 }
 
 }  // namespace ttk

@@ -12,7 +12,11 @@ namespace ttk {
 namespace {
 
 constexpr double kPi = 3.14159265358979323846;
-constexpr int kTM = 32;   // rows per update tile
+// rows per update tile: FP32 tiles of 64 rows (two output rows per thread), FP64 of 32
+template <typename T>
+struct UpdTM {
+  static constexpr int value = sizeof(T) == 8 ? 32 : 64;
+};
 // rows per TSQR block over the merged core: FP64 registers hold 32 rows per column, FP32 64
 template <typename T>
 struct BigBR {
@@ -138,15 +142,18 @@ static void fill_stencil(SrcStencil<S>& src, const tt_plan* p, const S* Z, int r
   src.bcval = p->bcval;
 }
 
+// Launches the persistent update pass; *grid_out (if given) receives the number of CTAs, i.e.
+// of energy partial pairs written.
 template <typename T, class Src, class Epi>
-static tt_status launch_update(cudaStream_t s, const Src& src, LivePattern lp, long nrows, const double* W,
-                               int kcap, const Epi& epi, double* partials) {
-  const size_t smem = update_smem_bytes<T, kTM>(lp.ncap(), kcap);
+static tt_status launch_update(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows,
+                               const double* W, int kcap, const Epi& epi, double* partials, long* grid_out) {
+  constexpr int TM = UpdTM<T>::value;
+  const size_t smem = update_smem_bytes<T, TM, Src, Epi>(lp.ncap(), kcap);
   if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
-  cudaFuncSetAttribute(k_update<T, kTM, Src, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  const long grid = (nrows + kTM - 1) / kTM;
+  const long grid = update_grid<T, TM, Src, Epi>(num_sms, lp.ncap(), kcap, nrows);
+  if (grid_out) *grid_out = grid;
   TimerScope scope(kUpdate, s);
-  k_update<T, kTM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials); count_launch();
+  k_update<T, TM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -225,8 +232,8 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   job.RZ = RZ;
   tt_status st = small_round(s, ctx->num_sms, job, ws);
   if (st != TT_OK || ws.dry) return st;
-  st = launch_update<T>(s, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
-                             EpiPlain<S>{(S*)x->core[0], K1}, nullptr);
+  st = launch_update<T>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
+                        EpiPlain<S>{(S*)x->core[0], K1}, nullptr, nullptr);
   if (st != TT_OK) return st;
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
   k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b.core1, b.core2,
@@ -248,9 +255,10 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   const int R1 = lp1.ncap();
   RoundBufs b1 = take_round_bufs<T>(ws, ctx->num_sms, d, R1, N, n1, n2, K1, K2, K1);
   S* Zsrc = ws.take<S>((size_t)N * (K1 + 1));
-  const long ngrid = (N + kTM - 1) / kTM;
+  const long ngrid = (N + 31) / 32;  // bounds the persistent update grids (tiles of >= 32 rows)
   double* part1 = ws.take<double>((size_t)2 * ngrid);
   double* part2 = ws.take<double>((size_t)2 * ngrid);
+  long ngrid1 = 0, ngrid2 = 0;
   double* part0 = ws.take<double>((size_t)((N + 255) / 256));
   double* sums = ws.take<double>(8);
   double* vJ0 = ws.take<double>(K1);
@@ -303,8 +311,8 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     j2.lp = lp2;
     return small_round(s, ctx->num_sms, j2, ws);
   }
-  st = launch_update<T>(s, src1, lp1, N, b1.W, K1,
-                             EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps}, part1);
+  st = launch_update<T>(s, ctx->num_sms, src1, lp1, N, b1.W, K1,
+                        EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps}, part1, &ngrid1);
   if (st != TT_OK) return st;
   k_save_ranks<<<1, 32, 0, s>>>(ctx->ctrl); count_launch();
   lp2.r_ptr = &ctx->ctrl->k[2];
@@ -327,16 +335,16 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   j2.vJ = b2.vJ;
   st = small_round(s, ctx->num_sms, j2, ws);
   if (st != TT_OK) return st;
-  st = launch_update<T>(s, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
-                             EpiFinal<S>{(S*)I->core[0], K1, b2.vJ}, part2);
+  st = launch_update<T>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
+                        EpiFinal<S>{(S*)I->core[0], K1, b2.vJ}, part2, &ngrid2);
   if (st != TT_OK) return st;
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
   k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b2.core1, b2.core2,
                                                             (S*)I->core[1], d == 3 ? (S*)I->core[2] : nullptr,
                                                             ctx->ctrl, I->rank); count_launch();
   if (energy) {
-    reduce_partials(s, part1, ngrid, 2, sums + 2, 1.0);
-    reduce_partials(s, part2, ngrid, 2, sums + 4, 1.0);
+    reduce_partials(s, part1, ngrid1, 2, sums + 2, 1.0);
+    reduce_partials(s, part2, ngrid2, 2, sums + 4, 1.0);
     k_energy_pack<<<1, 32, 0, s>>>(sums, sums + 2, sums + 4, 4.0 * kPi / p->c * p->dV, energy); count_launch();
   }
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
