@@ -26,6 +26,12 @@ sys.path.insert(0, ROOT)
 METRIC = "TT transport steps/s and core-contraction TFLOP/s at fixed tol, FP64 vs mixed"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
+# DRAM bytes (read + write) of one transport-sum TSQR leaf launch at r = 32: ncu capture of the
+# same kernel on the 96 x 96 x 64-group workload (589,824 rows), scaled to 1,048,576 rows.
+LEAF_TRAFFIC = {"mixed": (78.895360e6 + 29.995008e6) * 1048576 / 589824,
+                "fp64": (203.504640e6 + 5.422080e6) * 1048576 / 589824}
+LEAF_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tsqr_leaf on the 96x96 "
+                       "workload, scaled by rows to 128x128")
 
 
 def parse():
@@ -209,8 +215,8 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     for i in range(args.steps):
         rb, ra = r_seq[i][1], r_seq[i + 1][1]
         flops += counted_flops(N, rb, ra, ra)
-        R1, R2 = 5 * rb, ra + 1
-        leaf_flops += 2.0 * N * (R1 * R1 + R2 * R2)
+        R1 = 5 * rb  # transport-sum columns (Z and its 4 upwind images; vacuum: no inflow columns)
+        leaf_flops += 2.0 * N * R1 * R1
     ws = dist.get_world_size() if dist else 1
     out = {"value": ws * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
            "tflops": flops / (total_ms / 1e3) / 1e12,
@@ -224,10 +230,13 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     else:
         peak, src, bound = FP32_PEAK_TFLOPS, ("FP32 FMA units: 152 SMs x 128/clk x 2 flop x 2070 MHz "
                                               "(no FP32 entry in MEASURED_PEAKS.json)"), "alu"
-    out["roofline"] = {"kernel": "k_tsqr_leaf (Householder TSQR over the transport and source sums)",
+    traffic = LEAF_TRAFFIC.get(precision) if args.size == "full" else None
+    out["roofline"] = {"kernel": "k_tsqr_leaf over the transport sum (one launch per step, R1 = 5r columns)",
                        "bound": bound, "achieved": leaf_tf, "peak": peak, "unit": "TFLOP/s",
-                       "frac": (leaf_tf / peak) if leaf_tf else None, "traffic": None, "peak_source": src,
-                       "share": kms["tsqr_leaf"] / total_ms if total_ms else None}
+                       "frac": (leaf_tf / peak) if leaf_tf else None,
+                       "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None,
+                       "traffic_source": LEAF_TRAFFIC_SOURCE if traffic else None,
+                       "peak_source": src, "share": kms["tsqr_leaf"] / total_ms if total_ms else None}
     return out, x, energy
 
 
@@ -262,11 +271,13 @@ def run_ours(args):
     line = {"metric": METRIC, "value": R["value"], "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": R["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 passes over the merged core, f64 small cores" if head == "mixed" else "f64",
+            "dtype": "f32" if head == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": wl.name, "nx": wl.nx, "ny": wl.ny, "groups": wl.ngroup,
                        "ordinates": [wl.ntheta, wl.nphi], "tol": wl.tol, "rmax": wl.rmax,
-                       "precision": head, "state_dtype": "f32" if head == "mixed" else "f64",
+                       "precision": ("mixed: f32 passes over the merged core, f64 small cores"
+                                     if head == "mixed" else "fp64"),
+                       "state_dtype": "f32" if head == "mixed" else "f64",
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "tflops": R["tflops"], "roofline": R["roofline"],

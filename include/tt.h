@@ -106,13 +106,15 @@ tt_status tt_context_destroy(tt_context *ctx);
  * later call records CUDA events on the context stream around its hot kernels, grouped as
  * TT_TIMER_* categories.  Launch counts are always collected. */
 typedef enum {
-  TT_TIMER_TSQR_LEAF = 0,   /* leaf pass of the tall-skinny QR over the merged core        */
+  TT_TIMER_TSQR_LEAF = 0,   /* leaf pass of the tall-skinny QR over the merged core (the
+                               transport sum in tt_step, the tensor itself in tt_round)    */
   TT_TIMER_TSQR_MERGE = 1,  /* merge tree of the R factors                                 */
   TT_TIMER_SMALL = 2,       /* small-core sweep (QRs, Jacobi SVDs, rank decisions)         */
   TT_TIMER_UPDATE = 3,      /* update pass Z_new = Z_sum W (and the fused source step)     */
-  TT_TIMER_OTHER = 4        /* everything else (counted only)                              */
+  TT_TIMER_OTHER = 4,       /* everything else (counted only)                              */
+  TT_TIMER_TSQR_LEAF_SOURCE = 5  /* leaf pass over the source sum (second rounding of tt_step) */
 } tt_timer;
-#define TT_TIMER_COUNT 5
+#define TT_TIMER_COUNT 6
 tt_status tt_context_set_timing(tt_context *ctx, int enable);
 
 /* Synchronise the context stream and report, per tt_timer category, the summed kernel time

@@ -31,7 +31,7 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc")
-TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other")
+TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
 
 class TTError(RuntimeError):

@@ -153,7 +153,7 @@ tt_status tt_context_counters(tt_context* ctx, double* ms, int64_t* launches, in
   ttk::Instr* in = static_cast<ttk::Instr*>(ctx->instr);
   set_device(ctx);
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
-  double acc[ttk::kNumCat] = {0, 0, 0, 0, 0};
+  double acc[ttk::kNumCat] = {};
   for (const auto& r : in->recs) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return TT_ERR_CUDA;

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(256) k_tsqr_merge(LivePattern lp, int nin, con
 // (ncap x ncap, row-major, upper triangular) inside ws_a or ws_b.
 template <typename T, int BR, class Src>
 tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows, int max_leaves,
-                   double* ws_a, double* ws_b, double** Rfinal) {
+                   double* ws_a, double* ws_b, double** Rfinal, int leaf_cat = kTsqrLeaf) {
   const int ncap = lp.ncap();
   const size_t smem = tsqr_smem_bytes<T, BR>(ncap);
   if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
@@ -320,7 +320,7 @@ tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, 
   cudaFuncSetAttribute(k_tsqr_leaf<T, BR, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k_tsqr_merge<T, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   {
-    TimerScope scope(kTsqrLeaf, s);
+    TimerScope scope(leaf_cat, s);
     k_tsqr_leaf<T, BR, Src><<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
   }
   TimerScope scope(kTsqrMerge, s);

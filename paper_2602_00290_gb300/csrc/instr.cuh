@@ -7,11 +7,11 @@
 
 namespace ttk {
 
-enum TimerCat { kTsqrLeaf = 0, kTsqrMerge = 1, kSmall = 2, kUpdate = 3, kOther = 4, kNumCat = 5 };
+enum TimerCat { kTsqrLeaf = 0, kTsqrMerge = 1, kSmall = 2, kUpdate = 3, kOther = 4, kTsqrLeafSrc = 5, kNumCat = 6 };
 
 struct Instr {
   bool timing = false;
-  long launches[kNumCat] = {0, 0, 0, 0, 0};
+  long launches[kNumCat] = {};
   int active = -1;  // category of the open scope (scopes do not nest)
   struct Rec {
     int cat;

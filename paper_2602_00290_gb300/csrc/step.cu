@@ -319,7 +319,8 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- second rounding: [D^-1 Z_new, g]
   k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0); count_launch();
   double* RZ2 = nullptr;
-  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, BigLeaves<T>::per_sm * ctx->num_sms, b2.tsqr_a, b2.tsqr_b, &RZ2);
+  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, BigLeaves<T>::per_sm * ctx->num_sms, b2.tsqr_a, b2.tsqr_b, &RZ2,
+                                    kTsqrLeafSrc);
   if (st != TT_OK) return st;
   SmallJob j2 = j1;
   j2.lp = lp2;
