@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--size", default="full", choices=["full", "medium", "small"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="plane", choices=["plane", "batched"],
+                    help="plane: the 128x128 single-problem step (the headline line); batched: the "
+                         "256-problem batch stepped as one CUDA graph (a separate measurement)")
+    ap.add_argument("--nprob", type=int, default=256)
+    ap.add_argument("--batch-scale", type=int, default=1)
+    ap.add_argument("--streams", type=int, default=16)
     return ap.parse_args()
 
 
@@ -335,10 +341,64 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """Independent problems of uneven shape (Nx = Ny in 32..192, G in 16..96, 8x16..16x32
+    ordinates, r_max 8..48, x- inflow) stepped together through tt_batch_step (one CUDA graph per
+    step); reports batch steps/s and problem steps/s for the chosen precision(s)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2602_00290_gb300 import _build
+    _build.build()
+    import paper_2602_00290_gb300 as tt
+    from paper_2602_00290_gb300.workloads import batch_config3
+
+    wls = batch_config3(args.nprob, seed=3, scale=args.batch_scale)
+    ctx = tt.Context()
+    plans = [tt.Plan(ctx, wl) for wl in wls]
+    rows = sum(w.nrow for w in wls)
+    unknowns = sum(w.nrow * w.ntheta * w.nphi for w in wls)
+    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    out = {"metric": "batched TT transport steps/s", "unit": "batch steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+           "config": {"workload": f"batch of {len(wls)} independent 2-D problems", "seed": 3,
+                      "scale": args.batch_scale, "rows": rows, "full_grid_unknowns": unknowns,
+                      "streams": args.streams}}
+    for prec in precs:
+        dtype = "f64" if prec == "fp64" else "f32"
+        states = [tt.initial_state(p, [w.rmax, w.rmax], dtype) for p, w in zip(plans, wls)]
+        b = tt.Batch(ctx, plans, states, [w.tol for w in wls], [w.rmax for w in wls], prec, args.streams)
+        b.step(max(args.warmup, 1))
+        b.sync()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(ctx.stream)
+        b.step(args.steps)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        b.sync()
+        ms = e0.elapsed_time(e1)
+        info = b.info()
+        ranks = [s.ranks()[1:-1] for s in states]
+        out[prec] = {"value": args.steps / (ms / 1e3), "ms_per_step": ms / args.steps,
+                     "problem_steps_per_s": len(wls) * args.steps / (ms / 1e3),
+                     "gpu_launches_per_step": info["launches_per_step"],
+                     "workspace_gb": info["workspace_bytes"] / 1e9,
+                     "state_gb": sum(c.numel() * c.element_size() for s in states for c in s.cores) / 1e9,
+                     "mean_rank": float(sum(r[0] for r in ranks)) / len(ranks)}
+        b.close()
+        del states
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_ours(args)
 
 

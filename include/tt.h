@@ -182,6 +182,35 @@ tt_status tt_apply_transport(tt_context *ctx, const tt_plan *plan, const tt_tens
 tt_status tt_step(tt_context *ctx, const tt_plan *plan, tt_tensor *I, double tol, int32_t rmax,
                   tt_precision prec, double *energy_dev);
 
+/* ---- Batched stepping of independent problems (many plans and states, one CUDA graph) ----
+ * Each problem's step is the tt_step of the paper's step-then-truncate scheme (Sec. 2.1 source
+ * update, Sec. 3.1 rounding, Appendix A transport); the batching itself has no counterpart in
+ * the paper.  A batch steps nprob independent problems together: plans[i] with state states[i] (descriptor
+ * copied; the cores stay owned by the caller and must stay allocated until tt_batch_destroy),
+ * tolerance tol[i] and rank cap rmax[i], all at precision prec.  Each problem runs exactly the
+ * launch sequence of tt_step on its own device control block and workspace region (sized once
+ * here by dry runs and allocated as one buffer); problems are spread over nstreams streams
+ * (<= 0: 16), largest first onto the least-loaded stream, so that the latency-bound small-core
+ * phases of different problems overlap.  The cooperative Jacobi of the FP64 path runs as a
+ * single CTA per problem inside a batch (concurrent problems never wait on one another).
+ * Same argument checks as tt_step (TT_ERR_ARG, TT_ERR_SHAPE, TT_ERR_CAPACITY). */
+typedef struct tt_batch tt_batch;
+tt_status tt_batch_create(tt_context *ctx, int32_t nprob, const tt_plan *const *plans, const tt_tensor *states,
+                          const double *tol, const int32_t *rmax, tt_precision prec, int32_t nstreams,
+                          tt_batch **out);
+/* Advance every problem of the batch by nsteps time steps, asynchronously on the context stream.
+ * The first call captures one batched step as a CUDA graph (so it must not itself be made under
+ * an outer stream capture); every step is a replay of that graph.  Device-detected errors are
+ * latched per problem and reported by tt_batch_sync. */
+tt_status tt_batch_step(tt_batch *b, int32_t nsteps);
+/* Synchronise the context stream; status_out[nprob] (nullable) receives each problem's latched
+ * status; returns the first non-OK one. */
+tt_status tt_batch_sync(tt_batch *b, int32_t *status_out);
+/* Kernel launches in one captured batched step (-1 before the first tt_batch_step), total
+ * workspace bytes, streams used.  Each pointer is nullable. */
+tt_status tt_batch_info(const tt_batch *b, int64_t *launches_per_step, size_t *workspace_bytes, int32_t *nstreams);
+tt_status tt_batch_destroy(tt_batch *b);
+
 /* *out_dev <- <x, y> like tt_dot, for callers that cannot allocate device memory: programs
  * that reserve a fixed device-memory budget up front and may not grow it, and code that must
  * not block while it runs (a real-time loop, a host callback), where cudaMalloc/cudaFree can

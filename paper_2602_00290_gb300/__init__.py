@@ -11,6 +11,7 @@ Functions keep the C names: ``tt_step``, ``tt_round``, ``tt_apply_transport``,
 from __future__ import annotations
 
 import ctypes
+import sys
 import os
 from typing import List, Optional, Sequence
 
@@ -30,7 +31,8 @@ PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED}
 EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sync", "tt_workspace_query",
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
-           "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc")
+           "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
+           "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy")
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
 
@@ -92,6 +94,14 @@ def lib():
             "tt_context_counters": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
             "tt_context_diagnostics": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int],
             "tt_dot_noalloc": [vp, ctypes.POINTER(_Tensor), ctypes.POINTER(_Tensor), vp],
+            "tt_batch_create": [vp, ctypes.c_int32, ctypes.POINTER(vp), ctypes.POINTER(_Tensor),
+                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                ctypes.c_int32, ctypes.POINTER(vp)],
+            "tt_batch_step": [vp, ctypes.c_int32],
+            "tt_batch_sync": [vp, ctypes.POINTER(ctypes.c_int32)],
+            "tt_batch_info": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
+                              ctypes.POINTER(ctypes.c_int32)],
+            "tt_batch_destroy": [vp],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -159,6 +169,9 @@ class Context:
             self.handle = None
 
     def __del__(self):
+        # no CUDA teardown while the interpreter shuts down (the driver may already be gone)
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -272,6 +285,9 @@ class Plan:
             self.handle = None
 
     def __del__(self):
+        # no CUDA teardown while the interpreter shuts down (the driver may already be gone)
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
@@ -320,6 +336,57 @@ def tt_dot_noalloc(stream, x: TT, y: TT, out):
     _check(lib().tt_dot_noalloc(h, ctypes.byref(x._struct()), ctypes.byref(y._struct()),
                                 ctypes.c_void_p(out.data_ptr())), "tt_dot_noalloc")
     return out
+
+
+class Batch:
+    """Independent problems stepped together (tt_batch_*): plans[i] with states[i] (TT objects,
+    kept alive by the batch), tolerances and rank caps per problem, one precision."""
+
+    def __init__(self, ctx: Context, plans, states, tol, rmax, prec="fp64", nstreams=0):
+        n = len(plans)
+        assert len(states) == n
+        tol = [float(t) for t in (tol if hasattr(tol, "__len__") else [tol] * n)]
+        rmax = [int(r) for r in (rmax if hasattr(rmax, "__len__") else [rmax] * n)]
+        self.ctx, self.plans, self.states = ctx, list(plans), list(states)
+        self._structs = (_Tensor * n)(*[s._struct() for s in states])
+        hp = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+        h = ctypes.c_void_p()
+        _check(lib().tt_batch_create(ctx.handle, n, hp, self._structs, (ctypes.c_double * n)(*tol),
+                                     (ctypes.c_int32 * n)(*rmax), PRECISIONS[prec], int(nstreams), ctypes.byref(h)),
+               "tt_batch_create")
+        self.handle = h
+        self.n = n
+
+    def step(self, nsteps=1):
+        _check(lib().tt_batch_step(self.handle, int(nsteps)), "tt_batch_step")
+
+    def sync(self):
+        """Per-problem latched statuses (raises on the first error)."""
+        st = (ctypes.c_int32 * self.n)()
+        rc = lib().tt_batch_sync(self.handle, st)
+        _check(rc, "tt_batch_sync")
+        return list(st)
+
+    def info(self):
+        n = ctypes.c_int64()
+        b = ctypes.c_size_t()
+        k = ctypes.c_int32()
+        _check(lib().tt_batch_info(self.handle, ctypes.byref(n), ctypes.byref(b), ctypes.byref(k)), "tt_batch_info")
+        return {"launches_per_step": n.value, "workspace_bytes": b.value, "streams": k.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tt_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        # no CUDA teardown while the interpreter shuts down (the driver may already be gone)
+        if sys.is_finalizing():
+            return
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tt_round(ctx: Context, x: TT, tol: float, rmax: int, prec="fp64"):

@@ -108,6 +108,8 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->ws = nullptr;
   ctx->ws_bytes = 0;
   ctx->instr = new ttk::Instr();
+  ctx->coop_grid_max = 0;
+  ctx->tsqr_leaf_cap = 0;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {

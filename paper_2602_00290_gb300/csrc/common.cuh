@@ -96,6 +96,8 @@ struct tt_context {
   int num_sms;
   int smem_optin;
   void* instr;  // ttk::Instr, opt-in counters and kernel timers
+  int coop_grid_max;  // > 0: cap on the CTAs of a cooperative launch (concurrent streams)
+  int tsqr_leaf_cap;  // > 0: cap on the TSQR leaves over the merged core (batched problems)
 };
 
 struct tt_plan {

@@ -673,9 +673,10 @@ __global__ void k_jacobi_write_v(int n, const double* __restrict__ V, const int*
 // Warps take the n/2 pairs of each round; one barrier per round.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restrict__ R, double* __restrict__ U,
-                                                    double* __restrict__ raw, int maxsweep) {
+                                                    double* __restrict__ raw, int maxsweep, T* gwork) {
   extern __shared__ __align__(16) unsigned char jrt_smem[];
-  T* At = reinterpret_cast<T*>(jrt_smem);  // column c at At[c * n]
+  // column c at At[c * n]: in shared memory, or in global scratch when n x n does not fit
+  T* At = gwork ? gwork : reinterpret_cast<T*>(jrt_smem);
   __shared__ int rot_flag;
   __shared__ float red[33];
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) At[idx] = (T)R[idx];
@@ -858,12 +859,18 @@ void reduce_partials(cudaStream_t s, const double* partials, long nblocks, int s
 template <int E>
 static cudaError_t launch_coop(int grid, int m, int n, double* A, double* V, DevCtrl* ctrl, int maxsweep,
                                cudaStream_t s) {
+  // a single CTA is always co-resident with itself: plain launch (capturable in any graph)
+  if (grid == 1) {
+    k_coop_jacobi<E><<<1, 256, 0, s>>>(m, n, A, V, ctrl, maxsweep);
+    return cudaGetLastError();
+  }
   void* args[] = {&m, &n, &A, &V, &ctrl, &maxsweep};
   return cudaLaunchCooperativeKernel((const void*)k_coop_jacobi<E>, dim3(grid), dim3(256), args, 0, s);
 }
 
 tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, double* V, double* sigma, double* U,
-                      int ldu, int ncols_out, double* Vout, int* perm, double* tmp, DevCtrl* ctrl) {
+                      int ldu, int ncols_out, double* Vout, int* perm, double* tmp, DevCtrl* ctrl,
+                      int grid_max) {
   if (m > 16 * 256) return TT_ERR_UNSUPPORTED;
   // barrier state, abort flag and sweep counters start at zero for every launch
   const size_t off = offsetof(DevCtrl, bar_count);
@@ -878,6 +885,7 @@ tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, doub
   int grid = npairs;
   const int resident = num_sms * (occ > 0 ? occ : 1);
   if (grid > resident) grid = resident;
+  if (grid_max > 0 && grid > grid_max) grid = grid_max;
   if (grid < 1) grid = 1;
   const int maxsweep = 40;
   cudaError_t e;
@@ -904,7 +912,7 @@ tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, doub
 // cooperative Jacobi sweep on its transpose copy: sigma (n, sorted) and Vout (n x n,
 // row-major, column j for sigma_j).
 static tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const double* M, Bump& ws, double* sigma,
-                           double* Vout, DevCtrl* ctrl) {
+                           double* Vout, DevCtrl* ctrl, int grid_max) {
   double* At = ws.take<double>((size_t)m * n);
   double* V = ws.take<double>((size_t)n * n);
   double* tmp = ws.take<double>(n);
@@ -912,7 +920,7 @@ static tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const doub
   if (ws.dry) return TT_OK;
   k_transpose<<<(unsigned)(((long)m * n + 255) / 256 < 1024 ? ((long)m * n + 255) / 256 : 1024), 256, 0, s>>>(
       m, n, M, At); count_launch();
-  return coop_jacobi(s, num_sms, m, n, At, V, sigma, nullptr, 0, 0, Vout, perm, tmp, ctrl);
+  return coop_jacobi(s, num_sms, m, n, At, V, sigma, nullptr, 0, 0, Vout, perm, tmp, ctrl, grid_max);
 }
 
 // V[:, :K] (nv x ldv, row-major) <- Q and sig[j] = |T_jj| of V[:, :K] = Q T, by CholeskyQR2
@@ -958,16 +966,18 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   double* U = ws.take<double>((size_t)cols * cols);
   double* P = ws.take<double>((size_t)rows * cols);
   double* tmp = ws.take<double>(cols);
+  const size_t at_bytes = sizeof(float) * (size_t)cols * cols;
+  const bool in_smem = at_bytes <= 200 * 1024;
+  float* gwork = in_smem ? nullptr : ws.take<float>((size_t)cols * cols);
   *U_out = U;
   *P_out = P;
   if (ws.dry) return TT_OK;
   double* R = nullptr;
   tt_status st = run_tsqr<float, 64>(s, num_sms, src, lp, rows, 8, a, b, &R);
   if (st != TT_OK) return st;
-  const size_t smem = sizeof(float) * (size_t)cols * cols;
-  if (smem > 200 * 1024) return TT_ERR_UNSUPPORTED;
-  cudaFuncSetAttribute(k_jacobi_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_jacobi_rt<float><<<1, 1024, smem, s>>>(cols, R, U, raw, 40); count_launch();
+  const size_t smem = in_smem ? at_bytes : 0;
+  if (in_smem) cudaFuncSetAttribute(k_jacobi_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_jacobi_rt<float><<<1, 1024, smem, s>>>(cols, R, U, raw, 40, gwork); count_launch();
   k_rank_perm<<<1, 1024, 0, s>>>(cols, raw, perm); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
@@ -1057,7 +1067,7 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
     // the only bond: SVD of Y (R x n1)
     double* sig = ws.take<double>(n1);
     double* V = ws.take<double>((size_t)n1 * n1);
-    st = svd_right(s, num_sms, R, n1, Y, ws, sig, V, j.ctrl);
+    st = svd_right(s, num_sms, R, n1, Y, ws, sig, V, j.ctrl, j.coop_grid_max);
     if (st != TT_OK || ws.dry) return st;
     k_decide<<<1, 32, 0, s>>>(sig, n1, 1, 2, j.tol, j.rmax, j.K1cap, j.nrowsZ, j.lp.r_ptr, j.lp.nblk,
                               j.lp.nextra, 1, nullptr, 0, 0, nullptr, 0, n1, j.ctrl, 0, nullptr); count_launch();
@@ -1073,7 +1083,7 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
   // bond 2: SVD of Y viewed as (R n1) x n2
   double* sig2 = ws.take<double>(n2);
   double* V2 = ws.take<double>((size_t)n2 * n2);
-  st = svd_right(s, num_sms, R * n1, n2, Y, ws, sig2, V2, j.ctrl);
+  st = svd_right(s, num_sms, R * n1, n2, Y, ws, sig2, V2, j.ctrl, j.coop_grid_max);
   if (st != TT_OK) return st;
   const int nv = n1 * K2;
   double* Y2 = ws.take<double>((size_t)R * nv);
@@ -1093,7 +1103,8 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
   int* perm1 = ws.take<int>(R);
   double* V1 = ws.take<double>((size_t)nv * K1);
   if (ws.dry) return TT_OK;
-  st = coop_jacobi(s, num_sms, nv, R, Y2, nullptr, sig1, V1, K1, K1 < R ? K1 : R, nullptr, perm1, tmp1, j.ctrl);
+  st = coop_jacobi(s, num_sms, nv, R, Y2, nullptr, sig1, V1, K1, K1 < R ? K1 : R, nullptr, perm1, tmp1, j.ctrl,
+                   j.coop_grid_max);
   if (st != TT_OK) return st;
   k_decide<<<1, 32, 0, s>>>(sig1, R, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
                             nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, nullptr); count_launch();

@@ -23,6 +23,7 @@ struct Bump {
 
 // Inputs/outputs of one small-core sweep (all FP64, capacity layout).
 struct SmallJob {
+  int coop_grid_max;  // > 0: cap on the CTAs of the cooperative Jacobi
   int d;          // 2 or 3
   int n1, n2;     // angular mode sizes (n2 = 1 for d = 2)
   long nrowsZ;    // N_Z (bounds the rank of the merged-core unfolding)
@@ -77,5 +78,6 @@ namespace ttk {
 // With V != null the rotations are accumulated in V (n x n) and Vout (row-major n x n,
 // column j the right singular vector of sigma_j) is written.
 tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, double* V, double* sigma, double* U,
-                      int ldu, int ncols_out, double* Vout, int* perm, double* tmp, DevCtrl* ctrl);
+                      int ldu, int ncols_out, double* Vout, int* perm, double* tmp, DevCtrl* ctrl,
+                      int grid_max = 0);
 }  // namespace ttk

@@ -157,6 +157,14 @@ static tt_status launch_update(cudaStream_t s, int num_sms, const Src& src, Live
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
+// Cap on the TSQR leaves over the merged core: a full wave of resident CTAs, or the context's
+// own cap (a batch gives each problem a share of the GPU in proportion to its rows).
+template <typename T>
+inline int leaf_cap(const tt_context* ctx) {
+  const int full = BigLeaves<T>::per_sm * ctx->num_sms;
+  return (ctx->tsqr_leaf_cap > 0 && ctx->tsqr_leaf_cap < full) ? ctx->tsqr_leaf_cap : full;
+}
+
 // Workspace carving shared by dry runs (size queries) and real runs.
 struct RoundBufs {
   double* tsqr_a;
@@ -171,10 +179,10 @@ struct RoundBufs {
 };
 
 template <typename T>
-static RoundBufs take_round_bufs(Bump& ws, int num_sms, int d, int R, long nrows, int n1, int n2, int K1, int K2,
-                                 int rcapin1) {
+static RoundBufs take_round_bufs(Bump& ws, int num_sms, int max_leaves, int d, int R, long nrows, int n1, int n2,
+                                 int K1, int K2, int rcapin1) {
   RoundBufs b;
-  const long L = tsqr_max_leaves<T, BigBR<T>::value>(num_sms, R, nrows, BigLeaves<T>::per_sm * num_sms);
+  const long L = tsqr_max_leaves<T, BigBR<T>::value>(num_sms, R, nrows, max_leaves);
   b.tsqr_a = ws.take<double>((size_t)L * R * R);
   b.tsqr_b = ws.take<double>((size_t)((L + 1) / 2) * R * R);
   b.Bbase = ws.take<double>((size_t)rcapin1 * n1 * n2);
@@ -196,7 +204,7 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   const int K1 = x->rcap[1], K2 = (d == 3) ? x->rcap[2] : 1;
   LivePattern lp{x->rank + 1, K1, 1, 0};
   const int R = lp.ncap();
-  RoundBufs b = take_round_bufs<T>(ws, ctx->num_sms, d, R, N, n1, n2, K1, K2, K1);
+  RoundBufs b = take_round_bufs<T>(ws, ctx->num_sms, leaf_cap<T>(ctx), d, R, N, n1, n2, K1, K2, K1);
   SmallJob job{};
   job.d = d;
   job.n1 = n1;
@@ -218,12 +226,13 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   job.Bnew = b.Bnew;
   job.vJ = b.vJ;
   job.ctrl = ctx->ctrl;
+  job.coop_grid_max = ctx->coop_grid_max;
   job.mixed = (sizeof(T) == 4);
   double* domega_ones = ws.take<double>((size_t)n1 * n2);
   job.domega = domega_ones;
   double* RZ = nullptr;
   if (!ws.dry) {
-    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, BigLeaves<T>::per_sm * ctx->num_sms, b.tsqr_a,
+    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, leaf_cap<T>(ctx), b.tsqr_a,
                                          b.tsqr_b, &RZ);
     if (st != TT_OK) return st;
     right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, b.Bbase);
@@ -253,7 +262,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- first rounding: the transport sum, never materialised
   LivePattern lp1{I->rank + 1, K1, p->nterm + 1, p->nbc};
   const int R1 = lp1.ncap();
-  RoundBufs b1 = take_round_bufs<T>(ws, ctx->num_sms, d, R1, N, n1, n2, K1, K2, K1);
+  RoundBufs b1 = take_round_bufs<T>(ws, ctx->num_sms, leaf_cap<T>(ctx), d, R1, N, n1, n2, K1, K2, K1);
   S* Zsrc = ws.take<S>((size_t)N * (K1 + 1));
   const long ngrid = (N + 31) / 32;  // bounds the persistent update grids (tiles of >= 32 rows)
   double* part1 = ws.take<double>((size_t)2 * ngrid);
@@ -285,6 +294,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   j1.Bnew = b1.Bnew;
   j1.vJ = b1.vJ;
   j1.ctrl = ctx->ctrl;
+  j1.coop_grid_max = ctx->coop_grid_max;
   j1.mixed = (sizeof(T) == 4);
   double* RZ1 = nullptr;
   if (!ws.dry) {
@@ -297,7 +307,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     }
     k_b0_transport<<<256, 256, 0, s>>>(K1, p->nterm, p->nbc, n1, n2, b1.Bbase, p->fac1, p->fac2, p->bc_term_dev,
                                        b1.B0); count_launch();
-    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, src1, lp1, N, BigLeaves<T>::per_sm * ctx->num_sms, b1.tsqr_a, b1.tsqr_b, &RZ1);
+    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, src1, lp1, N, leaf_cap<T>(ctx), b1.tsqr_a, b1.tsqr_b, &RZ1);
     if (st != TT_OK) return st;
   }
   j1.RZ = RZ1;
@@ -305,7 +315,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   if (st != TT_OK) return st;
   // ---- source step fused into the write of the rounded transport update
   LivePattern lp2{nullptr, K1, 1, 1};
-  RoundBufs b2 = take_round_bufs<T>(ws, ctx->num_sms, d, lp2.ncap(), N, n1, n2, K1, K2, K1);
+  RoundBufs b2 = take_round_bufs<T>(ws, ctx->num_sms, leaf_cap<T>(ctx), d, lp2.ncap(), N, n1, n2, K1, K2, K1);
   if (ws.dry) {
     SmallJob j2 = j1;
     j2.lp = lp2;
@@ -319,7 +329,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- second rounding: [D^-1 Z_new, g]
   k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0); count_launch();
   double* RZ2 = nullptr;
-  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, BigLeaves<T>::per_sm * ctx->num_sms, b2.tsqr_a, b2.tsqr_b, &RZ2,
+  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, leaf_cap<T>(ctx), b2.tsqr_a, b2.tsqr_b, &RZ2,
                                     kTsqrLeafSrc);
   if (st != TT_OK) return st;
   SmallJob j2 = j1;

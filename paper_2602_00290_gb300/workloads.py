@@ -180,6 +180,32 @@ def plane_config1(nx: int = 128, ny: int = 128, G: int = 64, ntheta: int = 16, n
         rho_kappa_a=ka, rho_kappa_s=0.1 * ka, tol=tol, rmax=rmax, steps=steps, seed=seed)
 
 
+def batch_config3(nprob: int = 256, seed: int = 3, scale: int = 1, tol: float = 1e-6,
+                  steps: int = 20) -> list:
+    """Independent 2-D problems of uneven shape stepped as one batch: Nx = Ny ~ U{32, 64, ..., 192},
+    G ~ U{16, 32, ..., 96}, ordinates ~ U{8x16, 12x24, 16x32}, r_max ~ U{8, ..., 48}, each with its
+    own seeded density blobs and line factors, and isotropic Planck inflow on the x- face at
+    T_b ~ U[0.1, 1] (the rest vacuum).  `scale` > 1 divides the cell counts and group counts by
+    `scale` and halves the ordinates (floor 4 x 8), for parity runs the oracle can finish."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(nprob):
+        n = int(rng.choice([32, 64, 96, 128, 160, 192]))
+        G = int(rng.choice([16, 32, 48, 64, 80, 96]))
+        nth, nph = [(8, 16), (12, 24), (16, 32)][int(rng.integers(3))]
+        rmax = int(rng.integers(8, 49))
+        Tb = float(rng.uniform(0.1, 1.0))
+        pseed = int(rng.integers(1, 1 << 30))
+        if scale > 1:
+            n, G = max(4, n // scale), max(2, G // scale)
+            nth, nph = max(4, nth // 2), max(8, nph // 2)
+            rmax = max(2, min(rmax // scale + 2, nth))
+        wl = plane_config1(nx=n, ny=n, G=G, ntheta=nth, nphi=nph, rmax=rmax, tol=tol, steps=steps, seed=pseed)
+        out.append(replace(wl, name=f"batch{i}_{n}x{n}_g{G}_{nth}x{nph}_r{rmax}",
+                           inflow_temperature=(Tb, None, None, None, None, None)))
+    return out
+
+
 def random_tt(n: Sequence[int], ranks: Sequence[int], seed: int, scale: float = 1.0):
     """Cores with iid N(0,1) entries, core k of shape (r_{k-1}, n_k, r_k)."""
     rng = np.random.default_rng(seed)
