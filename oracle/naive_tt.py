@@ -150,6 +150,36 @@ def round_tt(tt, tol, rmax=1 << 30, info=None):
     return cores
 
 
+def right_part(cores):
+    """Contraction of cores (r0, n_1, r_1) ... (r_{m-1}, n_m, 1) into an r0 x (n_1 ... n_m) matrix."""
+    B = cores[0]
+    for c in cores[1:]:
+        B = np.tensordot(B, c, axes=([B.ndim - 1], [0]))
+    return B.reshape(B.shape[0], -1)
+
+
+def round_tt_gram(tt, tol, rmax=1 << 30, info=None):
+    """Gram-based rounding of the first bond (the Gram method among the three rounding methods
+    of Sec. 3.1): the left unfolding A of the first core enters only through its Gram matrix
+    G = A^T A = V diag(lam) V^T, whose square root R = diag(lam^(1/2)) V^T stands in for the QR
+    factor (R^T R = A^T A, so every unfolding of X' = R x (cores 2..d) has the singular values and
+    right singular vectors of the same unfolding of X).  X' is rounded by round_tt; its new
+    cores 2..d are those of X, and the new first core is A projected onto the new right frame,
+    A (B_old B_new^T) (the Q U S of the QR route).  Accuracy: Gram squares the condition number,
+    so singular values below about sqrt(eps) |X| are not resolved."""
+    d = len(tt)
+    r0, n, r1 = tt[0].shape
+    A = tt[0].reshape(r0 * n, r1)
+    lam, V = np.linalg.eigh(A.T @ A)
+    R = np.sqrt(np.clip(lam, 0.0, None))[:, None] * V.T
+    small = [R.reshape(1, r1, r1)] + [c.copy() for c in tt[1:]]
+    out = round_tt(small, tol, rmax, info)
+    Bold = right_part(tt[1:])
+    Bnew = right_part(out[1:])
+    first = (A @ (Bold @ Bnew.T)).reshape(r0, n, Bnew.shape[0])
+    return [first] + out[1:]
+
+
 # --- merged-topology transport and source (upwind, vacuum or Dirichlet inflow) -------------
 
 def angular_terms(coef):
@@ -256,11 +286,13 @@ def source_sum(tt, coef):
     return add(scaled, iso)
 
 
-def step(tt, coef, tol, rmax, info=None):
-    """One step-then-truncate time step: transport, round, source, round (end of Sec. 3.1)."""
+def step(tt, coef, tol, rmax, info=None, rounding="svd"):
+    """One step-then-truncate time step: transport, round, source, round (end of Sec. 3.1).
+    rounding: "svd" (round_tt) or "gram" (round_tt_gram), used for both roundings."""
+    rnd = round_tt_gram if rounding == "gram" else round_tt
     i1, i2 = {}, {}
-    x = round_tt(transport_sum(tt, coef), tol, rmax, i1)
-    x = round_tt(source_sum(x, coef), tol, rmax, i2)
+    x = rnd(transport_sum(tt, coef), tol, rmax, i1)
+    x = rnd(source_sum(x, coef), tol, rmax, i2)
     if info is not None:
         info["transport_round"] = i1
         info["source_round"] = i2

@@ -175,3 +175,64 @@ def test_compression_counts_parameters():
     x = random_tt(n, [5, 3], seed=1)
     params = sum(c.size for c in x)
     assert nt.compression(7, 3, 4, 8, 5, 3) == pytest.approx(np.prod(n) / params, rel=1e-15)
+
+
+# --- Gram-based rounding (the Gram method of Sec. 3.1) -------------------------------------
+
+@pytest.mark.parametrize("tol", [1e-2, 1e-4, 3e-6])
+def test_round_gram_equals_svd_rounding_on_resolved_spectra(tol):
+    """Where every kept singular value is far above sqrt(eps)|X|, the Gram route is the SVD
+    route: same ranks, same result to round-off."""
+    n = [233, 5, 9]
+    a = nt.add_many([nt.scale(random_tt(n, [3, 2], seed=20 + i), 10.0 ** -i) for i in range(4)])
+    i1, i2 = {}, {}
+    w = nt.round_tt(a, tol, 20, i1)
+    g = nt.round_tt_gram(a, tol, 20, i2)
+    assert nt.ranks(g) == nt.ranks(w)
+    assert np.linalg.norm(nt.full(g) - nt.full(w)) <= 1e-12 * np.linalg.norm(nt.full(w))
+    for b1, b2 in zip(i1["bonds"], i2["bonds"]):
+        k = b1["rank"]
+        assert np.allclose(b2["sigma"][:k], b1["sigma"][:k], rtol=1e-10, atol=0)
+
+
+def test_round_gram_known_spectrum_and_exact_rank():
+    """A matrix with a prescribed spectrum (d = 2): Gram rounding recovers the singular values
+    to 1e-10 relative while they stay above 1e-4 of the largest; at a tolerance above its
+    sqrt(eps) noise floor (1e-6) it keeps the exact rank of a rank-6 tensor and reconstructs it."""
+    rng = np.random.default_rng(5)
+    m, k = 300, 6
+    U, _ = np.linalg.qr(rng.standard_normal((m, k)))
+    V, _ = np.linalg.qr(rng.standard_normal((40, k)))
+    s = 10.0 ** -np.arange(k) * 0.5
+    A = (U * s) @ V.T
+    tt = [A.reshape(1, m, 40), np.eye(40).reshape(40, 40, 1)]
+    info = {}
+    g = nt.round_tt_gram(tt, 1e-6, 40, info)
+    assert nt.ranks(g) == [1, k, 1]
+    assert np.allclose(info["bonds"][0]["sigma"][:4], s[:4], rtol=1e-10, atol=0)
+    assert np.linalg.norm(nt.full(g).reshape(m, 40) - A) <= 1e-10 * np.linalg.norm(A)
+
+
+def test_round_gram_loses_the_squared_condition_tail():
+    """The paper's caution: forming A^T A squares the condition number.  Singular values near
+    1e-10 |A| are not resolved by the Gram route (they are by the SVD route)."""
+    rng = np.random.default_rng(6)
+    m = 200
+    U, _ = np.linalg.qr(rng.standard_normal((m, 5)))
+    V, _ = np.linalg.qr(rng.standard_normal((30, 5)))
+    s = np.array([1.0, 1e-2, 1e-4, 1e-10, 1e-11])
+    tt = [((U * s) @ V.T).reshape(1, m, 30), np.eye(30).reshape(30, 30, 1)]
+    i1, i2 = {}, {}
+    nt.round_tt(tt, 1e-14, 30, i1)
+    nt.round_tt_gram(tt, 1e-14, 30, i2)
+    sv, sg = i1["bonds"][0]["sigma"], i2["bonds"][0]["sigma"]
+    assert np.allclose(sv[:5], s, rtol=1e-5, atol=0)
+    assert np.allclose(sg[:3], s[:3], rtol=1e-8, atol=0)
+    assert abs(sg[3] - s[3]) > 1e-2 * s[3]
+
+
+def test_round_gram_zero_tensor():
+    z = [np.zeros((1, 20, 3)), np.zeros((3, 4, 2)), np.zeros((2, 5, 1))]
+    g = nt.round_tt_gram(z, 1e-6)
+    assert nt.ranks(g) == [1, 1, 1, 1]
+    assert not np.any(nt.full(g))
