@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--size", default="full", choices=["full", "medium", "small"])
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gram", action="store_true", help="skip the FP64 leg with Gram rounding")
     ap.add_argument("--workload", default="plane", choices=["plane", "batched"],
                     help="plane: the 128x128 single-problem step (the headline line); batched: the "
                          "256-problem batch stepped as one CUDA graph (a separate measurement)")
@@ -172,8 +173,9 @@ def run_reference(args):
     return 0
 
 
-def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index):
+def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index, rounding="tsqr"):
     """W warm-up then K timed tt_step calls for one precision; returns (line fields, state)."""
+    ctx.set_rounding(rounding)
     dtype = "f64" if precision == "fp64" else "f32"
     rcap = [wl.rmax, wl.rmax]
     x = tt.initial_state(plan, rcap, dtype)
@@ -243,6 +245,7 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
                        "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None,
                        "traffic_source": LEAF_TRAFFIC_SOURCE if traffic else None,
                        "peak_source": src, "share": kms["tsqr_leaf"] / total_ms if total_ms else None}
+    ctx.set_rounding("tsqr")
     return out, x, energy
 
 
@@ -271,6 +274,9 @@ def run_ours(args):
     results, states = {}, {}
     for prec in precs:
         results[prec], states[prec], energy = time_precision(tt, torch, ctx, plan, wl, args, prec, dist, vis)
+    if "fp64" in precs and not args.no_gram:
+        results["fp64_gram"], states["fp64_gram"], _ = time_precision(tt, torch, ctx, plan, wl, args, "fp64", dist,
+                                                                      vis, rounding="gram")
     head = "mixed" if "mixed" in results else "fp64"
     R = results[head]
     x = states[head]
@@ -298,6 +304,13 @@ def run_ours(args):
         Em = tt.tt_energy_density(ctx, plan, states["mixed"]).cpu().numpy()
         Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()
         line["mixed_vs_fp64_energy_density_rel_err"] = float(np.linalg.norm(Em - Ed) / np.linalg.norm(Ed))
+    if "fp64_gram" in results:
+        G = results["fp64_gram"]
+        line["fp64_gram"] = {k: G[k] for k in ("value", "ms_per_step", "tflops", "breakdown_ms_per_step",
+                                               "gpu_launches", "ranks", "jacobi")}
+        Eg = tt.tt_energy_density(ctx, plan, states["fp64_gram"]).cpu().numpy()
+        Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()
+        line["fp64_gram"]["energy_density_rel_err_vs_tsqr"] = float(np.linalg.norm(Eg - Ed) / np.linalg.norm(Ed))
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     if args.e2e_steps > 0:
         stream = ctx.stream

@@ -90,6 +90,15 @@ typedef struct {
 } tt_problem;
 
 typedef struct tt_context tt_context;
+/* Factor of the merged core in the first sweep of every rounding (tt_round, tt_step).
+ * TT_ROUND_TSQR: Householder TSQR (the SVD-based rounding of Sec. 3.1; the default).
+ * TT_ROUND_GRAM: Gram-based (Sec. 3.1 lists it among the solver's rounding methods): the FP64 Gram
+ * matrix G = A^T A of the merged core's unfolding (virtual transport sum included) and
+ * R = diag(lambda^(1/2)) V^T from its Jacobi eigen-decomposition replace the TSQR's R; the rest
+ * of the rounding is unchanged.  Forming G squares the condition number (the paper's caution):
+ * singular values below about 1e-8 |X| are not resolved, so use it at tolerances above that. */
+typedef enum { TT_ROUND_TSQR = 0, TT_ROUND_GRAM = 1 } tt_rounding;
+
 typedef struct tt_plan tt_plan;
 
 /* Status text for a tt_status value (static storage, never NULL). */
@@ -116,6 +125,10 @@ typedef enum {
 } tt_timer;
 #define TT_TIMER_COUNT 6
 tt_status tt_context_set_timing(tt_context *ctx, int enable);
+
+/* Select the rounding method of the context (TT_ERR_ARG for an unknown method).  With
+ * TT_ROUND_GRAM the TT_TIMER_TSQR_LEAF(_SOURCE) categories time the Gram pass instead. */
+tt_status tt_context_set_rounding(tt_context *ctx, tt_rounding method);
 
 /* Synchronise the context stream and report, per tt_timer category, the summed kernel time
  * in milliseconds (ms[TT_TIMER_COUNT], nullable) and the number of kernel launches

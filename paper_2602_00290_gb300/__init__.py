@@ -27,12 +27,13 @@ TT_F64, TT_F32 = 0, 1
 TT_PREC_FP64, TT_PREC_MIXED = 0, 1
 TT_QUAD_GAUSS_LEGENDRE_MU, TT_QUAD_LATLONG_MIDPOINT = 0, 1
 PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED}
+ROUNDINGS = {"tsqr": 0, "gram": 1}
 
 EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sync", "tt_workspace_query",
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
-           "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy")
+           "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding")
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
 
@@ -102,6 +103,7 @@ def lib():
             "tt_batch_info": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_size_t),
                               ctypes.POINTER(ctypes.c_int32)],
             "tt_batch_destroy": [vp],
+            "tt_context_set_rounding": [vp, ctypes.c_int],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -146,6 +148,10 @@ class Context:
 
     def sync(self):
         _check(lib().tt_sync(self.handle), "tt_sync")
+
+    def set_rounding(self, method: str):
+        """"tsqr" (Householder TSQR, default) or "gram" (Gram matrix + Jacobi square root)."""
+        _check(lib().tt_context_set_rounding(self.handle, ROUNDINGS[method]), "tt_context_set_rounding")
 
     def set_timing(self, enable: bool):
         _check(lib().tt_context_set_timing(self.handle, 1 if enable else 0), "tt_context_set_timing")

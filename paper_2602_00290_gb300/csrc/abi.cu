@@ -110,6 +110,7 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->instr = new ttk::Instr();
   ctx->coop_grid_max = 0;
   ctx->tsqr_leaf_cap = 0;
+  ctx->rounding = TT_ROUND_TSQR;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
@@ -141,6 +142,12 @@ tt_status tt_context_destroy(tt_context* ctx) {
   for (cudaEvent_t e : in->pool) cudaEventDestroy(e);
   delete in;
   delete ctx;
+  return TT_OK;
+}
+
+tt_status tt_context_set_rounding(tt_context* ctx, tt_rounding method) {
+  if (!ctx || (method != TT_ROUND_TSQR && method != TT_ROUND_GRAM)) return TT_ERR_ARG;
+  ctx->rounding = method;
   return TT_OK;
 }
 

@@ -98,6 +98,7 @@ struct tt_context {
   void* instr;  // ttk::Instr, opt-in counters and kernel timers
   int coop_grid_max;  // > 0: cap on the CTAs of a cooperative launch (concurrent streams)
   int tsqr_leaf_cap;  // > 0: cap on the TSQR leaves over the merged core (batched problems)
+  int rounding;       // tt_rounding of tt_round / tt_step
 };
 
 struct tt_plan {

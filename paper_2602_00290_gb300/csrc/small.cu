@@ -911,8 +911,8 @@ tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, doub
 // SVD of an m x n row-major matrix M (right singular vectors and singular values) by the
 // cooperative Jacobi sweep on its transpose copy: sigma (n, sorted) and Vout (n x n,
 // row-major, column j for sigma_j).
-static tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const double* M, Bump& ws, double* sigma,
-                           double* Vout, DevCtrl* ctrl, int grid_max) {
+tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const double* M, Bump& ws, double* sigma,
+                    double* Vout, DevCtrl* ctrl, int grid_max) {
   double* At = ws.take<double>((size_t)m * n);
   double* V = ws.take<double>((size_t)n * n);
   double* tmp = ws.take<double>(n);

@@ -77,6 +77,10 @@ namespace ttk {
 // thresholds (at most 40 sweeps, else TT_ERR_TIMEOUT is latched).
 // With V != null the rotations are accumulated in V (n x n) and Vout (row-major n x n,
 // column j the right singular vector of sigma_j) is written.
+// SVD of an m x n row-major matrix M by the cooperative one-sided Jacobi on its transpose: sigma (n,
+// decreasing) and Vout (n x n row-major, column j the right singular vector of sigma_j).
+tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const double* M, Bump& ws, double* sigma,
+                    double* Vout, DevCtrl* ctrl, int grid_max);
 tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, double* V, double* sigma, double* U,
                       int ldu, int ncols_out, double* Vout, int* perm, double* tmp, DevCtrl* ctrl,
                       int grid_max = 0);

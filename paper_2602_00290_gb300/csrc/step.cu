@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include "bigpass.cuh"
+#include "gram.cuh"
 #include "small.cuh"
 #include "step.cuh"
 
@@ -231,10 +232,16 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   double* domega_ones = ws.take<double>((size_t)n1 * n2);
   job.domega = domega_ones;
   double* RZ = nullptr;
-  if (!ws.dry) {
+  if (ctx->rounding == TT_ROUND_GRAM) {
+    tt_status st = gram_factor(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, ws, ctx->ctrl,
+                               ctx->coop_grid_max, &RZ);
+    if (st != TT_OK) return st;
+  } else if (!ws.dry) {
     tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, leaf_cap<T>(ctx), b.tsqr_a,
                                          b.tsqr_b, &RZ);
     if (st != TT_OK) return st;
+  }
+  if (!ws.dry) {
     right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, b.Bbase);
     cudaMemsetAsync(domega_ones, 0, sizeof(double) * (size_t)n1 * n2, s);
   }
@@ -307,6 +314,12 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     }
     k_b0_transport<<<256, 256, 0, s>>>(K1, p->nterm, p->nbc, n1, n2, b1.Bbase, p->fac1, p->fac2, p->bc_term_dev,
                                        b1.B0); count_launch();
+  }
+  const bool gram = (ctx->rounding == TT_ROUND_GRAM);
+  if (gram) {
+    tt_status st = gram_factor(s, ctx->num_sms, src1, lp1, N, ws, ctx->ctrl, ctx->coop_grid_max, &RZ1);
+    if (st != TT_OK) return st;
+  } else if (!ws.dry) {
     tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, src1, lp1, N, leaf_cap<T>(ctx), b1.tsqr_a, b1.tsqr_b, &RZ1);
     if (st != TT_OK) return st;
   }
@@ -319,6 +332,11 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   if (ws.dry) {
     SmallJob j2 = j1;
     j2.lp = lp2;
+    if (gram) {
+      double* RZ2 = nullptr;
+      st = gram_factor(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, ws, ctx->ctrl, ctx->coop_grid_max, &RZ2);
+      if (st != TT_OK) return st;
+    }
     return small_round(s, ctx->num_sms, j2, ws);
   }
   st = launch_update<T>(s, ctx->num_sms, src1, lp1, N, b1.W, K1,
@@ -329,8 +347,12 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- second rounding: [D^-1 Z_new, g]
   k_b0_source<<<64, 256, 0, s>>>(K1, nang, b1.Bnew, b2.B0); count_launch();
   double* RZ2 = nullptr;
-  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, leaf_cap<T>(ctx), b2.tsqr_a, b2.tsqr_b, &RZ2,
-                                    kTsqrLeafSrc);
+  if (gram)
+    st = gram_factor(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, ws, ctx->ctrl, ctx->coop_grid_max, &RZ2,
+                     kTsqrLeafSrc);
+  else
+    st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, leaf_cap<T>(ctx), b2.tsqr_a,
+                                      b2.tsqr_b, &RZ2, kTsqrLeafSrc);
   if (st != TT_OK) return st;
   SmallJob j2 = j1;
   j2.lp = lp2;
