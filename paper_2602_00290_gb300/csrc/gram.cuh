@@ -1,7 +1,7 @@
 // Gram-based factor of the merged core (the Gram method among the paper's rounding methods,
-// Sec. 3.1): G = A^T A of the (possibly virtual) N_Z x R matrix A in FP64, then the square root
-// R = diag(lambda^(1/2)) V^T from the eigen-decomposition of G, which stands in for the TSQR's
-// R factor (the small-core sweep uses R only through R^T R).  Forming G squares the condition
+// Sec. 3.1): G = A^T A of the (possibly virtual) N_Z x R matrix A in FP64, then a square root
+// R of G (R^T R = G, from a diagonally pivoted Cholesky), which stands in for the TSQR's R factor
+// (the small-core sweep uses R only through R^T R).  Forming G squares the condition
 // number: singular values below about sqrt(eps) |A| are not resolved.
 #pragma once
 #include "bigpass.cuh"
@@ -129,14 +129,69 @@ __global__ void k_gram_reduce(int ncap, int nsplit, int npairs, const double* __
   G[idx] = s;
 }
 
-// RZ[j][c] = sqrt(max(sigma_j, 0)) V[c][j]  (V: n x n row-major, column j for sigma_j)
-__global__ void k_gram_root(int n, const double* __restrict__ sigma, const double* __restrict__ V,
-                            double* __restrict__ RZ) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= n * n) return;
-  const int j = idx / n, c = idx - (idx / n) * n;
-  const double sj = sigma[j] > 0.0 ? sqrt(sigma[j]) : 0.0;
-  RZ[idx] = sj * V[(size_t)c * n + j];
+// Diagonally pivoted Cholesky of the PSD Gram matrix G (n x n, overwritten): P^T G P = R^T R,
+// stopped once the largest remaining pivot is at the round-off level of the largest diagonal
+// entry (the rank of a rank-deficient sum).  Writes RZ = R P^T (n x n row-major, rows beyond the
+// rank zero), so that RZ^T RZ = G.  One CTA; G stays in global memory (L2).
+__global__ void __launch_bounds__(1024) k_gram_pchol(int n, double* __restrict__ G, double* __restrict__ RZ,
+                                                     int* __restrict__ perm) {
+  __shared__ double rowj[512];
+  __shared__ double redv[32];
+  __shared__ int redi[32];
+  __shared__ double d0;
+  __shared__ int pj;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < n; i += blockDim.x) perm[i] = i;
+  for (long i = tid; i < (long)n * n; i += blockDim.x) RZ[i] = 0.0;
+  __syncthreads();
+  const double thr_rel = 4.0 * n * 2.220446049250313e-16;
+  for (int j = 0; j < n; ++j) {
+    // largest remaining diagonal entry
+    double best = -1.0;
+    int bi = j;
+    for (int q = j + tid; q < n; q += blockDim.x) {
+      const int a = perm[q];
+      const double v = G[(size_t)a * n + a];
+      if (v > best) { best = v; bi = q; }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { redv[warp] = best; redi[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double b = redv[0];
+      int q = redi[0];
+      for (int w = 1; w < nw; ++w)
+        if (redv[w] > b || (redv[w] == b && redi[w] < q)) { b = redv[w]; q = redi[w]; }
+      if (j == 0) d0 = b;
+      const int t = perm[j];
+      perm[j] = perm[q];
+      perm[q] = t;
+      pj = (b > thr_rel * d0 && b > 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!pj) break;  // the rest is round-off: rows j.. of RZ stay zero
+    const int aj = perm[j];
+    const double rjj = sqrt(G[(size_t)aj * n + aj]);
+    const double inv = 1.0 / rjj;
+    for (int q = j + tid; q < n; q += blockDim.x) {
+      const int a = perm[q];
+      const double r = (q == j) ? rjj : G[(size_t)aj * n + a] * inv;
+      rowj[q] = r;
+      RZ[(size_t)j * n + a] = r;
+    }
+    __syncthreads();
+    const int m = n - j - 1;
+    for (long idx = tid; idx < (long)m * m; idx += blockDim.x) {
+      const int q1 = j + 1 + (int)(idx / m), q2 = j + 1 + (int)(idx % m);
+      G[(size_t)perm[q1] * n + perm[q2]] -= rowj[q1] * rowj[q2];
+    }
+    __syncthreads();
+  }
 }
 
 // Square-root factor RZ (ncap x ncap, row-major) of the Gram matrix of the source's columns.
@@ -156,10 +211,10 @@ tt_status gram_factor(cudaStream_t s, int num_sms, const Src& src, LivePattern l
   rps = ((rps + kGramTM - 1) / kGramTM) * kGramTM;
   nsplit = (nrows + rps - 1) / rps;
   if (nsplit < 1) nsplit = 1;
+  if (ncap > 512) return TT_ERR_UNSUPPORTED;
   double* part = ws.take<double>((size_t)nsplit * npairs * kGramBlk * kGramBlk);
   double* G = ws.take<double>((size_t)ncap * ncap);
-  double* sig = ws.take<double>(ncap);
-  double* V = ws.take<double>((size_t)ncap * ncap);
+  int* perm = ws.take<int>(ncap);
   double* RZ = ws.take<double>((size_t)ncap * ncap);
   *RZ_out = RZ;
   if (!ws.dry) {
@@ -170,9 +225,8 @@ tt_status gram_factor(cudaStream_t s, int num_sms, const Src& src, LivePattern l
     const long nn = (long)ncap * ncap;
     k_gram_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(ncap, (int)nsplit, npairs, part, G); count_launch();
   }
-  tt_status st = svd_right(s, num_sms, ncap, ncap, G, ws, sig, V, ctrl, coop_grid_max);
-  if (st != TT_OK || ws.dry) return st;
-  k_gram_root<<<(ncap * ncap + 255) / 256, 256, 0, s>>>(ncap, sig, V, RZ); count_launch();
+  if (ws.dry) return TT_OK;
+  k_gram_pchol<<<1, 1024, 0, s>>>(ncap, G, RZ, perm); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
