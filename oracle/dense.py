@@ -44,7 +44,7 @@ class _Params(ctypes.Structure):
                 ("dir", ctypes.c_void_p * 3), ("domega", ctypes.c_void_p),
                 ("lam", ctypes.c_double * 3), ("acoef", ctypes.c_void_p),
                 ("scoef", ctypes.c_void_p), ("eps", ctypes.c_void_p),
-                ("inflow", ctypes.c_void_p * 6)]
+                ("inflow", ctypes.c_void_p * 6), ("flux", ctypes.c_int), ("alpha_local", ctypes.c_int)]
 
 
 def _ptr(a):
@@ -73,6 +73,8 @@ class DenseSolver:
         p.acoef, p.scoef, p.eps = _ptr(self._keep[4]), _ptr(self._keep[5]), _ptr(self._keep[6])
         for f in range(6):
             p.inflow[f] = _ptr(self._inflow[f])
+        p.flux = 1 if c.flux == "rusanov" else 0
+        p.alpha_local = 1 if c.alpha_local else 0
         self._p = p
         self._lib = _load()
 

@@ -13,6 +13,12 @@
  *   I^{m+1}= (I* + a eps + s J^{m+1}) / (1 + a + s)           s = c dt rho kappa_s
  *
  * Ghost cells hold the face's isotropic inflow spectrum, or 0 for vacuum.
+ *
+ * flux = 1 replaces the upwind flux by the Rusanov flux of Appendix A ('Value of n'):
+ * F_{i+1/2} = n (I_i + I_{i+1}) / 2 - alpha (I_{i+1} - I_i) / 2 with alpha = 1 (the largest
+ * speed, c |n| <= c), i.e. T I_i = lam [ n (I_{i+1} - I_{i-1}) / 2 - (I_{i+1} - 2 I_i + I_{i-1}) / 2 ],
+ * read with vacuum ghost cells (0) on every face.  alpha_local = 1 takes alpha = |n| per direction
+ * instead, which is the upwind flux again (a consistency check of the two schemes).
  * Layout: I[k * nang + q], merged row k = g + G*(ix + nx*(iy + ny*iz)), angle q.
  */
 #include <math.h>
@@ -31,6 +37,8 @@ typedef struct {
     const double *scoef;    /* per row: c dt rho kappa_s */
     const double *eps;      /* per row: emission epsilon_f(T) */
     const double *inflow[6];/* per face (x-,x+,y-,y+,z-,z+): G-spectrum or NULL (vacuum) */
+    int flux;               /* 0 upwind, 1 Rusanov (vacuum ghost cells) */
+    int alpha_local;        /* Rusanov with alpha = |n| (reduces to upwind) */
 } dense_params;
 
 static double ghost(const dense_params *p, int face, int g) {
@@ -66,6 +74,13 @@ int dense_step(const dense_params *p, const double *I, double *Iout, double *Ist
                 double acc = 0.0;
                 for (int ax = 0; ax < p->ndim; ++ax) {
                     double n = p->dir[ax][q];
+                    if (p->flux == 1) {
+                        const double lo = (idx[ax] > 0) ? I[(k - stride[ax]) * nang + q] : 0.0;
+                        const double hi = (idx[ax] < extent[ax] - 1) ? I[(k + stride[ax]) * nang + q] : 0.0;
+                        const double alpha = p->alpha_local ? fabs(n) : 1.0;
+                        acc += p->lam[ax] * (0.5 * n * (hi - lo) - 0.5 * alpha * (hi - 2.0 * v + lo));
+                        continue;
+                    }
                     if (n >= 0.0) {
                         double up = (idx[ax] > 0) ? I[(k - stride[ax]) * nang + q] : ghost(p, 2 * ax, g);
                         acc += p->lam[ax] * n * (v - up);

@@ -186,9 +186,22 @@ def angular_terms(coef):
     """Transport terms of the TT operator (Appendix A, 'Value of n').
 
     Returns a list of (axis, w, factors) where factors is one diagonal per angular core
-    such that n_axis * 1[n_axis (>=|<) 0] = prod of the factors over the angular nodes."""
+    such that n_axis * 1[n_axis (>=|<) 0] = prod of the factors over the angular nodes (upwind,
+    w = +1 / -1).  For the Rusanov flux the two terms of an axis are w = +2 (the central
+    difference, factors of the full n_axis) and w = -2 (the diffusion term, factors 1)."""
     d = coef.dirs
     terms = []
+    if getattr(coef, "flux", "upwind") == "rusanov":
+        if coef.ntheta > 0 and coef.nphi == 1 and "w" in d:
+            terms.append((0, +2, [d["mu"]]))
+            terms.append((0, -2, [np.ones_like(d["mu"])]))
+            return terms
+        mu, phi, st = d["mu"], d["phi"], d["sintheta"]
+        full = {0: [st, np.cos(phi)], 1: [st, np.sin(phi)], 2: [mu, np.ones(coef.nphi)]}
+        for ax in range(coef.ndim):
+            terms.append((ax, +2, full[ax]))
+            terms.append((ax, -2, [np.ones(coef.ntheta), np.ones(coef.nphi)]))
+        return terms
     if coef.ntheta > 0 and coef.nphi == 1 and "w" in d:   # planar slab, single mu core
         mu = d["mu"]
         terms.append((0, +1, [np.where(mu >= 0.0, mu, 0.0)]))
@@ -242,7 +255,11 @@ def transport_sum(tt, coef):
     idx = _cell_index(coef)
     for (ax, w, facs) in angular_terms(coef):
         lam = coef.lam[ax]
-        if w > 0:
+        if w == 2:      # Rusanov central part: lam n (I_{i+1} - I_{i-1}) / 2
+            DZ = 0.5 * (_shift_rows(Z, coef, ax, +1) - _shift_rows(Z, coef, ax, -1))
+        elif w == -2:   # Rusanov diffusion part: -lam (I_{i+1} - 2 I_i + I_{i-1}) / 2
+            DZ = -0.5 * (_shift_rows(Z, coef, ax, +1) - 2.0 * Z + _shift_rows(Z, coef, ax, -1))
+        elif w > 0:
             DZ = Z - _shift_rows(Z, coef, ax, -1)          # I_i - I_{i-1}
         else:
             DZ = _shift_rows(Z, coef, ax, +1) - Z          # I_{i+1} - I_i
@@ -250,6 +267,8 @@ def transport_sum(tt, coef):
         for j, f in enumerate(facs):
             cores.append(_apply_diag(tt[1 + j], f))
         summands.append(cores)
+        if abs(w) == 2:
+            continue    # Rusanov: vacuum ghost cells only
         face = 2 * ax + (0 if w > 0 else 1)
         b = coef.inflow[face]
         if b is not None:

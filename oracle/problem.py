@@ -37,6 +37,8 @@ class StepCoefficients:
     dA: np.ndarray             # face area per axis (3,)
     c: float
     dt: float
+    flux: str = "upwind"       # "upwind" or "rusanov" (Appendix A, 'Value of n')
+    alpha_local: bool = False  # Rusanov with the local speed |n_a| (reduces to upwind; a pin)
 
     @property
     def nrow(self):
@@ -64,9 +66,14 @@ def build(wl) -> StepCoefficients:
             inflow.append(planck.emission(float(Tb), wl.group_edges, wl.c, wl.a_rad))
     dV = float(np.prod(dx[:wl.ndim]))
     dA = np.array([dV / dx[a] for a in range(3)])
+    flux = getattr(wl, "flux", "upwind")
+    if flux not in ("upwind", "rusanov"):
+        raise ValueError(f"unknown flux {flux!r}")
+    if flux == "rusanov" and any(b is not None for b in inflow):
+        raise ValueError("the Rusanov flux is read with vacuum ghost cells only")
     return StepCoefficients(wl.ndim, wl.nx, wl.ny, wl.nz, wl.ngroup, wl.ntheta, wl.nphi,
                             lam, acoef, scoef, eps, inflow, quadrature.directions(wl),
-                            dV, dA, wl.c, wl.dt)
+                            dV, dA, wl.c, wl.dt, flux)
 
 
 def initial_rows(wl, coef: StepCoefficients) -> np.ndarray:
