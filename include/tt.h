@@ -63,6 +63,13 @@ typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_precision;
 
 typedef enum { TT_QUAD_GAUSS_LEGENDRE_MU = 0, TT_QUAD_LATLONG_MIDPOINT = 1 } tt_quadrature;
 
+/* Numerical flux of the transport operator (Appendix A, 'Value of n'; both give n = 2 d_X rank-1
+ * terms).  UPWIND: per axis the two one-sided differences times n_a 1[n_a >= 0] and n_a 1[n_a < 0].
+ * RUSANOV: per axis the central difference (I_{i+1} - I_{i-1})/2 times n_a and the isotropic
+ * diffusion term -(I_{i+1} - 2 I_i + I_{i-1})/2 (largest speed alpha = c), read with vacuum
+ * ghost cells: a Rusanov problem with an inflow face is TT_ERR_UNSUPPORTED. */
+typedef enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1 } tt_flux;
+
 typedef struct {
   int32_t d;                       /* number of cores, 2 or 3                               */
   int32_t n[TT_MAX_CORES];         /* mode sizes n_0..n_{d-1}                               */
@@ -87,6 +94,7 @@ typedef struct {
   const double *rho_kappa_a;       /* device double[N_X*G] per merged row                   */
   const double *rho_kappa_s;       /* device double[N_X*G] per merged row                   */
   double inflow_temperature[6];    /* faces x-,x+,y-,y+,z-,z+; < 0 means vacuum             */
+  int32_t flux;                    /* tt_flux                                               */
 } tt_problem;
 
 typedef struct tt_context tt_context;

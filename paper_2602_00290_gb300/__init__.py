@@ -57,7 +57,7 @@ class _Problem(ctypes.Structure):
                 ("c", ctypes.c_double), ("dt", ctypes.c_double), ("a_rad", ctypes.c_double),
                 ("group_edges", ctypes.c_void_p), ("temperature", ctypes.c_void_p),
                 ("rho_kappa_a", ctypes.c_void_p), ("rho_kappa_s", ctypes.c_void_p),
-                ("inflow_temperature", ctypes.c_double * 6)]
+                ("inflow_temperature", ctypes.c_double * 6), ("flux", ctypes.c_int32)]
 
 
 _lib = None
@@ -265,6 +265,7 @@ class Plan:
         for f in range(6):
             t = wl.inflow_temperature[f] if f < len(wl.inflow_temperature) else None
             p.inflow_temperature[f] = -1.0 if t is None else float(t)
+        p.flux = {"upwind": 0, "rusanov": 1}[getattr(wl, "flux", "upwind")]
         h = ctypes.c_void_p()
         _check(lib().tt_plan_create(ctx.handle, ctypes.byref(p), ctypes.byref(h)), "tt_plan_create")
         self.handle = h

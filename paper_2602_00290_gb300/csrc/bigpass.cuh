@@ -65,7 +65,7 @@ struct SrcStencil {
   int bc_term[kMaxTerms];  // operator of each inflow column
   const double* bcval;     // [nbc][G] signed lambda * inflow
   struct Col {
-    int kind;  // 0: Z, 1: operator image, 2: inflow column, 3: none
+    int kind;  // 0: Z, 1: upwind image, 2: inflow column, 3: none, 4/5: Rusanov central/diffusion
     int q, ax, w, b;
     double lam;
     float lamf;
@@ -78,7 +78,8 @@ struct SrcStencil {
       cc.kind = 0;
       cc.q = c;
     } else if (t <= nterm) {
-      cc.kind = 1;
+      const int wc = w[t - 1];
+      cc.kind = (wc == 2) ? 4 : (wc == -2) ? 5 : 1;
       cc.q = c - t * rcap;
       cc.ax = axis[t - 1];
       cc.w = w[t - 1];
@@ -99,6 +100,12 @@ struct SrcStencil {
     if (cc.kind == 3) return 0.0;
     const long s = stride[cc.ax];
     const int idx = (int)((k / s) % ext[cc.ax]);
+    if (cc.kind >= 4) {  // Rusanov (vacuum ghost cells)
+      const double lo = (idx > 0) ? (double)Z[(k - s) * ldz + cc.q] : 0.0;
+      const double hi = (idx < ext[cc.ax] - 1) ? (double)Z[(k + s) * ldz + cc.q] : 0.0;
+      if (cc.kind == 4) return -0.5 * cc.lam * (hi - lo);
+      return 0.5 * cc.lam * (hi - 2.0 * (double)Z[k * ldz + cc.q] + lo);
+    }
     if (cc.kind == 1) {
       const double zk = (double)Z[k * ldz + cc.q];
       double diff;
@@ -132,6 +139,13 @@ struct SrcStencil {
   __device__ __forceinline__ T loadT(const Col& cc, long k, unsigned fl) const {
     if (cc.kind == 0) return (T)Z[k * ldz + cc.q];
     if (cc.kind == 3) return T(0);
+    if (cc.kind >= 4) {  // Rusanov (vacuum ghost cells)
+      const T lamT = (sizeof(T) == 8) ? (T)cc.lam : (T)cc.lamf;
+      const T lo = ((fl >> (2 * cc.ax)) & 1u) ? (T)Z[(k - cc.s) * ldz + cc.q] : T(0);
+      const T hi = ((fl >> (2 * cc.ax + 1)) & 1u) ? (T)Z[(k + cc.s) * ldz + cc.q] : T(0);
+      if (cc.kind == 4) return T(-0.5) * lamT * (hi - lo);
+      return T(0.5) * lamT * (hi - T(2) * (T)Z[k * ldz + cc.q] + lo);
+    }
     if (cc.kind == 1) {
       const T lamT = (sizeof(T) == 8) ? (T)cc.lam : (T)cc.lamf;
       const T zk = (T)Z[k * ldz + cc.q];

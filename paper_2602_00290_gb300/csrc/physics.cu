@@ -66,6 +66,19 @@ __global__ void k_angular_factors(int d, int nterm, const int* axis, const int* 
   const int t = blockIdx.x;
   if (t >= nterm) return;
   const int ax = axis[t], ww = w[t];
+  if (ww == 2 || ww == -2) {
+    // Rusanov: the central term carries the full n_a, the diffusion term no angular factor
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+      const double m = mu[i];
+      fac1[t * n1 + i] = (ww < 0) ? 1.0 : ((d == 2 || ax == 2) ? m : sqrt(1.0 - m * m));
+    }
+    for (int p = threadIdx.x; p < n2; p += blockDim.x) {
+      double f = 1.0;
+      if (ww > 0 && d == 3 && ax < 2) f = (ax == 0) ? cos(phi[p]) : sin(phi[p]);
+      fac2[t * n2 + p] = f;
+    }
+    return;
+  }
   for (int i = threadIdx.x; i < n1; i += blockDim.x) {
     double m = mu[i], f;
     if (d == 2) {
@@ -221,11 +234,13 @@ tt_status physics_setup(tt_context* ctx, const tt_problem* p, tt_plan* plan) {
   int faces[kMaxTerms];
   double sgnlam[kMaxTerms];
   plan->nbc = 0;
+  const bool rusanov = (p->flux == TT_FLUX_RUSANOV);
   for (int t = 0; t < plan->nterm; ++t) {
     plan->term_axis[t] = t / 2;
-    plan->term_w[t] = (t % 2 == 0) ? +1 : -1;
+    // upwind: +1 / -1 (one-sided differences); Rusanov: +2 (central) / -2 (diffusion)
+    plan->term_w[t] = ((t % 2 == 0) ? +1 : -1) * (rusanov ? 2 : 1);
     const int face = 2 * (t / 2) + (t % 2);  // w=+ reads the minus-face ghost
-    if (p->inflow_temperature[face] >= 0.0) {
+    if (!rusanov && p->inflow_temperature[face] >= 0.0) {
       plan->bc_term[plan->nbc] = t;
       faces[plan->nbc] = face;
       sgnlam[plan->nbc] = (t % 2 == 0 ? 1.0 : -1.0) * plan->lam[t / 2];
