@@ -95,6 +95,13 @@ typedef struct {
   const double *rho_kappa_s;       /* device double[N_X*G] per merged row                   */
   double inflow_temperature[6];    /* faces x-,x+,y-,y+,z-,z+; < 0 means vacuum             */
   int32_t flux;                    /* tt_flux                                               */
+  const double *rho_cv;            /* device double[N_X] volumetric heat capacity rho c_v, or
+                                      NULL: the material temperature stays fixed.  Non-NULL
+                                      couples it (Sec. 2.1, Eq. Tupdate): every tt_step solves
+                                      the f(T^dagger) root per cell, uses epsilon(T^dagger) in
+                                      the source update and advances T by total energy
+                                      conservation with the rounded state's J^{m+1}.  The plan
+                                      then carries the material state of ONE problem.      */
 } tt_problem;
 
 typedef struct tt_context tt_context;
@@ -169,7 +176,9 @@ tt_status tt_plan_destroy(tt_plan *plan);
 /* Device arrays owned by the plan (valid until tt_plan_destroy), for inspection:
  * which = 0: emission per row (N_Z), 1: solid-angle weights (N_theta*N_phi),
  *         2: mu nodes (N_theta), 3: phi nodes (N_phi), 4: c*dt*rho*kappa_a per row,
- *         5: c*dt*rho*kappa_s per row, 6: inflow spectra [6][G] (0 for vacuum faces). */
+ *         5: c*dt*rho*kappa_s per row, 6: inflow spectra [6][G] (0 for vacuum faces),
+ *         7: material temperature per cell (N_X; advanced by tt_step when coupled),
+ *         8: T^dagger of the last coupled step per cell (N_X; TT_ERR_ARG when not coupled). */
 tt_status tt_plan_array(const tt_plan *plan, int which, const double **ptr, int64_t *len);
 
 /* y <- alpha * x + y by rank concatenation (TT addition, Sec. 3.1): ranks add.

@@ -57,7 +57,8 @@ class _Problem(ctypes.Structure):
                 ("c", ctypes.c_double), ("dt", ctypes.c_double), ("a_rad", ctypes.c_double),
                 ("group_edges", ctypes.c_void_p), ("temperature", ctypes.c_void_p),
                 ("rho_kappa_a", ctypes.c_void_p), ("rho_kappa_s", ctypes.c_void_p),
-                ("inflow_temperature", ctypes.c_double * 6), ("flux", ctypes.c_int32)]
+                ("inflow_temperature", ctypes.c_double * 6), ("flux", ctypes.c_int32),
+                ("rho_cv", ctypes.c_void_p)]
 
 
 _lib = None
@@ -266,6 +267,12 @@ class Plan:
             t = wl.inflow_temperature[f] if f < len(wl.inflow_temperature) else None
             p.inflow_temperature[f] = -1.0 if t is None else float(t)
         p.flux = {"upwind": 0, "rusanov": 1}[getattr(wl, "flux", "upwind")]
+        rcv = getattr(wl, "rho_cv", None)
+        if rcv is not None:
+            self._arrays.append(torch.as_tensor(np.asarray(rcv, dtype=np.float64), device=dev).contiguous())
+            p.rho_cv = self._arrays[-1].data_ptr()
+        else:
+            p.rho_cv = None
         h = ctypes.c_void_p()
         _check(lib().tt_plan_create(ctx.handle, ctypes.byref(p), ctypes.byref(h)), "tt_plan_create")
         self.handle = h
@@ -282,6 +289,14 @@ class Plan:
         if n.value == 0:
             return np.empty(0)
         return _wrap_device_ptr(ptr.value, n.value).cpu().numpy().copy()
+
+    def temperature(self):
+        """Material temperature per cell (advanced by tt_step when the problem is coupled)."""
+        return self.array(7)
+
+    def t_dagger(self):
+        """T^dagger of the last coupled step per cell."""
+        return self.array(8)
 
     def new_state(self, rcap: Sequence[int], dtype="f64"):
         return TT(self.n, rcap, dtype)

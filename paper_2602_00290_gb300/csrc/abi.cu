@@ -236,7 +236,8 @@ tt_status tt_plan_create(tt_context* ctx, const tt_problem* prob, tt_plan** out)
 
 tt_status tt_plan_destroy(tt_plan* p) {
   if (!p) return TT_ERR_ARG;
-  double* arrs[] = {p->eps, p->acoef, p->scoef, p->domega, p->mu, p->phi, p->fac1, p->fac2, p->inflow, p->bcval, p->edges};
+  double* arrs[] = {p->eps,    p->acoef,  p->scoef, p->domega, p->mu,     p->phi,  p->fac1,
+                    p->fac2,   p->inflow, p->bcval, p->edges,  p->temp,   p->rho_cv, p->tdag};
   for (double* a : arrs)
     if (a) cudaFree(a);
   if (p->bc_term_dev) cudaFree(p->bc_term_dev);
@@ -254,6 +255,10 @@ tt_status tt_plan_array(const tt_plan* p, int which, const double** ptr, int64_t
     case 4: *ptr = p->acoef; *len = p->nrow; break;
     case 5: *ptr = p->scoef; *len = p->nrow; break;
     case 6: *ptr = p->inflow; *len = 6 * (int64_t)p->G; break;
+    case 7: *ptr = p->temp; *len = (int64_t)p->nx * p->ny * p->nz; break;
+    case 8:
+      if (!p->coupled) return TT_ERR_ARG;
+      *ptr = p->tdag; *len = (int64_t)p->nx * p->ny * p->nz; break;
     default: return TT_ERR_ARG;
   }
   return TT_OK;

@@ -420,10 +420,12 @@ struct EpiFinal {
   SO* out;
   long ld;
   const double* vJ;
+  double* jout;  // optional: J of every final row (the coupled temperature update reads it)
   static constexpr bool kExtra = false;
   static constexpr bool kDot = true;
-  __device__ __forceinline__ void prep(long, double js, double& scale, double& extra, double& e0,
+  __device__ __forceinline__ void prep(long k, double js, double& scale, double& extra, double& e0,
                                        double& e1) const {
+    if (jout) jout[k] = js;
     scale = 1.0;
     extra = 0.0;
     e0 = js;

@@ -127,9 +127,18 @@ struct tt_plan {
   double* bcval;   // [nbc][G] signed lambda * inflow spectrum of each inflow column
   double* edges;   // [G+1]
   int* bc_term_dev;  // [kMaxTerms] operator index of each inflow column
+  double a_rad;
+  int coupled;       // material temperature advanced by tt_step (Sec. 2.1, Eq. Tupdate)
+  double* temp;      // [N_X] material temperature (coupled: state, else the fixed input)
+  double* rho_cv;    // [N_X] volumetric heat capacity (coupled only)
+  double* tdag;      // [N_X] T^dagger of the last step (coupled only)
 };
 
 // Internal entry points shared between translation units.
 namespace ttk {
 tt_status physics_setup(tt_context* ctx, const tt_problem* prob, tt_plan* plan);
+// Coupled temperature (physics.cu): T^dagger per cell from J* per row, writing plan->tdag and
+// epsilon(T^dagger) into plan->eps; then T^{m+1} from J* and the rounded state's J^{m+1}.
+tt_status coupled_t_dagger(cudaStream_t s, tt_plan* p, const double* jstar);
+tt_status coupled_t_update(cudaStream_t s, tt_plan* p, const double* jstar, const double* jnew);
 }

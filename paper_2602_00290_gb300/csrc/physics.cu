@@ -6,6 +6,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "instr.cuh"
 
 namespace ttk {
 namespace {
@@ -203,6 +204,92 @@ __global__ void k_bcval(int nbc, int G, const int* __restrict__ face, const doub
   }
 }
 
+// d epsilon_f / dT = 4 epsilon_f / T - (c a T^3 / 4 pi)(15/pi^4) [x^4/(e^x - 1)]_{x_lo}^{x_hi},
+// x = nu / T (the derivative of the Planck group integral, Eqs. Ttoeps1-2).
+__device__ double demission_dT(double T, double eps, double lo, double hi, double c, double a) {
+  if (!(T > 0.0)) return 0.0;
+  const double pref = c * a * T * T * T / (4.0 * kPi) * 15.0 / (kPi * kPi * kPi * kPi);
+  auto edge = [](double x) { return (x > 0.0 && x < 700.0) ? x * x * x * x / expm1(x) : 0.0; };
+  const double xl = lo / T, xh = isinf(hi) ? 0.0 : hi / T;
+  return 4.0 * eps / T - pref * ((isinf(hi) ? 0.0 : edge(xh)) - edge(xl));
+}
+
+// One warp per cell: T^dagger = root of f(T) = T^m + C sum_f w_f (J*_f - eps_f(T)) - T with
+// C = 4 pi / (c rho c_v), w_f = a_f / (1 + a_f) (the paper's f(T^dagger), Sec. 2.1), by Newton
+// steps kept inside a shrinking bracket [lo, hi] (f(lo) > 0 > f(hi)); then eps rows <- eps(T^dagger).
+__global__ void k_t_dagger(long ncell, int G, double c, double a, const double* __restrict__ edges,
+                           const double* __restrict__ Tm, const double* __restrict__ rho_cv,
+                           const double* __restrict__ acoef, const double* __restrict__ jstar,
+                           double* __restrict__ tdag, double* __restrict__ eps) {
+  __shared__ double b[kBern];
+  if (threadIdx.x == 0) bernoulli_over_factorial(b);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
+  for (long cell = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); cell < ncell; cell += warps) {
+    const double T0 = Tm[cell];
+    const double C = 4.0 * kPi / (c * rho_cv[cell]);
+    // f(T) and f'(T), lanes over groups
+    auto eval = [&](double T, double& f, double& df) {
+      double s = 0.0, ds = 0.0;
+      for (int g = lane; g < G; g += 32) {
+        const long k = (long)cell * G + g;
+        const double w = acoef[k] / (1.0 + acoef[k]);
+        const double e = emission(T, edges[g], edges[g + 1], c, a, b);
+        s += w * (jstar[k] - e);
+        ds += w * demission_dT(T, e, edges[g], edges[g + 1], c, a);
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        ds += __shfl_xor_sync(0xffffffffu, ds, o);
+      }
+      f = T0 + C * s - T;
+      df = -C * ds - 1.0;
+    };
+    double f, df;
+    eval(0.0, f, df);
+    double T = 0.0;
+    if (f > 0.0) {
+      double lo = 0.0, hi = T0 > 1e-3 ? T0 : 1e-3;
+      double fh, dh;
+      eval(hi, fh, dh);
+      for (int it = 0; it < 200 && fh > 0.0; ++it) {
+        lo = hi;
+        hi *= 2.0;
+        eval(hi, fh, dh);
+      }
+      T = 0.5 * (lo + hi);
+      for (int it = 0; it < 200; ++it) {
+        eval(T, f, df);
+        if (f > 0.0) lo = T; else hi = T;
+        double Tn = T - f / df;
+        if (!(Tn > lo && Tn < hi)) Tn = 0.5 * (lo + hi);
+        const double step = fabs(Tn - T);
+        T = Tn;
+        if (step <= 1e-15 * T || hi - lo <= 1e-15 * hi) break;
+      }
+    }
+    if (lane == 0) tdag[cell] = T;
+    for (int g = lane; g < G; g += 32) eps[(long)cell * G + g] = emission(T, edges[g], edges[g + 1], c, a, b);
+  }
+}
+
+// rho c_v (T^{m+1} - T^m) = (4 pi / c) sum_f (J*_f - J^{m+1}_f), one warp per cell.
+__global__ void k_t_update(long ncell, int G, double c, const double* __restrict__ rho_cv,
+                           const double* __restrict__ jstar, const double* __restrict__ jnew,
+                           double* __restrict__ T) {
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
+  for (long cell = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); cell < ncell; cell += warps) {
+    double s = 0.0;
+    for (int g = lane; g < G; g += 32) s += jstar[(long)cell * G + g] - jnew[(long)cell * G + g];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) T[cell] += 4.0 * kPi / (c * rho_cv[cell]) * s;
+  }
+}
+
 }  // namespace
 
 tt_status physics_setup(tt_context* ctx, const tt_problem* p, tt_plan* plan) {
@@ -262,6 +349,14 @@ tt_status physics_setup(tt_context* ctx, const tt_problem* p, tt_plan* plan) {
   TT_ALLOC(plan->inflow, 6 * G);
   TT_ALLOC(plan->bcval, plan->nbc * G);
   TT_ALLOC(plan->edges, G + 1);
+  const long ncell = (long)p->nx * p->ny * p->nz;
+  TT_ALLOC(plan->temp, ncell);
+  plan->a_rad = p->a_rad;
+  plan->coupled = (p->rho_cv != nullptr) ? 1 : 0;
+  if (plan->coupled) {
+    TT_ALLOC(plan->rho_cv, ncell);
+    TT_ALLOC(plan->tdag, ncell);
+  }
   if (cudaMalloc((void**)&plan->bc_term_dev, sizeof(int) * kMaxTerms) != cudaSuccess) return TT_ERR_CUDA;
 #undef TT_ALLOC
   // small host->device parameter blocks
@@ -283,6 +378,11 @@ tt_status physics_setup(tt_context* ctx, const tt_problem* p, tt_plan* plan) {
   cudaMemcpyAsync(d_tb, hdb, sizeof(hdb), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(plan->bc_term_dev, plan->bc_term, sizeof(int) * kMaxTerms, cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(plan->edges, p->group_edges, sizeof(double) * (G + 1), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(plan->temp, p->temperature, sizeof(double) * ncell, cudaMemcpyDeviceToDevice, s);
+  if (plan->coupled) {
+    cudaMemcpyAsync(plan->rho_cv, p->rho_cv, sizeof(double) * ncell, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(plan->tdag, 0, sizeof(double) * ncell, s);
+  }
   k_quadrature<<<1, 32, 0, s>>>(p->quadrature, p->ntheta, plan->d == 3 ? p->nphi : 1, plan->mu,
                                 plan->phi, plan->domega);
   k_angular_factors<<<plan->nterm, 128, 0, s>>>(plan->d, plan->nterm, d_axis, d_axis + kMaxTerms,
@@ -301,6 +401,21 @@ tt_status physics_setup(tt_context* ctx, const tt_problem* p, tt_plan* plan) {
   cudaFree(d_tb);
   if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return TT_ERR_CUDA;
   return TT_OK;
+}
+
+tt_status coupled_t_dagger(cudaStream_t s, tt_plan* p, const double* jstar) {
+  const long ncell = (long)p->nx * p->ny * p->nz;
+  const long blocks = (ncell + 7) / 8 < 2048 ? (ncell + 7) / 8 : 2048;
+  k_t_dagger<<<(unsigned)blocks, 256, 0, s>>>(ncell, p->G, p->c, p->a_rad, p->edges, p->temp, p->rho_cv, p->acoef,
+                                              jstar, p->tdag, p->eps); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+tt_status coupled_t_update(cudaStream_t s, tt_plan* p, const double* jstar, const double* jnew) {
+  const long ncell = (long)p->nx * p->ny * p->nz;
+  const long blocks = (ncell + 7) / 8 < 2048 ? (ncell + 7) / 8 : 2048;
+  k_t_update<<<(unsigned)blocks, 256, 0, s>>>(ncell, p->G, p->c, p->rho_cv, jstar, jnew, p->temp); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
 }  // namespace ttk

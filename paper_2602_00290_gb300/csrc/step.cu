@@ -31,6 +31,34 @@ struct BigLeaves {
   static constexpr int per_sm = sizeof(T) == 8 ? 2 : 3;
 };
 
+// u = W vJ (R x k times k): J* of the rounded transport update is A u row by row.
+__global__ void k_wvj(int R, int k, const double* __restrict__ W, const double* __restrict__ vJ,
+                      double* __restrict__ u) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= R) return;
+  double s = 0.0;
+  for (int j = 0; j < k; ++j) s += W[(size_t)c * k + j] * vJ[j];
+  u[c] = s;
+}
+
+// J*[k] = sum_c A[k][c] u[c] over the (virtual) sum's live columns, one warp per row (FP64).
+template <class Src>
+__global__ void k_jstar(Src src, LivePattern lp, long nrows, const double* __restrict__ u,
+                        double* __restrict__ jstar) {
+  const int ncap = lp.ncap();
+  const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
+  const int lane = threadIdx.x & 31;
+  const long warps = (long)gridDim.x * (blockDim.x >> 5);
+  for (long k = blockIdx.x * (long)(blockDim.x >> 5) + (threadIdx.x >> 5); k < nrows; k += warps) {
+    double s = 0.0;
+    for (int c = lane; c < ncap; c += 32)
+      if (lp.live(c, r)) s += src.load(src.col(c), k) * u[c];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) jstar[k] = s;
+  }
+}
+
 // B0 of the transport sum: block t = 0 is the right part of the state, block t = 1..nterm is
 // the same right part scaled by the operator's angular factors f1_t(l) f2_t(p), and each
 // inflow column carries the factors alone (Appendix A: rank-1 operators and the rank-1
@@ -329,6 +357,12 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- source step fused into the write of the rounded transport update
   LivePattern lp2{nullptr, K1, 1, 1};
   RoundBufs b2 = take_round_bufs<T>(ws, ctx->num_sms, leaf_cap<T>(ctx), d, lp2.ncap(), N, n1, n2, K1, K2, K1);
+  double *cpl_u = nullptr, *jstar = nullptr, *jnew = nullptr;
+  if (p->coupled) {
+    cpl_u = ws.take<double>(R1);
+    jstar = ws.take<double>(N);
+    jnew = ws.take<double>(N);
+  }
   if (ws.dry) {
     SmallJob j2 = j1;
     j2.lp = lp2;
@@ -338,6 +372,15 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
       if (st != TT_OK) return st;
     }
     return small_round(s, ctx->num_sms, j2, ws);
+  }
+  if (p->coupled) {
+    // material temperature (Sec. 2.1): T^dagger per cell from J* of the rounded transport
+    // update, epsilon(T^dagger) into the plan before the source step reads it
+    k_wvj<<<(R1 + 255) / 256, 256, 0, s>>>(R1, K1, b1.W, b1.vJ, cpl_u); count_launch();
+    const long jb = (N + 7) / 8 < 4096 ? (N + 7) / 8 : 4096;
+    k_jstar<<<(unsigned)jb, 256, 0, s>>>(src1, lp1, N, cpl_u, jstar); count_launch();
+    st = coupled_t_dagger(s, const_cast<tt_plan*>(p), jstar);  // the plan holds the material state
+    if (st != TT_OK) return st;
   }
   st = launch_update<T>(s, ctx->num_sms, src1, lp1, N, b1.W, K1,
                         EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps}, part1, &ngrid1);
@@ -369,8 +412,12 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   st = small_round(s, ctx->num_sms, j2, ws);
   if (st != TT_OK) return st;
   st = launch_update<T>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
-                        EpiFinal<S>{(S*)I->core[0], K1, b2.vJ}, part2, &ngrid2);
+                        EpiFinal<S>{(S*)I->core[0], K1, b2.vJ, jnew}, part2, &ngrid2);
   if (st != TT_OK) return st;
+  if (p->coupled) {
+    st = coupled_t_update(s, const_cast<tt_plan*>(p), jstar, jnew);
+    if (st != TT_OK) return st;
+  }
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
   k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b2.core1, b2.core2,
                                                             (S*)I->core[1], d == 3 ? (S*)I->core[2] : nullptr,

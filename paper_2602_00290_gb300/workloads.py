@@ -54,6 +54,7 @@ class Workload:
     temperature: np.ndarray        # (N_X,) material temperature per cell (fixed)
     rho_kappa_a: np.ndarray        # (N_X*G,) per merged row
     rho_kappa_s: np.ndarray        # (N_X*G,) per merged row
+    rho_cv: Optional[np.ndarray] = None  # per cell: couples the material temperature
     flux: str = "upwind"            # "upwind" or "rusanov" (vacuum boundaries only)
     inflow_temperature: Tuple[Optional[float], ...] = (None,) * 6
     initial_temperature: Optional[np.ndarray] = None  # radiation temperature per cell for I^0
