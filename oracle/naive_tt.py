@@ -339,3 +339,43 @@ def energy_density_rows(tt, coef):
 def compression(nX, nnu, ntheta, nphi, rzt, rtp):
     """Eq. (compression), Sec. 3.2."""
     return (nX * nnu * ntheta * nphi) / (nX * nnu * rzt + ntheta * rzt * rtp + nphi * rtp)
+
+
+# --- internal structure of the merged core (Sec. 5.2) --------------------------------------
+
+def delta_rank(S, delta_rel):
+    """Smallest k with sqrt(sum_{j >= k} sigma_j^2) <= delta_rel * ||sigma||_2 (the delta-SVD of
+    Sec. 5.4: relative Frobenius error below delta)."""
+    S = np.asarray(S, dtype=float)
+    tot = math.sqrt(float(np.sum(S ** 2)))
+    if tot == 0.0:
+        return 1
+    t = _tail(S)
+    for k in range(1, len(S) + 1):
+        if t[k] <= delta_rel * tot:
+            return k
+    return len(S)
+
+
+def internal_ranks(Z, G, delta_rel):
+    """Internal delta-ranks of the merged core Z (N_X G x r, row k = g + G cell), Sec. 5.2:
+    r1 (frequency-leading) of reshape(Z, [N_nu, N_X r]) and r1x (space-leading) of
+    reshape(Z, [N_X, N_nu r]).  The angular cores must be right-orthonormal (a rounded state), so
+    that these local errors are global ones.  Returns (r1, r1x, sigma_nu, sigma_x)."""
+    nrow, r = Z.shape
+    nX = nrow // G
+    Z3 = Z.reshape(nX, G, r)                              # [cell][g][q]
+    M_nu = np.transpose(Z3, (1, 0, 2)).reshape(G, nX * r)
+    M_x = Z3.reshape(nX, G * r)
+    s_nu = np.linalg.svd(M_nu, compute_uv=False)
+    s_x = np.linalg.svd(M_x, compute_uv=False)
+    return delta_rank(s_nu, delta_rel), delta_rank(s_x, delta_rel), s_nu, s_x
+
+
+def relative_compression(nX, nnu, ntheta, nphi, r1, r1x, r2, r3):
+    """Eqs. (rel_compression_nu) and (rel_compression_x): (C_rel^nu, C_rel^x), with N_TT the
+    parameter count of the merged-core TT."""
+    ntt = nX * nnu * r2 + ntheta * r2 * r3 + nphi * r3
+    c_nu = ntt / (nnu * r1 + nX * r1 * r2 + ntheta * r2 * r3 + nphi * r3)
+    c_x = ntt / (nX * r1x + nnu * r1x * r2 + ntheta * r2 * r3 + nphi * r3)
+    return c_nu, c_x
