@@ -311,6 +311,22 @@ def run_ours(args):
         Eg = tt.tt_energy_density(ctx, plan, states["fp64_gram"]).cpu().numpy()
         Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()
         line["fp64_gram"]["energy_density_rel_err_vs_tsqr"] = float(np.linalg.norm(Eg - Ed) / np.linalg.norm(Ed))
+    # internal structure of the final state's merged core (Sec. 5.2): delta-ranks at the rounding
+    # tolerance and the compression ratios of Eqs. (compression), (rel_compression_nu/_x)
+    try:
+        t0 = time.time()
+        r1, r1x, _, _ = tt.tt_internal_ranks(ctx, plan, x, wl.tol)
+        r2, r3 = x.ranks()[1], x.ranks()[2]
+        nX, nnu, nth, nph = wl.nx * wl.ny * wl.nz, wl.ngroup, wl.ntheta, wl.nphi
+        ntt = nX * nnu * r2 + nth * r2 * r3 + nph * r3
+        line["internal_ranks"] = {
+            "delta": wl.tol, "r1_nu": r1, "r1_x": r1x, "tt_ranks": [r2, r3],
+            "compression": nX * nnu * nth * nph / ntt,
+            "compression_rel_nu": ntt / (nnu * r1 + nX * r1 * r2 + nth * r2 * r3 + nph * r3),
+            "compression_rel_x": ntt / (nX * r1x + nnu * r1x * r2 + nth * r2 * r3 + nph * r3),
+            "seconds": time.time() - t0}
+    except Exception as e:  # the analysis is a report, not part of the timed step
+        line["internal_ranks"] = {"error": str(e)}
     # end-to-end through the C ABI with host buffers (pinned), copies inside the timed region
     if args.e2e_steps > 0:
         stream = ctx.stream

@@ -212,6 +212,18 @@ tt_status tt_apply_transport(tt_context *ctx, const tt_plan *plan, const tt_tens
 tt_status tt_step(tt_context *ctx, const tt_plan *plan, tt_tensor *I, double tol, int32_t rmax,
                   tt_precision prec, double *energy_dev);
 
+/* Internal delta-ranks of the merged core (Sec. 5.2): r1 (frequency-leading) and r1x
+ * (space-leading) of reshape(Z, [N_nu, N_X r]) and reshape(Z, [N_X, N_nu r]) at relative tolerance
+ * delta_rel (the delta-SVD of Sec. 5.4: smallest rank whose discarded singular values have a
+ * Frobenius norm <= delta_rel |Z|).  x must be a rounded state (angular cores right-orthonormal,
+ * as tt_round and tt_step leave them), so that the local errors are global ones.  Synchronous:
+ * ranks[2] (host) receives r1, r1x; sigma_nu / sigma_x (host, nullable) receive up to nsigma_*
+ * singular values, decreasing.  The singular values come from FP64 Gram matrices (N_nu x N_nu and
+ * N_nu rcap x N_nu rcap, at most 4096) and Jacobi eigen-solves, so values below about 1e-8 of the
+ * largest are not resolved.  TT_ERR_UNSUPPORTED beyond 4096. */
+tt_status tt_internal_ranks(tt_context *ctx, const tt_plan *plan, const tt_tensor *x, double delta_rel,
+                            int32_t *ranks, double *sigma_nu, int64_t nsigma_nu, double *sigma_x, int64_t nsigma_x);
+
 /* ---- Batched stepping of independent problems (many plans and states, one CUDA graph) ----
  * Each problem's step is the tt_step of the paper's step-then-truncate scheme (Sec. 2.1 source
  * update, Sec. 3.1 rounding, Appendix A transport); the batching itself has no counterpart in

@@ -33,7 +33,8 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
-           "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding")
+           "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding",
+           "tt_internal_ranks")
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
 
@@ -105,6 +106,9 @@ def lib():
                               ctypes.POINTER(ctypes.c_int32)],
             "tt_batch_destroy": [vp],
             "tt_context_set_rounding": [vp, ctypes.c_int],
+            "tt_internal_ranks": [vp, vp, ctypes.POINTER(_Tensor), ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                  ctypes.c_int64],
         }
         for name, args in sigs.items():
             f = getattr(L, name)
@@ -409,6 +413,20 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def tt_internal_ranks(ctx: Context, plan: "Plan", x: TT, delta_rel: float):
+    """(r1, r1x, sigma_nu, sigma_x): internal delta-ranks of the merged core (tt_internal_ranks)."""
+    G = plan.wl.ngroup
+    ncx = G * x.rcap[1]
+    nX = x.n[0] // G
+    r = (ctypes.c_int32 * 2)()
+    snu = (ctypes.c_double * G)()
+    nsx = min(nX, ncx)
+    sx = (ctypes.c_double * nsx)()
+    _check(lib().tt_internal_ranks(ctx.handle, plan.handle, ctypes.byref(x._struct()), float(delta_rel), r, snu, G,
+                                   sx, nsx), "tt_internal_ranks")
+    return int(r[0]), int(r[1]), np.array(snu[:]), np.array(sx[:])
 
 
 def tt_round(ctx: Context, x: TT, tol: float, rmax: int, prec="fp64"):

@@ -344,6 +344,25 @@ tt_status tt_step(tt_context* ctx, const tt_plan* plan, tt_tensor* I, double tol
   });
 }
 
+tt_status tt_internal_ranks(tt_context* ctx, const tt_plan* plan, const tt_tensor* x, double delta_rel,
+                            int32_t* ranks, double* sigma_nu, int64_t nsigma_nu, double* sigma_x, int64_t nsigma_x) {
+  if (!ctx || !plan || !ranks || !(delta_rel >= 0.0) || nsigma_nu < 0 || nsigma_x < 0) return TT_ERR_ARG;
+  tt_status st = check_tensor(x);
+  if (st == TT_OK) st = check_plan_tensor(plan, x);
+  if (st != TT_OK) return st;
+  set_device(ctx);
+  int r[2] = {0, 0};
+  st = with_ws(ctx, [&](ttk::Bump& ws) {
+    return (x->dtype == TT_F64) ? ttk::internal_ranks_impl<double>(ctx, plan, x, delta_rel, r, sigma_nu, nsigma_nu,
+                                                                   sigma_x, nsigma_x, ws)
+                                : ttk::internal_ranks_impl<float>(ctx, plan, x, delta_rel, r, sigma_nu, nsigma_nu,
+                                                                  sigma_x, nsigma_x, ws);
+  });
+  ranks[0] = r[0];
+  ranks[1] = r[1];
+  return st;
+}
+
 tt_status tt_energy_density(tt_context* ctx, const tt_plan* plan, const tt_tensor* x, double* out_dev) {
   if (!ctx || !plan || !out_dev) return TT_ERR_ARG;
   tt_status st = check_tensor(x);

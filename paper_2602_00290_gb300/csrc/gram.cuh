@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_gram_tiles(Src src, LivePattern lp, lon
 }
 
 // G[a][b] (full ncap x ncap) = sum over splits, in split order, of the canonical block entry.
-__global__ void k_gram_reduce(int ncap, int nsplit, int npairs, const double* __restrict__ part,
+static __global__ void k_gram_reduce(int ncap, int nsplit, int npairs, const double* __restrict__ part,
                               double* __restrict__ G) {
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long)ncap * ncap) return;
@@ -133,7 +133,7 @@ __global__ void k_gram_reduce(int ncap, int nsplit, int npairs, const double* __
 // stopped once the largest remaining pivot is at the round-off level of the largest diagonal
 // entry (the rank of a rank-deficient sum).  Writes RZ = R P^T (n x n row-major, rows beyond the
 // rank zero), so that RZ^T RZ = G.  One CTA; G stays in global memory (L2).
-__global__ void __launch_bounds__(1024) k_gram_pchol(int n, double* __restrict__ G, double* __restrict__ RZ,
+static __global__ void __launch_bounds__(1024) k_gram_pchol(int n, double* __restrict__ G, double* __restrict__ RZ,
                                                      int* __restrict__ perm) {
   __shared__ double rowj[512];
   __shared__ double redv[32];
@@ -194,15 +194,15 @@ __global__ void __launch_bounds__(1024) k_gram_pchol(int n, double* __restrict__
   }
 }
 
-// Square-root factor RZ (ncap x ncap, row-major) of the Gram matrix of the source's columns.
-// Takes its workspace from `ws` in dry runs too (same order), launches nothing then.
+// Gram matrix G = A^T A (ncap x ncap, row-major, FP64) of the source's columns.  Takes its
+// workspace from `ws` in dry runs too (same order) and launches nothing then.
 template <class Src>
-tt_status gram_factor(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows, Bump& ws,
-                      DevCtrl* ctrl, int coop_grid_max, double** RZ_out, int timer_cat = kTsqrLeaf) {
+tt_status gram_matrix(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows, Bump& ws,
+                      double** G_out, int timer_cat = kTsqrLeaf) {
   const int ncap = lp.ncap();
   const int npairs = gram_npairs(ncap);
   const size_t smem = gram_smem_bytes<Src>();
-  int occ = 3;
+  const int occ = 3;
   long nsplit = ((long)num_sms * occ + npairs - 1) / npairs;
   const long maxsplit = (nrows + kGramTM - 1) / kGramTM;
   if (nsplit > maxsplit) nsplit = maxsplit;
@@ -211,20 +211,32 @@ tt_status gram_factor(cudaStream_t s, int num_sms, const Src& src, LivePattern l
   rps = ((rps + kGramTM - 1) / kGramTM) * kGramTM;
   nsplit = (nrows + rps - 1) / rps;
   if (nsplit < 1) nsplit = 1;
-  if (ncap > 512) return TT_ERR_UNSUPPORTED;
   double* part = ws.take<double>((size_t)nsplit * npairs * kGramBlk * kGramBlk);
   double* G = ws.take<double>((size_t)ncap * ncap);
+  *G_out = G;
+  if (ws.dry) return TT_OK;
+  cudaFuncSetAttribute(k_gram_tiles<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  TimerScope scope(timer_cat, s);
+  k_gram_tiles<Src><<<dim3((unsigned)nsplit, (unsigned)npairs), 256, smem, s>>>(src, lp, nrows, rps, part);
+  count_launch();
+  const long nn = (long)ncap * ncap;
+  k_gram_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(ncap, (int)nsplit, npairs, part, G); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+// Square-root factor RZ (ncap x ncap, row-major) of the Gram matrix of the source's columns.
+// Takes its workspace from `ws` in dry runs too (same order), launches nothing then.
+template <class Src>
+tt_status gram_factor(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows, Bump& ws,
+                      DevCtrl* ctrl, int coop_grid_max, double** RZ_out, int timer_cat = kTsqrLeaf) {
+  const int ncap = lp.ncap();
+  if (ncap > 512) return TT_ERR_UNSUPPORTED;
+  double* G = nullptr;
+  tt_status st = gram_matrix(s, num_sms, src, lp, nrows, ws, &G, timer_cat);
+  if (st != TT_OK) return st;
   int* perm = ws.take<int>(ncap);
   double* RZ = ws.take<double>((size_t)ncap * ncap);
   *RZ_out = RZ;
-  if (!ws.dry) {
-    cudaFuncSetAttribute(k_gram_tiles<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    TimerScope scope(timer_cat, s);
-    k_gram_tiles<Src><<<dim3((unsigned)nsplit, (unsigned)npairs), 256, smem, s>>>(src, lp, nrows, rps, part);
-    count_launch();
-    const long nn = (long)ncap * ncap;
-    k_gram_reduce<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(ncap, (int)nsplit, npairs, part, G); count_launch();
-  }
   if (ws.dry) return TT_OK;
   k_gram_pchol<<<1, 1024, 0, s>>>(ncap, G, RZ, perm); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;

@@ -21,5 +21,8 @@ template <typename S>
 tt_status dot_into(cudaStream_t s, const tt_tensor* x, const tt_tensor* y, double* out, double* scratch,
                    size_t cap);
 template <typename S>
+tt_status internal_ranks_impl(tt_context* ctx, const tt_plan* p, const tt_tensor* x, double delta, int* ranks,
+                              double* sig_nu, long nsig_nu, double* sig_x, long nsig_x, Bump& ws);
+template <typename S>
 tt_status dot_impl(tt_context* ctx, const tt_tensor* x, const tt_tensor* y, double* out, Bump& ws);
 }  // namespace ttk
