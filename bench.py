@@ -308,6 +308,16 @@ def run_ours(args):
         G = results["fp64_gram"]
         line["fp64_gram"] = {k: G[k] for k in ("value", "ms_per_step", "tflops", "breakdown_ms_per_step",
                                                "gpu_launches", "ranks", "jacobi")}
+        # the Gram pass over the transport sum (symmetric: N R1 (R1 + 1) flops at R1 = 5r)
+        rh = G["rank_history"]
+        gflops = sum(2.0 * wl.nrow * (5 * r[0]) * (5 * r[0] + 1) / 2.0 for r in rh[:-1])
+        gms = G["breakdown_ms_per_step"]["tsqr_leaf"] * args.steps
+        ach = gflops / (gms / 1e3) / 1e12 if gms > 0 else None
+        line["fp64_gram"]["roofline"] = {
+            "kernel": "k_gram_tiles + k_gram_reduce over the transport sum (FP64 Gram, upper triangle)",
+            "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS if ach else None,
+            "peak_source": "FP64 FMA units: 152 SMs x 2/clk x 2 flop x 2070 MHz"}
         Eg = tt.tt_energy_density(ctx, plan, states["fp64_gram"]).cpu().numpy()
         Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()
         line["fp64_gram"]["energy_density_rel_err_vs_tsqr"] = float(np.linalg.norm(Eg - Ed) / np.linalg.norm(Ed))

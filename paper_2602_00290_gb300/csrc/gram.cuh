@@ -56,7 +56,9 @@ __global__ void __launch_bounds__(256) k_gram_tiles(Src src, LivePattern lp, lon
     livec[i] = (ok && lp.live(c, r)) ? 1 : 0;
   }
   const int ty = tid >> 4, tx = tid & 15;
-  const bool active = !(diag && ty > tx);
+  // micro-tiles wholly below the diagonal of a diagonal block, or wholly beyond the last
+  // column (the last block of a width that is not a multiple of 64), have nothing to compute
+  const bool active = !(diag && ty > tx) && (bi * kGramBlk + 4 * ty < ncap) && (bj * kGramBlk + 4 * tx < ncap);
   double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
@@ -202,8 +204,10 @@ tt_status gram_matrix(cudaStream_t s, int num_sms, const Src& src, LivePattern l
   const int ncap = lp.ncap();
   const int npairs = gram_npairs(ncap);
   const size_t smem = gram_smem_bytes<Src>();
-  const int occ = 3;
-  long nsplit = ((long)num_sms * occ + npairs - 1) / npairs;
+  // about 8 waves of CTAs (3 per SM): the block pairs differ in work (diagonal and edge blocks
+  // skip micro-tiles), and many short CTAs let the scheduler balance them
+  const int occ = 3, waves = 8;
+  long nsplit = ((long)num_sms * occ * waves + npairs - 1) / npairs;
   const long maxsplit = (nrows + kGramTM - 1) / kGramTM;
   if (nsplit > maxsplit) nsplit = maxsplit;
   if (nsplit < 1) nsplit = 1;
