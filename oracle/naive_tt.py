@@ -305,10 +305,15 @@ def source_sum(tt, coef):
     return add(scaled, iso)
 
 
-def step(tt, coef, tol, rmax, info=None, rounding="svd"):
+def step(tt, coef, tol, rmax, info=None, rounding="svd", omega=None):
     """One step-then-truncate time step: transport, round, source, round (end of Sec. 3.1).
-    rounding: "svd" (round_tt) or "gram" (round_tt_gram), used for both roundings."""
-    rnd = round_tt_gram if rounding == "gram" else round_tt
+    rounding: "svd" (round_tt), "gram" (round_tt_gram) or "randomized" (round_tt_randomized with
+    the sketch omega), used for both roundings."""
+    if rounding == "randomized":
+        def rnd(x, t, r, i=None):
+            return round_tt_randomized(x, t, r, omega, i)
+    else:
+        rnd = round_tt_gram if rounding == "gram" else round_tt
     i1, i2 = {}, {}
     x = rnd(transport_sum(tt, coef), tol, rmax, i1)
     x = rnd(source_sum(x, coef), tol, rmax, i2)
@@ -379,3 +384,25 @@ def relative_compression(nX, nnu, ntheta, nphi, r1, r1x, r2, r3):
     c_nu = ntt / (nnu * r1 + nX * r1 * r2 + ntheta * r2 * r3 + nphi * r3)
     c_x = ntt / (nX * r1x + nnu * r1x * r2 + ntheta * r2 * r3 + nphi * r3)
     return c_nu, c_x
+
+
+def round_tt_randomized(tt, tol, rmax, omega, info=None):
+    """Randomized rounding of the first bond (the randomized method among the three rounding
+    methods of Sec. 3.1): the first unfolding X_(1) = A B (A the first core's left unfolding, B the
+    right part) is sketched as Y = X_(1) omega = A (B omega) with a caller-drawn omega
+    (n_2 ... n_d x l); Q from the QR of Y spans the sketch, and C = Q^T A stands in for the QR
+    factor of A (X' = C x (cores 2..d) = Q^T X).  X' is rounded by round_tt (the SVD-based
+    truncation at the same tolerance); its new cores 2..d are X's, and the new first core is A
+    projected onto the new right frame, A (B_old B_new^T).  With l >= rank(A) this is SVD rounding;
+    otherwise it keeps what the sketch captured (randomized range finder)."""
+    r0, n, r1 = tt[0].shape
+    A = tt[0].reshape(r0 * n, r1)
+    Bold = right_part(tt[1:])
+    Y = A @ (Bold @ omega)
+    Q, _ = np.linalg.qr(Y, mode="reduced")
+    C = Q.T @ A
+    small = [C.reshape(1, C.shape[0], r1)] + [c.copy() for c in tt[1:]]
+    out = round_tt(small, tol, rmax, info)
+    Bnew = right_part(out[1:])
+    first = (A @ (Bold @ Bnew.T)).reshape(r0, n, Bnew.shape[0])
+    return [first] + out[1:]

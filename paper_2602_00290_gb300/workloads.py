@@ -208,6 +208,11 @@ def batch_config3(nprob: int = 256, seed: int = 3, scale: int = 1, tol: float = 
     return out
 
 
+def sketch_matrix(nang: int, ell: int, seed: int = 11) -> np.ndarray:
+    """Gaussian N(0, 1) sketch omega (nang x ell) for randomized rounding, seeded."""
+    return np.random.default_rng(seed).standard_normal((nang, ell))
+
+
 def random_tt(n: Sequence[int], ranks: Sequence[int], seed: int, scale: float = 1.0):
     """Cores with iid N(0,1) entries, core k of shape (r_{k-1}, n_k, r_k)."""
     rng = np.random.default_rng(seed)

@@ -236,3 +236,42 @@ def test_round_gram_zero_tensor():
     g = nt.round_tt_gram(z, 1e-6)
     assert nt.ranks(g) == [1, 1, 1, 1]
     assert not np.any(nt.full(g))
+
+
+# --- randomized rounding (the randomized method of Sec. 3.1) --------------------------------
+
+def test_round_randomized_equals_svd_rounding_when_the_sketch_spans_the_range():
+    """With l >= rank of the first unfolding the sketch's range is the whole range: the
+    randomized route is the SVD route (ranks and result)."""
+    from paper_2602_00290_gb300.workloads import sketch_matrix
+    n = [233, 5, 9]
+    a = nt.add_many([nt.scale(random_tt(n, [3, 2], seed=20 + i), 10.0 ** -i) for i in range(4)])
+    om = sketch_matrix(5 * 9, 14, seed=3)          # rank of the first unfolding <= 12
+    for tol in (1e-2, 1e-4, 1e-8):
+        i1, i2 = {}, {}
+        w = nt.round_tt(a, tol, 20, i1)
+        g = nt.round_tt_randomized(a, tol, 20, om, i2)
+        assert nt.ranks(g) == nt.ranks(w)
+        assert np.linalg.norm(nt.full(g) - nt.full(w)) <= 1e-11 * np.linalg.norm(nt.full(w))
+
+
+def test_round_randomized_range_finder_error_bound():
+    """Sketching with l = k + p columns: the discarded part of the sketch obeys the randomized
+    range-finder bound E|X - Q Q^T X| <= (1 + sqrt(k/(p-1))) (sum_{j>k} s_j^2)^(1/2) (Halko,
+    Martinsson, Tropp); a seeded draw stays within 10x that, and the leading singular values
+    are recovered when the spectrum decays fast."""
+    from paper_2602_00290_gb300.workloads import sketch_matrix
+    rng = np.random.default_rng(9)
+    m, ncol, k, p = 400, 60, 6, 6
+    U, _ = np.linalg.qr(rng.standard_normal((m, ncol)))
+    V, _ = np.linalg.qr(rng.standard_normal((ncol, ncol)))
+    s = 10.0 ** (-0.5 * np.arange(ncol))
+    A = (U * s) @ V.T
+    tt = [A.reshape(1, m, ncol), np.eye(ncol).reshape(ncol, ncol, 1)]
+    om = sketch_matrix(ncol, k + p, seed=5)
+    info = {}
+    g = nt.round_tt_randomized(tt, 0.0, k, om, info)
+    err = np.linalg.norm(nt.full(g).reshape(m, ncol) - A)
+    bound = (1 + math.sqrt(k / (p - 1))) * math.sqrt(np.sum(s[k:] ** 2))
+    assert err <= 10 * bound
+    assert np.allclose(info["bonds"][0]["sigma"][:3], s[:3], rtol=1e-3)
