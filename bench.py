@@ -277,6 +277,11 @@ def run_ours(args):
     if "fp64" in precs and not args.no_gram:
         results["fp64_gram"], states["fp64_gram"], _ = time_precision(tt, torch, ctx, plan, wl, args, "fp64", dist,
                                                                       vis, rounding="gram")
+        # randomized rounding: Gaussian sketch of r_max + 8 columns (seeded)
+        from paper_2602_00290_gb300.workloads import sketch_matrix
+        ctx.set_sketch(sketch_matrix(wl.ntheta * wl.nphi, wl.rmax + 8, seed=11))
+        results["fp64_randomized"], states["fp64_randomized"], _ = time_precision(
+            tt, torch, ctx, plan, wl, args, "fp64", dist, vis, rounding="randomized")
     head = "mixed" if "mixed" in results else "fp64"
     R = results[head]
     x = states[head]
@@ -321,6 +326,14 @@ def run_ours(args):
         Eg = tt.tt_energy_density(ctx, plan, states["fp64_gram"]).cpu().numpy()
         Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()
         line["fp64_gram"]["energy_density_rel_err_vs_tsqr"] = float(np.linalg.norm(Eg - Ed) / np.linalg.norm(Ed))
+    if "fp64_randomized" in results:
+        Rr = results["fp64_randomized"]
+        line["fp64_randomized"] = {k: Rr[k] for k in ("value", "ms_per_step", "tflops", "breakdown_ms_per_step",
+                                                      "gpu_launches", "ranks")}
+        line["fp64_randomized"]["sketch_columns"] = wl.rmax + 8
+        Er = tt.tt_energy_density(ctx, plan, states["fp64_randomized"]).cpu().numpy()
+        Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()
+        line["fp64_randomized"]["energy_density_rel_err_vs_tsqr"] = float(np.linalg.norm(Er - Ed) / np.linalg.norm(Ed))
     # internal structure of the final state's merged core (Sec. 5.2): delta-ranks at the rounding
     # tolerance and the compression ratios of Eqs. (compression), (rel_compression_nu/_x)
     try:

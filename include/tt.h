@@ -108,11 +108,16 @@ typedef struct tt_context tt_context;
 /* Factor of the merged core in the first sweep of every rounding (tt_round, tt_step).
  * TT_ROUND_TSQR: Householder TSQR (the SVD-based rounding of Sec. 3.1; the default).
  * TT_ROUND_GRAM: Gram-based (Sec. 3.1 lists it among the solver's rounding methods): the FP64 Gram
- * matrix G = A^T A of the merged core's unfolding (virtual transport sum included) and
- * R = diag(lambda^(1/2)) V^T from its Jacobi eigen-decomposition replace the TSQR's R; the rest
- * of the rounding is unchanged.  Forming G squares the condition number (the paper's caution):
- * singular values below about 1e-8 |X| are not resolved, so use it at tolerances above that. */
-typedef enum { TT_ROUND_TSQR = 0, TT_ROUND_GRAM = 1 } tt_rounding;
+ * matrix G = A^T A of the merged core's unfolding (virtual transport sum included) and a square
+ * root R of G (R^T R = G, diagonally pivoted Cholesky) replace the TSQR's R; the rest of the
+ * rounding is unchanged.  Forming G squares the condition number (the paper's caution):
+ * singular values below about 1e-8 |X| are not resolved, so use it at tolerances above that.
+ * TT_ROUND_RANDOMIZED: randomized (Sec. 3.1 lists it too): the merged core's first unfolding is
+ * sketched as Y = A (B0 omega) with the caller's sketch omega (tt_context_set_sketch), Q from a
+ * Householder TSQR of Y's l columns, and C = Q^T A (FP64 accumulation) replaces the TSQR's R;
+ * the SVD-based truncation follows at the same tolerance.  With l >= the rank of the unfolding
+ * this is the SVD rounding; otherwise it keeps the directions the sketch captured. */
+typedef enum { TT_ROUND_TSQR = 0, TT_ROUND_GRAM = 1, TT_ROUND_RANDOMIZED = 2 } tt_rounding;
 
 typedef struct tt_plan tt_plan;
 
@@ -142,8 +147,15 @@ typedef enum {
 tt_status tt_context_set_timing(tt_context *ctx, int enable);
 
 /* Select the rounding method of the context (TT_ERR_ARG for an unknown method).  With
- * TT_ROUND_GRAM the TT_TIMER_TSQR_LEAF(_SOURCE) categories time the Gram pass instead. */
+ * TT_ROUND_GRAM the TT_TIMER_TSQR_LEAF(_SOURCE) categories time the Gram pass instead; with
+ * TT_ROUND_RANDOMIZED they time the TSQR of the sketch (the sketch itself is an update pass). */
 tt_status tt_context_set_rounding(tt_context *ctx, tt_rounding method);
+
+/* Sketch of randomized rounding: omega_dev (device, nang x ell row-major, FP64, caller-owned and
+ * kept allocated while the context rounds with it; e.g. iid N(0,1)), nang = n_1 ... n_{d-1} of
+ * the tensors rounded, 1 <= ell <= 64 (the target rank plus oversampling).  The same sketch is
+ * used at every rounding; a call whose angular size differs from nang fails with TT_ERR_SHAPE. */
+tt_status tt_context_set_sketch(tt_context *ctx, const double *omega_dev, int32_t nang, int32_t ell);
 
 /* Synchronise the context stream and report, per tt_timer category, the summed kernel time
  * in milliseconds (ms[TT_TIMER_COUNT], nullable) and the number of kernel launches

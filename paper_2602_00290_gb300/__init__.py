@@ -27,14 +27,14 @@ TT_F64, TT_F32 = 0, 1
 TT_PREC_FP64, TT_PREC_MIXED = 0, 1
 TT_QUAD_GAUSS_LEGENDRE_MU, TT_QUAD_LATLONG_MIDPOINT = 0, 1
 PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED}
-ROUNDINGS = {"tsqr": 0, "gram": 1}
+ROUNDINGS = {"tsqr": 0, "gram": 1, "randomized": 2}
 
 EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sync", "tt_workspace_query",
            "tt_plan_create", "tt_plan_destroy", "tt_plan_array", "tt_axpy", "tt_dot", "tt_round",
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
            "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding",
-           "tt_internal_ranks")
+           "tt_internal_ranks", "tt_context_set_sketch")
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
 
@@ -106,6 +106,7 @@ def lib():
                               ctypes.POINTER(ctypes.c_int32)],
             "tt_batch_destroy": [vp],
             "tt_context_set_rounding": [vp, ctypes.c_int],
+            "tt_context_set_sketch": [vp, vp, ctypes.c_int32, ctypes.c_int32],
             "tt_internal_ranks": [vp, vp, ctypes.POINTER(_Tensor), ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int64],
@@ -154,8 +155,17 @@ class Context:
     def sync(self):
         _check(lib().tt_sync(self.handle), "tt_sync")
 
+    def set_sketch(self, omega):
+        """Sketch of randomized rounding: omega (n_1...n_{d-1} x l) as a numpy or torch array."""
+        torch = _torch()
+        om = torch.as_tensor(np.asarray(omega, dtype=np.float64), device=torch.device("cuda", self.device)).contiguous()
+        self._sketch = om
+        _check(lib().tt_context_set_sketch(self.handle, ctypes.c_void_p(om.data_ptr()), int(om.shape[0]),
+                                           int(om.shape[1])), "tt_context_set_sketch")
+
     def set_rounding(self, method: str):
-        """"tsqr" (Householder TSQR, default) or "gram" (Gram matrix + Jacobi square root)."""
+        """"tsqr" (Householder TSQR, default), "gram" (Gram matrix + pivoted-Cholesky root) or
+        "randomized" (sketch of set_sketch, TSQR of the sketch, C = Q^T A)."""
         _check(lib().tt_context_set_rounding(self.handle, ROUNDINGS[method]), "tt_context_set_rounding")
 
     def set_timing(self, enable: bool):

@@ -111,6 +111,9 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->coop_grid_max = 0;
   ctx->tsqr_leaf_cap = 0;
   ctx->rounding = TT_ROUND_TSQR;
+  ctx->sketch = nullptr;
+  ctx->sketch_nang = 0;
+  ctx->sketch_ell = 0;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
@@ -145,8 +148,17 @@ tt_status tt_context_destroy(tt_context* ctx) {
   return TT_OK;
 }
 
+tt_status tt_context_set_sketch(tt_context* ctx, const double* omega_dev, int32_t nang, int32_t ell) {
+  if (!ctx || !omega_dev || nang < 1 || ell < 1 || ell > 64) return TT_ERR_ARG;
+  ctx->sketch = omega_dev;
+  ctx->sketch_nang = nang;
+  ctx->sketch_ell = ell;
+  return TT_OK;
+}
+
 tt_status tt_context_set_rounding(tt_context* ctx, tt_rounding method) {
-  if (!ctx || (method != TT_ROUND_TSQR && method != TT_ROUND_GRAM)) return TT_ERR_ARG;
+  if (!ctx || (method != TT_ROUND_TSQR && method != TT_ROUND_GRAM && method != TT_ROUND_RANDOMIZED))
+    return TT_ERR_ARG;
   ctx->rounding = method;
   return TT_OK;
 }

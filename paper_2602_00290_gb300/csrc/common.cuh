@@ -99,6 +99,8 @@ struct tt_context {
   int coop_grid_max;  // > 0: cap on the CTAs of a cooperative launch (concurrent streams)
   int tsqr_leaf_cap;  // > 0: cap on the TSQR leaves over the merged core (batched problems)
   int rounding;       // tt_rounding of tt_round / tt_step
+  const double* sketch;  // randomized rounding: omega (sketch_nang x sketch_ell, device, caller-owned)
+  int sketch_nang, sketch_ell;
 };
 
 struct tt_plan {

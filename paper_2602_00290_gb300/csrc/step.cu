@@ -6,6 +6,7 @@
 
 #include "bigpass.cuh"
 #include "gram.cuh"
+#include "rand.cuh"
 #include "small.cuh"
 #include "step.cuh"
 
@@ -224,6 +225,51 @@ static RoundBufs take_round_bufs(Bump& ws, int num_sms, int max_leaves, int d, i
   return b;
 }
 
+// Randomized factor RZ (R x R; rows >= l zero) of the source's columns A: Y = A (B0 omega) by the
+// update pass, Householder TSQR of Y, Q = Y R_Y^{-1} in place, C = Q^T A by the cross product.
+// Takes its workspace from `ws` in dry runs too (same order), launches nothing then.
+template <typename S, typename T, class Src>
+static tt_status randomized_factor(tt_context* ctx, cudaStream_t s, const Src& src, LivePattern lp, long N,
+                                   const double* B0, int nang, Bump& ws, double** RZ_out, int timer_cat) {
+  const int R = lp.ncap();
+  if (!ctx->sketch) return TT_ERR_ARG;
+  if (ctx->sketch_nang != nang) return TT_ERR_SHAPE;
+  const int l = ctx->sketch_ell < R ? ctx->sketch_ell : R;
+  double* Op = ws.take<double>((size_t)R * l);
+  S* Y = ws.take<S>((size_t)N * l);
+  const long L = tsqr_max_leaves<T, BigBR<T>::value>(ctx->num_sms, l, N, leaf_cap<T>(ctx));
+  double* ta = ws.take<double>((size_t)L * l * l);
+  double* tb = ws.take<double>((size_t)((L + 1) / 2) * l * l);
+  const int nbi = (l + 63) / 64, nbj = (R + 63) / 64;
+  long nsplit = ((long)ctx->num_sms * 3 * 8 + nbi * nbj - 1) / (nbi * nbj);
+  const long maxsplit = (N + kCrossTM - 1) / kCrossTM;
+  if (nsplit > maxsplit) nsplit = maxsplit;
+  if (nsplit < 1) nsplit = 1;
+  long rps = (N + nsplit - 1) / nsplit;
+  rps = ((rps + kCrossTM - 1) / kCrossTM) * kCrossTM;
+  nsplit = (N + rps - 1) / rps;
+  if (nsplit < 1) nsplit = 1;
+  double* part = ws.take<double>((size_t)nsplit * nbi * nbj * 64 * 64);
+  double* RZ = ws.take<double>((size_t)R * R);
+  *RZ_out = RZ;
+  if (ws.dry) return TT_OK;
+  small_gemm<double, double>(s, R, l, nang, B0, nang, 1, ctx->sketch, ctx->sketch_ell, 1, Op, l, nullptr, nullptr);
+  tt_status st = launch_update<T>(s, ctx->num_sms, src, lp, N, Op, l, EpiPlain<S>{Y, l}, nullptr, nullptr);
+  if (st != TT_OK) return st;
+  double* RY = nullptr;
+  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Y, l}, LivePattern{nullptr, l, 1, 0}, N,
+                                    leaf_cap<T>(ctx), ta, tb, &RY, timer_cat);
+  if (st != TT_OK) return st;
+  const long sb = (N + 127) / 128 < 4096 ? (N + 127) / 128 : 4096;
+  k_rand_solve<<<(unsigned)sb, 128, sizeof(double) * (size_t)l * l, s>>>(
+      N, l, RY, sizeof(S) == 4 ? (float*)Y : nullptr, sizeof(S) == 8 ? (double*)Y : nullptr); count_launch();
+  k_cross_tiles<SrcRows<S>, Src><<<dim3((unsigned)nsplit, (unsigned)(nbi * nbj)), 256, 0, s>>>(
+      SrcRows<S>{Y, l}, l, src, lp, N, rps, nbj, part); count_launch();
+  k_cross_reduce<<<(unsigned)(((long)R * R + 255) / 256), 256, 0, s>>>(l, R, (int)nsplit, nbi, nbj, part, RZ);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
 template <typename S, typename T>
 tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& ws) {
   cudaStream_t s = ctx->stream;
@@ -260,18 +306,22 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   double* domega_ones = ws.take<double>((size_t)n1 * n2);
   job.domega = domega_ones;
   double* RZ = nullptr;
+  if (!ws.dry) {
+    right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, b.Bbase);
+    cudaMemsetAsync(domega_ones, 0, sizeof(double) * (size_t)n1 * n2, s);
+  }
   if (ctx->rounding == TT_ROUND_GRAM) {
     tt_status st = gram_factor(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, ws, ctx->ctrl,
                                ctx->coop_grid_max, &RZ);
+    if (st != TT_OK) return st;
+  } else if (ctx->rounding == TT_ROUND_RANDOMIZED) {
+    tt_status st = randomized_factor<S, T>(ctx, s, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.Bbase, n1 * n2, ws,
+                                           &RZ, kTsqrLeaf);
     if (st != TT_OK) return st;
   } else if (!ws.dry) {
     tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, leaf_cap<T>(ctx), b.tsqr_a,
                                          b.tsqr_b, &RZ);
     if (st != TT_OK) return st;
-  }
-  if (!ws.dry) {
-    right_part<S>(s, d, K1, n1, K2, n2, (const S*)x->core[1], d == 3 ? (const S*)x->core[2] : nullptr, b.Bbase);
-    cudaMemsetAsync(domega_ones, 0, sizeof(double) * (size_t)n1 * n2, s);
   }
   job.RZ = RZ;
   tt_status st = small_round(s, ctx->num_sms, job, ws);
@@ -344,8 +394,12 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
                                        b1.B0); count_launch();
   }
   const bool gram = (ctx->rounding == TT_ROUND_GRAM);
+  const bool rnd = (ctx->rounding == TT_ROUND_RANDOMIZED);
   if (gram) {
     tt_status st = gram_factor(s, ctx->num_sms, src1, lp1, N, ws, ctx->ctrl, ctx->coop_grid_max, &RZ1);
+    if (st != TT_OK) return st;
+  } else if (rnd) {
+    tt_status st = randomized_factor<S, T>(ctx, s, src1, lp1, N, b1.B0, nang, ws, &RZ1, kTsqrLeaf);
     if (st != TT_OK) return st;
   } else if (!ws.dry) {
     tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, src1, lp1, N, leaf_cap<T>(ctx), b1.tsqr_a, b1.tsqr_b, &RZ1);
@@ -370,6 +424,10 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
       double* RZ2 = nullptr;
       st = gram_factor(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, ws, ctx->ctrl, ctx->coop_grid_max, &RZ2);
       if (st != TT_OK) return st;
+    } else if (rnd) {
+      double* RZ2 = nullptr;
+      st = randomized_factor<S, T>(ctx, s, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.B0, nang, ws, &RZ2, kTsqrLeafSrc);
+      if (st != TT_OK) return st;
     }
     return small_round(s, ctx->num_sms, j2, ws);
   }
@@ -393,6 +451,8 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   if (gram)
     st = gram_factor(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, ws, ctx->ctrl, ctx->coop_grid_max, &RZ2,
                      kTsqrLeafSrc);
+  else if (rnd)
+    st = randomized_factor<S, T>(ctx, s, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.B0, nang, ws, &RZ2, kTsqrLeafSrc);
   else
     st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, leaf_cap<T>(ctx), b2.tsqr_a,
                                       b2.tsqr_b, &RZ2, kTsqrLeafSrc);
