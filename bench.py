@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gram", action="store_true", help="skip the FP64 leg with Gram rounding")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="time the default TSQR kernels instead of the autotuned choice (tt_autotune)")
     ap.add_argument("--workload", default="plane", choices=["plane", "batched"],
                     help="plane: the 128x128 single-problem step (the headline line); batched: the "
                          "256-problem batch stepped as one CUDA graph (a separate measurement)")
@@ -184,6 +186,10 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     for _ in range(args.warmup):
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
     ctx.sync()
+    tune = None
+    if rounding == "tsqr" and not args.no_autotune:
+        # TSQR kernels and leaf counts for this state's shape, timed on a copy of it
+        tune = ctx.autotune(plan, x, wl.tol, wl.rmax, precision, steps=2)
     ranks = [x.ranks()]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     clocks = Clocks(clocks_index)
@@ -231,6 +237,8 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
            "breakdown_ms_per_step": {k: v / args.steps for k, v in kms.items()},
            "gpu_launches": int(sum(klaunch.values())), "clocks": clk, "ranks": r_seq[-1],
            "rank_history": [r[1:-1] for r in r_seq], "jacobi": diag}
+    if tune is not None:
+        out["tsqr_autotune"] = tune
     leaf_tf = leaf_flops / (kms["tsqr_leaf"] / 1e3) / 1e12 if kms["tsqr_leaf"] > 0 else None
     if precision == "fp64":
         peak, src, bound = FP64_PEAK_TFLOPS, ("FP64 FMA units: 152 SMs x 2/clk x 2 flop x 2070 MHz "
@@ -238,8 +246,12 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     else:
         peak, src, bound = FP32_PEAK_TFLOPS, ("FP32 FMA units: 152 SMs x 128/clk x 2 flop x 2070 MHz "
                                               "(no FP32 entry in MEASURED_PEAKS.json)"), "alu"
-    traffic = LEAF_TRAFFIC.get(precision) if args.size == "full" else None
-    out["roofline"] = {"kernel": "k_tsqr_leaf over the transport sum (one launch per step, R1 = 5r columns)",
+    variant = tune["transport"][0] if tune is not None else "column"
+    kname = {"column": "k_tsqr_leaf", "rowsplit": "k_tsqr_leaf_rs",
+             "column_dense": "k_tsqr_leaf (32-row blocks, 4 CTAs/SM)"}[variant]
+    # ncu traffic was taken on the column-owner kernel; another kernel has no counters yet
+    traffic = LEAF_TRAFFIC.get(precision) if (args.size == "full" and variant == "column") else None
+    out["roofline"] = {"kernel": kname + " over the transport sum (one launch per step, R1 = 5r columns)",
                        "bound": bound, "achieved": leaf_tf, "peak": peak, "unit": "TFLOP/s",
                        "frac": (leaf_tf / peak) if leaf_tf else None,
                        "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None,
@@ -301,10 +313,12 @@ def run_ours(args):
             "breakdown_ms_per_step": R["breakdown_ms_per_step"], "gpu_launches": R["gpu_launches"],
             "clocks": R["clocks"], "ranks": R["ranks"], "rank_history": R["rank_history"],
             "jacobi": R["jacobi"]}
+    if "tsqr_autotune" in R:
+        line["tsqr_autotune"] = R["tsqr_autotune"]
     if "fp64" in results and head != "fp64":
         F = results["fp64"]
         line["fp64"] = {k: F[k] for k in ("value", "ms_per_step", "tflops", "roofline", "breakdown_ms_per_step",
-                                          "gpu_launches", "ranks", "jacobi")}
+                                          "gpu_launches", "ranks", "jacobi", "tsqr_autotune") if k in F}
         line["speedup_mixed_over_fp64"] = R["value"] / F["value"]
         Em = tt.tt_energy_density(ctx, plan, states["mixed"]).cpu().numpy()
         Ed = tt.tt_energy_density(ctx, plan, states["fp64"]).cpu().numpy()

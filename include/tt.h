@@ -157,6 +157,35 @@ tt_status tt_context_set_rounding(tt_context *ctx, tt_rounding method);
  * used at every rounding; a call whose angular size differs from nang fails with TT_ERR_SHAPE. */
 tt_status tt_context_set_sketch(tt_context *ctx, const double *omega_dev, int32_t nang, int32_t ell);
 
+/* Kernels of the tall-skinny QR over the merged core (the first sweep of the rounding, Sec. 3.1
+ * footnote), per pass shape: for passes of ncap columns at precision prec (TT_PREC_FP64: FP64
+ * passes; TT_PREC_MIXED: FP32 passes):
+ *   variant 0: one thread per column (the default; at most 256 threads, i.e. ncap <= 256);
+ *   variant 1: four lanes per column, each holding a quarter of the rows of a block (4 ncap <= 1024);
+ *   variant 2: FP32 only, one thread per column over 32-row blocks with registers held so that
+ *              four CTAs share an SM (ncap <= 160).
+ * A variant that cannot take the shape runs variant 0.  leaves = cap on the TSQR leaves: <= 0 gives the default wave (2 CTAs per SM for
+ * FP64, 3 for FP32); larger caps are clamped to 4 per SM.  The choice changes the order of
+ * rounding errors only.  ncap <= 0 clears every entry.  tt_context_get_tsqr reports what a pass
+ * of ncap columns would run.  The paper has no counterpart: these are launch-shape choices. */
+tt_status tt_context_set_tsqr(tt_context *ctx, tt_precision prec, int32_t ncap, int32_t variant, int32_t leaves);
+tt_status tt_context_get_tsqr(const tt_context *ctx, tt_precision prec, int32_t ncap, int32_t *variant,
+                              int32_t *leaves);
+
+/* Autotune the TSQR choice (tt_context_set_tsqr) of the two passes of tt_step for state I with
+ * this plan, tolerance and precision: the transport-sum pass ((2 d_X + 1) rcap_1 + n_b columns)
+ * and the source pass (rcap_1 + 1 columns).  Each candidate (variant x leaf cap, one pass at a
+ * time, the other at its best so far) is timed with CUDA events over `steps` (1..64) tt_steps,
+ * after one untimed step, on a device copy of I; I itself is not modified, and a coupled plan's
+ * material temperature is restored afterwards.  The fastest entries are stored in the context.
+ * Synchronous; allocates the copy with cudaMalloc, so never under stream capture (TT_ERR_ARG).
+ * chosen[4] (host, nullable): variant and leaf cap of the transport pass, then of the source
+ * pass; ms[2] (host, nullable): ms per step with the defaults and with the choice.  Only the
+ * TSQR rounding has these passes (TT_ERR_UNSUPPORTED under another tt_rounding).  The paper has
+ * no counterpart. */
+tt_status tt_autotune(tt_context *ctx, const tt_plan *plan, const tt_tensor *I, double tol, int32_t rmax,
+                      tt_precision prec, int32_t steps, int32_t *chosen, float *ms);
+
 /* Synchronise the context stream and report, per tt_timer category, the summed kernel time
  * in milliseconds (ms[TT_TIMER_COUNT], nullable) and the number of kernel launches
  * (launches[TT_TIMER_COUNT], nullable) since the last reset; reset != 0 clears both. */
@@ -217,7 +246,10 @@ tt_status tt_round(tt_context *ctx, tt_tensor *x, double rel_tol, int32_t rmax, 
 tt_status tt_apply_transport(tt_context *ctx, const tt_plan *plan, const tt_tensor *in, tt_tensor *out);
 
 /* One time step in place (end of Sec. 3.1): transport, round, source (Eq. discRTsource at
- * fixed T), round, all on the device without materialising the transport sum.
+ * fixed T), round, all on the device without materialising the transport sum.  Under
+ * TT_ROUND_TSQR the QR passes over the merged core take at most 256 columns:
+ * (2 d_X + 1) rcap_1 + n_b <= 256 (n_b inflow faces), else TT_ERR_UNSUPPORTED before the state
+ * is touched (tt_round: rcap_1 <= 256).
  * energy_dev (nullable, device double[4]) receives the radiation energy before and after
  * the step, the energy of the post-transport tensor, and the absorption-emission exchange
  * (4 pi / c) sum dV c dt rho kappa_a (eps - J^{m+1}). */

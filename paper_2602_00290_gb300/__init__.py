@@ -34,7 +34,9 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_apply_transport", "tt_step", "tt_energy_density", "tt_context_set_timing",
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
            "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding",
-           "tt_internal_ranks", "tt_context_set_sketch")
+           "tt_internal_ranks", "tt_context_set_sketch", "tt_context_set_tsqr", "tt_context_get_tsqr",
+           "tt_autotune")
+TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2}
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
 
@@ -107,6 +109,10 @@ def lib():
             "tt_batch_destroy": [vp],
             "tt_context_set_rounding": [vp, ctypes.c_int],
             "tt_context_set_sketch": [vp, vp, ctypes.c_int32, ctypes.c_int32],
+            "tt_context_set_tsqr": [vp, ctypes.c_int, i32, i32, i32],
+            "tt_context_get_tsqr": [vp, ctypes.c_int, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
+            "tt_autotune": [vp, vp, ctypes.POINTER(_Tensor), dbl, i32, ctypes.c_int, i32, ctypes.POINTER(i32),
+                            ctypes.POINTER(ctypes.c_float)],
             "tt_internal_ranks": [vp, vp, ctypes.POINTER(_Tensor), ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int64],
@@ -167,6 +173,34 @@ class Context:
         """"tsqr" (Householder TSQR, default), "gram" (Gram matrix + pivoted-Cholesky root) or
         "randomized" (sketch of set_sketch, TSQR of the sketch, C = Q^T A)."""
         _check(lib().tt_context_set_rounding(self.handle, ROUNDINGS[method]), "tt_context_set_rounding")
+
+    def set_tsqr(self, prec: str, ncap: int, variant: str = "column", leaves: int = 0):
+        """TSQR kernels for passes of ncap columns at precision prec ("fp64" / "mixed"):
+        variant "column" (one thread per column), "rowsplit" (four lanes per column) or
+        "column_dense" (FP32, 32-row blocks, four CTAs per SM), leaves = cap on the TSQR leaves
+        (0: the default wave).  ncap <= 0 clears every entry."""
+        _check(lib().tt_context_set_tsqr(self.handle, PRECISIONS[prec], int(ncap), TSQR_VARIANTS[variant],
+                                         int(leaves)), "tt_context_set_tsqr")
+
+    def get_tsqr(self, prec: str, ncap: int):
+        """(variant, leaf cap) a pass of ncap columns at precision prec runs with."""
+        v, l = ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().tt_context_get_tsqr(self.handle, PRECISIONS[prec], int(ncap), ctypes.byref(v), ctypes.byref(l)),
+               "tt_context_get_tsqr")
+        names = {i: k for k, i in TSQR_VARIANTS.items()}
+        return names[v.value], l.value
+
+    def autotune(self, plan: "Plan", I: "TT", tol: float, rmax: int, prec: str = "mixed", steps: int = 3):
+        """Time the TSQR choices of tt_step's two passes on a copy of I and keep the fastest
+        (tt_autotune).  Returns {"transport": (variant, leaves), "source": (...),
+        "ms_default": ..., "ms_tuned": ...}."""
+        ch = (ctypes.c_int32 * 4)()
+        ms = (ctypes.c_float * 2)()
+        _check(lib().tt_autotune(self.handle, plan.handle, ctypes.byref(I._struct()), float(tol), int(rmax),
+                                 PRECISIONS[prec], int(steps), ch, ms), "tt_autotune")
+        names = {i: k for k, i in TSQR_VARIANTS.items()}
+        return {"transport": (names[ch[0]], ch[1]), "source": (names[ch[2]], ch[3]),
+                "ms_default": float(ms[0]), "ms_tuned": float(ms[1])}
 
     def set_timing(self, enable: bool):
         _check(lib().tt_context_set_timing(self.handle, 1 if enable else 0), "tt_context_set_timing")

@@ -8,6 +8,7 @@
 #include "instr.cuh"
 #include "small.cuh"
 #include "step.cuh"
+#include "tune.cuh"
 
 namespace ttk {
 thread_local Instr* g_instr = nullptr;
@@ -114,20 +115,27 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->sketch = nullptr;
   ctx->sketch_nang = 0;
   ctx->sketch_ell = 0;
+  ctx->tune = new ttk::TsqrTune();
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
+    delete ttk::tune_of(ctx);
+    delete static_cast<ttk::Instr*>(ctx->instr);
     delete ctx;
     return TT_ERR_CUDA;
   }
   cudaMemsetAsync(ctx->ctrl, 0, sizeof(ttk::DevCtrl), ctx->stream);
   if (workspace_bytes > 0 && ensure_ws(ctx, workspace_bytes) != TT_OK) {
     cudaFree(ctx->ctrl);
+    delete ttk::tune_of(ctx);
+    delete static_cast<ttk::Instr*>(ctx->instr);
     delete ctx;
     return TT_ERR_CUDA;
   }
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
     cudaFree(ctx->ctrl);
+    delete ttk::tune_of(ctx);
+    delete static_cast<ttk::Instr*>(ctx->instr);
     delete ctx;
     return TT_ERR_CUDA;
   }
@@ -144,6 +152,7 @@ tt_status tt_context_destroy(tt_context* ctx) {
   ttk::Instr* in = static_cast<ttk::Instr*>(ctx->instr);
   for (cudaEvent_t e : in->pool) cudaEventDestroy(e);
   delete in;
+  delete ttk::tune_of(ctx);
   delete ctx;
   return TT_OK;
 }

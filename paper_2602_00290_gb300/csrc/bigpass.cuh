@@ -185,12 +185,35 @@ __device__ __forceinline__ void ld4(const double* p, double (&v)[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+// Quotient on the reflector chain: FP32 takes the fast reciprocal-based divide (2 ulp; both
+// divisors are at least sqrt(x2) >= 3.7e-23 and below the FP32 overflow range), FP64 the
+// IEEE one.
+template <typename T>
+__device__ __forceinline__ T chain_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float chain_div<float>(float a, float b) { return __fdividef(a, b); }
+
+// Live test of reflector j without a division per step: (block, offset) of j advanced with j.
+struct LiveWalk {
+  int t, o;
+  __device__ __forceinline__ LiveWalk(const LivePattern& lp, int j) : t(j / lp.rcap), o(j - (j / lp.rcap) * lp.rcap) {}
+  __device__ __forceinline__ bool next(const LivePattern& lp, int r) {
+    const bool live = (t < lp.nblk) ? (o < r) : true;
+    if (++o == lp.rcap) {
+      o = 0;
+      ++t;
+    }
+    return live;
+  }
+};
+
 template <typename T, int BR>
 __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, T* taub, int& buf,
                                           int jbeg, const LivePattern& lp, int r, bool mycol) {
   const int c = threadIdx.x;
+  LiveWalk walk(lp, jbeg);
   for (int j = jbeg; j < ncap; ++j) {
-    if (!lp.live(j, r)) continue;
+    if (!walk.next(lp, r)) continue;
     T* vb = vbuf + buf * BR;
     if (c == j) {
       T xp[4] = {T(0), T(0), T(0), T(0)};
@@ -203,10 +226,10 @@ __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, 
         const T alpha = *rjj;
         const T nrm = sqrt(alpha * alpha + x2);
         const T beta = (alpha >= T(0)) ? -nrm : nrm;
-        const T sc = T(1) / (alpha - beta);
+        const T sc = chain_div<T>(T(1), alpha - beta);
 #pragma unroll
         for (int i = 0; i < BR; ++i) vb[i] = B[i] * sc;
-        tau = (beta - alpha) / beta;
+        tau = chain_div<T>(beta - alpha, beta);
         *rjj = beta;
 #pragma unroll
         for (int i = 0; i < BR; ++i) B[i] = T(0);
@@ -245,9 +268,9 @@ __host__ __device__ inline size_t tsqr_smem_bytes(int ncap) {
   return sizeof(T) * (tsqr_r_elems(ncap) + 2 * BR + 4);
 }
 
-template <typename T, int BR, class Src>
-__global__ void __launch_bounds__(256) k_tsqr_leaf(Src src, LivePattern lp, long nrows, long rpc,
-                                                   double* __restrict__ Rout) {
+template <typename T, int BR, class Src, int MAXT = 256, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) k_tsqr_leaf(Src src, LivePattern lp, long nrows, long rpc,
+                                                          double* __restrict__ Rout) {
   extern __shared__ __align__(16) unsigned char tsqr_smem[];
   const int ncap = lp.ncap();
   T* Rs = reinterpret_cast<T*>(tsqr_smem);
@@ -312,16 +335,22 @@ __global__ void __launch_bounds__(256) k_tsqr_merge(LivePattern lp, int nin, con
 
 // Host driver: leaves then merge levels; returns the device pointer of the final R
 // (ncap x ncap, row-major, upper triangular) inside ws_a or ws_b.
-template <typename T, int BR, class Src>
+// Leaf kernels are instantiated with launch bounds (MAXT threads, MINB resident CTAs; FP32 by
+// default at most 128 registers, so that three 160-thread CTAs share an SM); the leaf count is
+// capped by the CTAs that are resident at once.
+template <typename T, int BR, int MAXT = 256, int MINB = (sizeof(T) == 4 ? 2 : 1), class Src>
 tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows, int max_leaves,
                    double* ws_a, double* ws_b, double** Rfinal, int leaf_cat = kTsqrLeaf) {
   const int ncap = lp.ncap();
   const size_t smem = tsqr_smem_bytes<T, BR>(ncap);
   if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
   const int threads = ((ncap + 31) / 32) * 32;
-  if (threads > 1024) return TT_ERR_UNSUPPORTED;
+  if (threads > MAXT || threads > 256) return TT_ERR_UNSUPPORTED;
   static_assert(BR > 0, "block rows");
-  const int per_sm = (int)((228 * 1024) / (smem + 1024));
+  auto leaf = k_tsqr_leaf<T, BR, Src, MAXT, MINB>;
+  cudaFuncSetAttribute(leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf, threads, smem) != cudaSuccess) return TT_ERR_CUDA;
   long L = (nrows + BR - 1) / BR;
   long cap = (long)num_sms * (per_sm > 0 ? per_sm : 1);
   if (max_leaves > 0 && cap > max_leaves) cap = max_leaves;
@@ -331,11 +360,13 @@ tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, 
   rpc = ((rpc + BR - 1) / BR) * BR;
   L = (nrows + rpc - 1) / rpc;
   if (L < 1) L = 1;
-  cudaFuncSetAttribute(k_tsqr_leaf<T, BR, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(k_tsqr_merge<T, BR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  constexpr int MBR = sizeof(T) == 4 ? 64 : 32;  // rows the merge tree absorbs at a time
+  const size_t msmem = tsqr_smem_bytes<T, MBR>(ncap);
+  if (msmem > 227 * 1024) return TT_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(k_tsqr_merge<T, MBR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
   {
     TimerScope scope(leaf_cat, s);
-    k_tsqr_leaf<T, BR, Src><<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
+    leaf<<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
   }
   TimerScope scope(kTsqrMerge, s);
   double* in = ws_a;
@@ -343,7 +374,7 @@ tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, 
   int n = (int)L;
   while (n > 1) {
     const int m = (n + 1) / 2;
-    k_tsqr_merge<T, BR><<<m, threads, smem, s>>>(lp, n, in, out); count_launch();
+    k_tsqr_merge<T, MBR><<<m, threads, msmem, s>>>(lp, n, in, out); count_launch();
     double* t = in;
     in = out;
     out = t;

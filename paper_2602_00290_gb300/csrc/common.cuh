@@ -101,6 +101,7 @@ struct tt_context {
   int rounding;       // tt_rounding of tt_round / tt_step
   const double* sketch;  // randomized rounding: omega (sketch_nang x sketch_ell, device, caller-owned)
   int sketch_nang, sketch_ell;
+  void* tune;  // ttk::TsqrTune, TSQR kernel choice per shape (owned; batch views share it)
 };
 
 struct tt_plan {

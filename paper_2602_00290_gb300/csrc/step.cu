@@ -9,6 +9,8 @@
 #include "rand.cuh"
 #include "small.cuh"
 #include "step.cuh"
+#include "tsqr_rs.cuh"
+#include "tune.cuh"
 
 namespace ttk {
 namespace {
@@ -195,6 +197,32 @@ inline int leaf_cap(const tt_context* ctx) {
   return (ctx->tsqr_leaf_cap > 0 && ctx->tsqr_leaf_cap < full) ? ctx->tsqr_leaf_cap : full;
 }
 
+// TSQR kernels and leaf cap for an ncap-column pass (the context's tuned entry, if any).
+template <typename T>
+inline TsqrCfg tsqr_cfg(const tt_context* ctx, int ncap) {
+  return resolve_tsqr(ctx, (int)sizeof(T), ncap, leaf_cap<T>(ctx));
+}
+
+// Leaves that any TSQR variant may launch over nrows rows (workspace bound): the 32-row blocks
+// of the smallest variant.
+template <typename T>
+inline long tsqr_leaf_bound(int num_sms, int ncap, long nrows, int max_leaves) {
+  return tsqr_max_leaves<T, 32>(num_sms, ncap, nrows, max_leaves);
+}
+
+template <typename T, class Src>
+inline tt_status run_tsqr_cfg(const TsqrCfg& cfg, cudaStream_t s, int num_sms, const Src& src, LivePattern lp,
+                              long nrows, double* ws_a, double* ws_b, double** Rfinal, int leaf_cat = kTsqrLeaf) {
+  constexpr int BR = BigBR<T>::value;
+  if (cfg.variant == kTsqrRowSplit)
+    return run_tsqr_rs<T, BR, 4>(s, num_sms, src, lp, nrows, cfg.leaves, ws_a, ws_b, Rfinal, leaf_cat);
+  if constexpr (sizeof(T) == 4) {
+    if (cfg.variant == kTsqrColumnDense)
+      return run_tsqr<T, 32, 160, 4>(s, num_sms, src, lp, nrows, cfg.leaves, ws_a, ws_b, Rfinal, leaf_cat);
+  }
+  return run_tsqr<T, BR>(s, num_sms, src, lp, nrows, cfg.leaves, ws_a, ws_b, Rfinal, leaf_cat);
+}
+
 // Workspace carving shared by dry runs (size queries) and real runs.
 struct RoundBufs {
   double* tsqr_a;
@@ -212,7 +240,7 @@ template <typename T>
 static RoundBufs take_round_bufs(Bump& ws, int num_sms, int max_leaves, int d, int R, long nrows, int n1, int n2,
                                  int K1, int K2, int rcapin1) {
   RoundBufs b;
-  const long L = tsqr_max_leaves<T, BigBR<T>::value>(num_sms, R, nrows, max_leaves);
+  const long L = tsqr_leaf_bound<T>(num_sms, R, nrows, max_leaves);
   b.tsqr_a = ws.take<double>((size_t)L * R * R);
   b.tsqr_b = ws.take<double>((size_t)((L + 1) / 2) * R * R);
   b.Bbase = ws.take<double>((size_t)rcapin1 * n1 * n2);
@@ -237,7 +265,8 @@ static tt_status randomized_factor(tt_context* ctx, cudaStream_t s, const Src& s
   const int l = ctx->sketch_ell < R ? ctx->sketch_ell : R;
   double* Op = ws.take<double>((size_t)R * l);
   S* Y = ws.take<S>((size_t)N * l);
-  const long L = tsqr_max_leaves<T, BigBR<T>::value>(ctx->num_sms, l, N, leaf_cap<T>(ctx));
+  const TsqrCfg ycfg = tsqr_cfg<T>(ctx, l);
+  const long L = tsqr_leaf_bound<T>(ctx->num_sms, l, N, ycfg.leaves);
   double* ta = ws.take<double>((size_t)L * l * l);
   double* tb = ws.take<double>((size_t)((L + 1) / 2) * l * l);
   const int nbi = (l + 63) / 64, nbj = (R + 63) / 64;
@@ -257,8 +286,8 @@ static tt_status randomized_factor(tt_context* ctx, cudaStream_t s, const Src& s
   tt_status st = launch_update<T>(s, ctx->num_sms, src, lp, N, Op, l, EpiPlain<S>{Y, l}, nullptr, nullptr);
   if (st != TT_OK) return st;
   double* RY = nullptr;
-  st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Y, l}, LivePattern{nullptr, l, 1, 0}, N,
-                                    leaf_cap<T>(ctx), ta, tb, &RY, timer_cat);
+  st = run_tsqr_cfg<T>(ycfg, s, ctx->num_sms, SrcRows<S>{Y, l}, LivePattern{nullptr, l, 1, 0}, N, ta, tb, &RY,
+                       timer_cat);
   if (st != TT_OK) return st;
   const long sb = (N + 127) / 128 < 4096 ? (N + 127) / 128 : 4096;
   k_rand_solve<<<(unsigned)sb, 128, sizeof(double) * (size_t)l * l, s>>>(
@@ -279,7 +308,8 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   const int K1 = x->rcap[1], K2 = (d == 3) ? x->rcap[2] : 1;
   LivePattern lp{x->rank + 1, K1, 1, 0};
   const int R = lp.ncap();
-  RoundBufs b = take_round_bufs<T>(ws, ctx->num_sms, leaf_cap<T>(ctx), d, R, N, n1, n2, K1, K2, K1);
+  const TsqrCfg cfg = tsqr_cfg<T>(ctx, R);
+  RoundBufs b = take_round_bufs<T>(ws, ctx->num_sms, cfg.leaves, d, R, N, n1, n2, K1, K2, K1);
   SmallJob job{};
   job.d = d;
   job.n1 = n1;
@@ -319,8 +349,8 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
                                            &RZ, kTsqrLeaf);
     if (st != TT_OK) return st;
   } else if (!ws.dry) {
-    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, leaf_cap<T>(ctx), b.tsqr_a,
-                                         b.tsqr_b, &RZ);
+    tt_status st = run_tsqr_cfg<T>(cfg, s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.tsqr_a,
+                                   b.tsqr_b, &RZ);
     if (st != TT_OK) return st;
   }
   job.RZ = RZ;
@@ -347,7 +377,8 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   // ---- first rounding: the transport sum, never materialised
   LivePattern lp1{I->rank + 1, K1, p->nterm + 1, p->nbc};
   const int R1 = lp1.ncap();
-  RoundBufs b1 = take_round_bufs<T>(ws, ctx->num_sms, leaf_cap<T>(ctx), d, R1, N, n1, n2, K1, K2, K1);
+  const TsqrCfg cfg1 = tsqr_cfg<T>(ctx, R1);
+  RoundBufs b1 = take_round_bufs<T>(ws, ctx->num_sms, cfg1.leaves, d, R1, N, n1, n2, K1, K2, K1);
   S* Zsrc = ws.take<S>((size_t)N * (K1 + 1));
   const long ngrid = (N + 31) / 32;  // bounds the persistent update grids (tiles of >= 32 rows)
   double* part1 = ws.take<double>((size_t)2 * ngrid);
@@ -402,7 +433,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     tt_status st = randomized_factor<S, T>(ctx, s, src1, lp1, N, b1.B0, nang, ws, &RZ1, kTsqrLeaf);
     if (st != TT_OK) return st;
   } else if (!ws.dry) {
-    tt_status st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, src1, lp1, N, leaf_cap<T>(ctx), b1.tsqr_a, b1.tsqr_b, &RZ1);
+    tt_status st = run_tsqr_cfg<T>(cfg1, s, ctx->num_sms, src1, lp1, N, b1.tsqr_a, b1.tsqr_b, &RZ1);
     if (st != TT_OK) return st;
   }
   j1.RZ = RZ1;
@@ -410,7 +441,8 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   if (st != TT_OK) return st;
   // ---- source step fused into the write of the rounded transport update
   LivePattern lp2{nullptr, K1, 1, 1};
-  RoundBufs b2 = take_round_bufs<T>(ws, ctx->num_sms, leaf_cap<T>(ctx), d, lp2.ncap(), N, n1, n2, K1, K2, K1);
+  const TsqrCfg cfg2 = tsqr_cfg<T>(ctx, lp2.ncap());
+  RoundBufs b2 = take_round_bufs<T>(ws, ctx->num_sms, cfg2.leaves, d, lp2.ncap(), N, n1, n2, K1, K2, K1);
   double *cpl_u = nullptr, *jstar = nullptr, *jnew = nullptr;
   if (p->coupled) {
     cpl_u = ws.take<double>(R1);
@@ -454,8 +486,8 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   else if (rnd)
     st = randomized_factor<S, T>(ctx, s, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.B0, nang, ws, &RZ2, kTsqrLeafSrc);
   else
-    st = run_tsqr<T, BigBR<T>::value>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, leaf_cap<T>(ctx), b2.tsqr_a,
-                                      b2.tsqr_b, &RZ2, kTsqrLeafSrc);
+    st = run_tsqr_cfg<T>(cfg2, s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.tsqr_a, b2.tsqr_b, &RZ2,
+                         kTsqrLeafSrc);
   if (st != TT_OK) return st;
   SmallJob j2 = j1;
   j2.lp = lp2;

@@ -1,0 +1,245 @@
+// Row-split Householder TSQR: the same reflector sequence as the column-owner leaf and merge
+// of bigpass.cuh (one reflector per live column, R kept packed in shared memory), with QS
+// consecutive lanes sharing a column.  Lane q of a column group holds rows q*RPT .. q*RPT+RPT-1
+// of the current block of BR rows in registers; norms and reflector dots are partial sums over
+// those rows, combined by an xor butterfly inside the group (every lane ends with the same
+// bits).  Against one thread per column this cuts the dependent chain of each reflector by QS
+// and keeps QS times as many warps busy to the right of the pivot.
+#pragma once
+#include "bigpass.cuh"
+
+namespace ttk {
+
+template <typename T, int BR, int QS>
+struct RsGeom {
+  static_assert(BR % (4 * QS) == 0, "rows per lane must be a multiple of 4");
+  static_assert(QS == 2 || QS == 4 || QS == 8, "group size");
+  static constexpr int RPT = BR / QS;  // rows a lane holds
+  static constexpr int SS = RPT + 4;   // reflector segment stride: the QS segments start on distinct banks
+};
+
+// packed R, the double-buffered reflector (QS segments each), two scalars, BR row flags
+template <typename T, int BR, int QS>
+__host__ __device__ inline size_t tsqr_rs_smem_bytes(int ncap) {
+  return sizeof(T) * (tsqr_r_elems(ncap) + 2 * QS * RsGeom<T, BR, QS>::SS + 4) + sizeof(unsigned) * BR;
+}
+template <int QS>
+__host__ __device__ inline int tsqr_rs_threads(int ncap) {
+  return ((ncap * QS + 31) / 32) * 32;
+}
+
+template <typename T>
+__device__ __forceinline__ void st4(T* p, T a, T b, T c, T d);
+template <>
+__device__ __forceinline__ void st4<float>(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void st4<double>(double* p, double a, double b, double c, double d) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+}
+
+template <typename T, int QS>
+__device__ __forceinline__ T group_sum(T v, unsigned gm) {
+#pragma unroll
+  for (int o = 1; o < QS; o <<= 1) v += __shfl_xor_sync(gm, v, o);
+  return v;
+}
+
+// Absorb a block held as B (rows of this lane's segment, column c) into the packed R.
+// Reflectors jbeg..ncap-1; column j's reflector is formed by its group, lane 0 of the group
+// owning R[.][c]; one barrier per reflector.
+template <typename T, int BR, int QS>
+__device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T* vbuf, T* taub, int& buf,
+                                             int jbeg, const LivePattern& lp, int r, bool mycol, int c, int q,
+                                             unsigned gm) {
+  constexpr int RPT = RsGeom<T, BR, QS>::RPT, SS = RsGeom<T, BR, QS>::SS;
+  const int lead = (threadIdx.x & 31) & ~(QS - 1);
+  LiveWalk walk(lp, jbeg);
+  for (int j = jbeg; j < ncap; ++j) {
+    if (!walk.next(lp, r)) continue;
+    T* vb = vbuf + buf * (QS * SS);
+    if (c == j) {
+      T xp[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) xp[i & 3] += B[i] * B[i];
+      const T x2 = group_sum<T, QS>((xp[0] + xp[1]) + (xp[2] + xp[3]), gm);
+      T tau = T(0);
+      if (x2 > T(0)) {
+        T sc = T(0);
+        if (q == 0) {
+          T* rjj = Rs + tri_off(j, ncap);
+          const T alpha = *rjj;
+          const T nrm = sqrt(alpha * alpha + x2);
+          const T beta = (alpha >= T(0)) ? -nrm : nrm;
+          sc = chain_div<T>(T(1), alpha - beta);
+          tau = chain_div<T>(beta - alpha, beta);
+          *rjj = beta;
+        }
+        sc = __shfl_sync(gm, sc, lead);
+        T* seg = vb + q * SS;
+#pragma unroll
+        for (int i = 0; i < RPT; i += 4) st4<T>(seg + i, B[i] * sc, B[i + 1] * sc, B[i + 2] * sc, B[i + 3] * sc);
+#pragma unroll
+        for (int i = 0; i < RPT; ++i) B[i] = T(0);
+      }
+      if (q == 0) taub[buf] = tau;
+    }
+    __syncthreads();
+    const T tau = taub[buf];
+    if (tau != T(0) && c > j && mycol) {
+      T v[RPT];
+      const T* seg = vb + q * SS;
+#pragma unroll
+      for (int i = 0; i < RPT; i += 4) {
+        T t4[4];
+        ld4(seg + i, t4);
+        v[i] = t4[0];
+        v[i + 1] = t4[1];
+        v[i + 2] = t4[2];
+        v[i + 3] = t4[3];
+      }
+      T* rjc = Rs + tri_off(j, ncap) + (c - j);
+      T wp[4] = {q == 0 ? *rjc : T(0), T(0), T(0), T(0)};
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) wp[i & 3] += v[i] * B[i];
+      T wv = group_sum<T, QS>((wp[0] + wp[1]) + (wp[2] + wp[3]), gm);
+      wv *= tau;
+      if (q == 0) *rjc -= wv;
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) B[i] -= wv * v[i];
+    }
+    buf ^= 1;
+  }
+}
+
+template <typename T, int BR, int QS, class Src>
+__global__ void __launch_bounds__(1024) k_tsqr_leaf_rs(Src src, LivePattern lp, long nrows, long rpc,
+                                                       double* __restrict__ Rout) {
+  extern __shared__ __align__(16) unsigned char tsqr_smem[];
+  constexpr int RPT = RsGeom<T, BR, QS>::RPT, SS = RsGeom<T, BR, QS>::SS;
+  const int ncap = lp.ncap();
+  T* Rs = reinterpret_cast<T*>(tsqr_smem);
+  T* vbuf = Rs + tsqr_r_elems(ncap);
+  T* taub = vbuf + 2 * QS * SS;
+  unsigned* flags = reinterpret_cast<unsigned*>(taub + 4);
+  const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
+  for (int i = threadIdx.x; i < ncap * (ncap + 1) / 2; i += blockDim.x) Rs[i] = T(0);
+  const int c = threadIdx.x / QS, q = threadIdx.x % QS;
+  const unsigned gm = ((1u << QS) - 1u) << ((threadIdx.x & 31) & ~(QS - 1));
+  const bool mycol = (c < ncap) && lp.live(c, r);
+  const auto cc = src.col(c < ncap ? c : 0);
+  const long beg = (long)blockIdx.x * rpc;
+  const long end = (beg + rpc < nrows) ? beg + rpc : nrows;
+  int buf = 0;
+  for (long r0 = beg; r0 < end; r0 += BR) {
+    __syncthreads();  // the previous block's loads of `flags` are done
+    for (int i = threadIdx.x; i < BR; i += blockDim.x) flags[i] = (r0 + i < end) ? src.row_flags(r0 + i) : 0u;
+    __syncthreads();
+    T B[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int ii = q * RPT + i;
+      B[i] = (mycol && r0 + ii < end) ? src.template loadT<T>(cc, r0 + ii, flags[ii]) : T(0);
+    }
+    hh_absorb_rs<T, BR, QS>(Rs, ncap, B, vbuf, taub, buf, 0, lp, r, mycol, c, q, gm);
+  }
+  __syncthreads();
+  write_R<T, BR>(Rs, ncap, Rout + (size_t)blockIdx.x * ncap * ncap);
+}
+
+// One level of the binary merge tree, row-split: output m = QR([R_{2m}; R_{2m+1}]).R
+template <typename T, int BR, int QS>
+__global__ void __launch_bounds__(1024) k_tsqr_merge_rs(LivePattern lp, int nin, const double* __restrict__ Rin,
+                                                        double* __restrict__ Rout) {
+  extern __shared__ __align__(16) unsigned char tsqr_smem[];
+  constexpr int RPT = RsGeom<T, BR, QS>::RPT, SS = RsGeom<T, BR, QS>::SS;
+  const int ncap = lp.ncap();
+  const size_t nn = (size_t)ncap * ncap;
+  const int a = 2 * blockIdx.x, b = a + 1;
+  const double* Ra = Rin + (size_t)a * nn;
+  double* Ro = Rout + (size_t)blockIdx.x * nn;
+  if (b >= nin) {
+    for (size_t i = threadIdx.x; i < nn; i += blockDim.x) Ro[i] = Ra[i];
+    return;
+  }
+  const double* Rb = Rin + (size_t)b * nn;
+  T* Rs = reinterpret_cast<T*>(tsqr_smem);
+  T* vbuf = Rs + tsqr_r_elems(ncap);
+  T* taub = vbuf + 2 * QS * SS;
+  const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
+  for (int idx = threadIdx.x; idx < ncap * ncap; idx += blockDim.x) {
+    const int i = idx / ncap, j = idx - (idx / ncap) * ncap;
+    if (j >= i) Rs[tri_off(i, ncap) + (j - i)] = (T)Ra[idx];
+  }
+  const int c = threadIdx.x / QS, q = threadIdx.x % QS;
+  const unsigned gm = ((1u << QS) - 1u) << ((threadIdx.x & 31) & ~(QS - 1));
+  const bool mycol = (c < ncap) && lp.live(c, r);
+  __syncthreads();
+  int buf = 0;
+  for (int i0 = 0; i0 < ncap; i0 += BR) {
+    T B[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) {
+      const int row = i0 + q * RPT + i;
+      B[i] = (mycol && row < ncap) ? (T)Rb[(size_t)row * ncap + c] : T(0);
+    }
+    // rows i0.. of an upper-triangular factor vanish in columns < i0
+    hh_absorb_rs<T, BR, QS>(Rs, ncap, B, vbuf, taub, buf, i0, lp, r, mycol, c, q, gm);
+  }
+  __syncthreads();
+  write_R<T, BR>(Rs, ncap, Ro);
+}
+
+// Host driver of the row-split TSQR; same contract as run_tsqr (final R, ncap x ncap row-major
+// upper triangular, in ws_a or ws_b).  The leaf count is at most one wave of resident CTAs,
+// max_leaves, and the column-owner driver's own bound (so workspace sized by tsqr_max_leaves
+// always suffices).
+template <typename T, int BR, int QS, class Src>
+tt_status run_tsqr_rs(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows, int max_leaves,
+                      double* ws_a, double* ws_b, double** Rfinal, int leaf_cat = kTsqrLeaf) {
+  const int ncap = lp.ncap();
+  const size_t smem = tsqr_rs_smem_bytes<T, BR, QS>(ncap);
+  if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
+  const int threads = tsqr_rs_threads<QS>(ncap);
+  if (threads > 1024) return TT_ERR_UNSUPPORTED;
+  auto leaf = k_tsqr_leaf_rs<T, BR, QS, Src>;
+  auto merge = k_tsqr_merge_rs<T, BR, QS>;
+  cudaFuncSetAttribute(leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf, threads, smem) != cudaSuccess) return TT_ERR_CUDA;
+  if (per_sm < 1) return TT_ERR_UNSUPPORTED;
+  long L = (nrows + BR - 1) / BR;
+  long cap = (long)num_sms * per_sm;
+  if (max_leaves > 0 && cap > max_leaves) cap = max_leaves;
+  const long colcap = tsqr_max_leaves<T, BR>(num_sms, ncap, nrows, max_leaves);
+  if (cap > colcap) cap = colcap;
+  if (L > cap) L = cap;
+  if (L < 1) L = 1;
+  long rpc = (nrows + L - 1) / L;
+  rpc = ((rpc + BR - 1) / BR) * BR;
+  L = (nrows + rpc - 1) / rpc;
+  if (L < 1) L = 1;
+  {
+    TimerScope scope(leaf_cat, s);
+    leaf<<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
+  }
+  TimerScope scope(kTsqrMerge, s);
+  double* in = ws_a;
+  double* out = ws_b;
+  int n = (int)L;
+  while (n > 1) {
+    const int m = (n + 1) / 2;
+    merge<<<m, threads, smem, s>>>(lp, n, in, out); count_launch();
+    double* t = in;
+    in = out;
+    out = t;
+    n = m;
+  }
+  *Rfinal = in;
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+}  // namespace ttk
