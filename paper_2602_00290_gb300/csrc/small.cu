@@ -670,16 +670,50 @@ __global__ void k_jacobi_write_v(int n, const double* __restrict__ V, const int*
 // in shared memory.  Jacobi on the transposed triangular factor converges in a few sweeps
 // (Drmac-Veselic preconditioning).  The normalised converged columns are the right singular
 // vectors of R, hence of A; they are written unsorted to U (row-major n x n, column c).
-// Warps take the n/2 pairs of each round; one barrier per round.
+// Teams of up to 32 lanes take the n/2 pairs of each round side by side; one barrier per round.
+// Sweep counts go to the context's Jacobi statistics (ctrl, nullable).
+// Lanes per column pair of the one-CTA Jacobi (1024 threads): the largest power of two <= 32 that
+// lets the pairs of a round run side by side.
+__host__ __device__ inline int jrt_ts(int n) {
+  const int np = n + (n & 1);
+  int ts = 32;
+  while (ts > 1 && (np / 2) * ts > 1024) ts >>= 1;
+  return ts;
+}
+// Column stride of the Jacobi copy of R^T: = ts (mod 32), so that the 32/ts teams of a warp, which
+// work on consecutive columns, read disjoint bank windows.
+__host__ __device__ inline int jrt_ld(int n) {
+  const int ts = jrt_ts(n);
+  return ((n + 31) / 32) * 32 + (ts < 32 ? ts : 0);
+}
+
+// Rotation arithmetic: FP32 takes the fast quotient and reciprocal square root (a few ulp; the
+// FP64 refinement that follows the FP32 sweep absorbs them), FP64 the IEEE operations.
 template <typename T>
+__device__ __forceinline__ T jrt_div(T a, T b) { return a / b; }
+template <>
+__device__ __forceinline__ float jrt_div<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T>
+__device__ __forceinline__ T jrt_rsqrt(T x) { return T(1) / sqrt(x); }
+template <>
+__device__ __forceinline__ float jrt_rsqrt<float>(float x) { return rsqrtf(x); }
+
+template <typename T, bool SMEM>
 __global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restrict__ R, double* __restrict__ U,
-                                                    double* __restrict__ raw, int maxsweep, T* gwork) {
+                                                    double* __restrict__ raw, int maxsweep, T* gwork,
+                                                    DevCtrl* ctrl) {
   extern __shared__ __align__(16) unsigned char jrt_smem[];
-  // column c at At[c * n]: in shared memory, or in global scratch when n x n does not fit
-  T* At = gwork ? gwork : reinterpret_cast<T*>(jrt_smem);
+  // column c at At[c * ld]: in shared memory (SMEM, so that every access compiles to a
+  // shared-memory load or store), or in global scratch when it does not fit; the stride
+  // puts the columns of the pairs that share a warp on different banks
+  const int ld = jrt_ld(n);
+  T* At = SMEM ? reinterpret_cast<T*>(jrt_smem) : gwork;
   __shared__ int rot_flag;
   __shared__ float red[33];
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) At[idx] = (T)R[idx];
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int c = idx / n;
+    At[(size_t)c * ld + (idx - c * n)] = (T)R[idx];
+  }
   // scale-free thresholds: pairs below the matrix round-off level are left alone
   float fro = 0.f;
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) fro += (float)(R[idx] * R[idx]);
@@ -697,18 +731,26 @@ __global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restr
   const T floor_abs = (sizeof(T) == 4 ? T(1e-14) : T(1e-32)) * (T)red[32];
   const int np = n + (n & 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // a team of ts lanes (power of two, <= 32) per column pair, so that the np/2 pairs of a
+  // round run side by side; team sums are xor butterflies inside the team
+  const int ts = jrt_ts(n);  // launched with 1024 threads
+  const int team = threadIdx.x / ts, tl = threadIdx.x & (ts - 1), nteams = blockDim.x / ts;
+  const unsigned tmask = (ts == 32) ? 0xffffffffu : (((1u << ts) - 1u) << (lane & ~(ts - 1)));
+  int sweeps = 0;
   for (int sweep = 0; sweep < maxsweep; ++sweep) {
     if (threadIdx.x == 0) rot_flag = 0;
     __syncthreads();
     for (int round = 0; round < np - 1; ++round) {
-      for (int pr = warp; pr < np / 2; pr += nwarps) {
+      for (int pr = team; pr < np / 2; pr += nteams) {
         int p, q;
         if (pr == 0) {
           p = round;
           q = np - 1;
         } else {
-          p = (round + pr) % (np - 1);
-          q = (round - pr + (np - 1)) % (np - 1);
+          p = round + pr;
+          if (p >= np - 1) p -= np - 1;
+          q = round - pr;
+          if (q < 0) q += np - 1;
         }
         if (p >= n || q >= n) continue;
         if (p > q) {
@@ -716,43 +758,54 @@ __global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restr
           p = q;
           q = t;
         }
-        T* ap = At + (size_t)p * n;
-        T* aq = At + (size_t)q * n;
+        T* ap = At + (size_t)p * ld;
+        T* aq = At + (size_t)q * ld;
         T a = 0, b = 0, g = 0;
-        for (int i = lane; i < n; i += 32) {
-          const T x = ap[i], y = aq[i];
-          a += x * x;
-          b += y * y;
-          g += x * y;
+        // unrolled by 4: the loads of four elements issue back to back
+#pragma unroll 4
+        for (int i = tl; i < n; i += ts) {
+          const T xi = ap[i], yi = aq[i];
+          a += xi * xi;
+          b += yi * yi;
+          g += xi * yi;
         }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
+        for (int o = 1; o < ts; o <<= 1) {
+          a += __shfl_xor_sync(tmask, a, o);
+          b += __shfl_xor_sync(tmask, b, o);
+          g += __shfl_xor_sync(tmask, g, o);
+        }
         if (fabs(g) > floor_abs && fabs(g) > rel_tol * sqrt(a) * sqrt(b)) {
           const T zeta = (b - a) / (T(2) * g);
           T t;
           if (fabs(zeta) > (sizeof(T) == 4 ? T(1e18) : T(1e150)))
             t = T(0.5) / zeta;
-          else
-            t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-          const T cs = T(1) / sqrt(T(1) + t * t), sn = cs * t;
-          for (int i = lane; i < n; i += 32) {
-            const T x = ap[i], y = aq[i];
-            ap[i] = cs * x - sn * y;
-            aq[i] = sn * x + cs * y;
+          else  // the divisor lies in [1, 2e18]: the fast quotient is exact to 2 ulp
+            t = jrt_div<T>(zeta >= T(0) ? T(1) : T(-1), fabs(zeta) + sqrt(T(1) + zeta * zeta));
+          const T cs = jrt_rsqrt<T>(T(1) + t * t), sn = cs * t;
+#pragma unroll 4
+          for (int i = tl; i < n; i += ts) {
+            const T xi = ap[i], yi = aq[i];
+            ap[i] = cs * xi - sn * yi;
+            aq[i] = sn * xi + cs * yi;
           }
-          if (lane == 0) rot_flag = 1;
+          if (tl == 0) rot_flag = 1;
         }
       }
       __syncthreads();
     }
     const int f = rot_flag;
     __syncthreads();
+    sweeps = sweep + 1;
     if (!f) break;
+  }
+  if (ctrl && threadIdx.x == 0) {
+    atomicMax(&ctrl->jac_sweeps_max, sweeps);
+    atomicAdd(&ctrl->jac_calls, 1);
+    atomicAdd(&ctrl->jac_sweeps_sum, sweeps);
   }
   // normalised columns -> U[i][c]
   for (int c = warp; c < n; c += nwarps) {
-    const T* ac = At + (size_t)c * n;
+    const T* ac = At + (size_t)c * ld;
     // FP64 norm of the stored column: U gets unit columns to FP64 accuracy, so that |A u_j|
     // differs from sigma_j only at second order in the FP32 rotation error
     double s2 = 0.0;
@@ -958,7 +1011,7 @@ static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K
 // and their FP32 singular values `raw`, with perm the order of decreasing raw.
 template <class Src>
 static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, long rows, int cols, Bump& ws,
-                                 double** U_out, double** P_out, double* raw, int* perm) {
+                                 double** U_out, double** P_out, double* raw, int* perm, DevCtrl* ctrl) {
   LivePattern lp{nullptr, cols, 1, 0};
   const long L = tsqr_max_leaves<float, 64>(num_sms, cols, rows, 8);
   double* a = ws.take<double>((size_t)L * cols * cols);
@@ -966,9 +1019,9 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   double* U = ws.take<double>((size_t)cols * cols);
   double* P = ws.take<double>((size_t)rows * cols);
   double* tmp = ws.take<double>(cols);
-  const size_t at_bytes = sizeof(float) * (size_t)cols * cols;
+  const size_t at_bytes = sizeof(float) * (size_t)cols * jrt_ld(cols);
   const bool in_smem = at_bytes <= 200 * 1024;
-  float* gwork = in_smem ? nullptr : ws.take<float>((size_t)cols * cols);
+  float* gwork = in_smem ? nullptr : ws.take<float>((size_t)cols * jrt_ld(cols));
   *U_out = U;
   *P_out = P;
   if (ws.dry) return TT_OK;
@@ -976,8 +1029,12 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   tt_status st = run_tsqr<float, 64>(s, num_sms, src, lp, rows, 8, a, b, &R);
   if (st != TT_OK) return st;
   const size_t smem = in_smem ? at_bytes : 0;
-  if (in_smem) cudaFuncSetAttribute(k_jacobi_rt<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_jacobi_rt<float><<<1, 1024, smem, s>>>(cols, R, U, raw, 40, gwork); count_launch();
+  if (in_smem) {
+    cudaFuncSetAttribute(k_jacobi_rt<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_jacobi_rt<float, true><<<1, 1024, smem, s>>>(cols, R, U, raw, 40, nullptr, ctrl); count_launch();
+  } else {
+    k_jacobi_rt<float, false><<<1, 1024, 0, s>>>(cols, R, U, raw, 40, gwork, ctrl); count_launch();
+  }
   k_rank_perm<<<1, 1024, 0, s>>>(cols, raw, perm); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
@@ -998,7 +1055,8 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   double* V2 = ws.take<double>((size_t)n2 * n2);
   double* tmp2 = ws.take<double>((size_t)n2 * n2);
   double *U2 = nullptr, *P2 = nullptr;
-  tt_status st = svd_right_mixed(s, num_sms, SrcRows<double>{Y, n2}, (long)R * n1, n2, ws, &U2, &P2, sigc2, perm2);
+  tt_status st = svd_right_mixed(s, num_sms, SrcRows<double>{Y, n2}, (long)R * n1, n2, ws, &U2, &P2, sigc2, perm2,
+                                 j.ctrl);
   if (st != TT_OK) return st;
   double* P2s = ws.take<double>((size_t)R * n1 * n2);
   const int nv = n1 * K2;
@@ -1031,7 +1089,7 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   double* tmpK = ws.take<double>((size_t)nv * Kr);
   double* V1 = ws.take<double>((size_t)nv * K1);
   double *U1 = nullptr, *P1 = nullptr;
-  st = svd_right_mixed(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &U1, &P1, sigc1, perm1);
+  st = svd_right_mixed(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &U1, &P1, sigc1, perm1, j.ctrl);
   if (st != TT_OK) return st;
   if (!ws.dry) {
     small_gemm<double, double>(s, nv, R, R, Y2, 1, nv, U1, R, 1, P1, R, nullptr, nullptr);  // P1 = A1 U1
