@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-gram", action="store_true", help="skip the FP64 leg with Gram rounding")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default TSQR kernels instead of the autotuned choice (tt_autotune)")
+    ap.add_argument("--tsqr", default="",
+                    help="pin the TSQR choice instead of autotuning, e.g. "
+                         "'transport=column_dense:608,source=rowsplit:456' (tt_context_set_tsqr)")
     ap.add_argument("--workload", default="plane", choices=["plane", "batched"],
                     help="plane: the 128x128 single-problem step (the headline line); batched: the "
                          "256-problem batch stepped as one CUDA graph (a separate measurement)")
@@ -187,7 +190,17 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
     ctx.sync()
     tune = None
-    if rounding == "tsqr" and not args.no_autotune:
+    if rounding == "tsqr" and args.tsqr:
+        # pinned choice (e.g. the autotuner's, to profile the same kernels without timing trials)
+        ncaps = {"transport": (2 * wl.ndim + 1) * wl.rmax, "source": wl.rmax + 1}
+        tune = {}
+        for item in args.tsqr.split(","):
+            role, spec = item.split("=")
+            variant, leaves = spec.split(":")
+            ctx.set_tsqr(precision, ncaps[role], variant, int(leaves))
+            tune[role] = ctx.get_tsqr(precision, ncaps[role])
+        tune["pinned"] = True
+    elif rounding == "tsqr" and not args.no_autotune:
         # TSQR kernels and leaf counts for this state's shape, timed on a copy of it
         tune = ctx.autotune(plan, x, wl.tol, wl.rmax, precision, steps=2)
     ranks = [x.ranks()]

@@ -164,7 +164,9 @@ tt_status tt_context_set_sketch(tt_context *ctx, const double *omega_dev, int32_
  *   variant 1: four lanes per column, each holding a quarter of the rows of a block (4 ncap <= 1024);
  *   variant 2: FP32 only, one thread per column over 32-row blocks with registers held so that
  *              four CTAs share an SM (ncap <= 160).
- * A variant that cannot take the shape runs variant 0.  leaves = cap on the TSQR leaves: <= 0 gives the default wave (2 CTAs per SM for
+ * A variant that cannot take the shape runs variant 0.  The variant picks the leaf kernel; the
+ * merge tree over the leaves' R factors runs four lanes per column in every variant when
+ * 4 ncap <= 1024.  leaves = cap on the TSQR leaves: <= 0 gives the default wave (2 CTAs per SM for
  * FP64, 3 for FP32); larger caps are clamped to 4 per SM.  The choice changes the order of
  * rounding errors only.  ncap <= 0 clears every entry.  tt_context_get_tsqr reports what a pass
  * of ncap columns would run.  The paper has no counterpart: these are launch-shape choices. */

@@ -333,6 +333,10 @@ __global__ void __launch_bounds__(256) k_tsqr_merge(LivePattern lp, int nin, con
   write_R<T, BR>(Rs, ncap, Ro);
 }
 
+// Merge tree over the leaves' R factors (defined with the row-split kernels in tsqr_rs.cuh).
+template <typename T>
+tt_status merge_tree(cudaStream_t s, LivePattern lp, int nleaves, double* ws_a, double* ws_b, double** Rfinal);
+
 // Host driver: leaves then merge levels; returns the device pointer of the final R
 // (ncap x ncap, row-major, upper triangular) inside ws_a or ws_b.
 // Leaf kernels are instantiated with launch bounds (MAXT threads, MINB resident CTAs; FP32 by
@@ -360,28 +364,11 @@ tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, 
   rpc = ((rpc + BR - 1) / BR) * BR;
   L = (nrows + rpc - 1) / rpc;
   if (L < 1) L = 1;
-  constexpr int MBR = sizeof(T) == 4 ? 64 : 32;  // rows the merge tree absorbs at a time
-  const size_t msmem = tsqr_smem_bytes<T, MBR>(ncap);
-  if (msmem > 227 * 1024) return TT_ERR_UNSUPPORTED;
-  cudaFuncSetAttribute(k_tsqr_merge<T, MBR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
   {
     TimerScope scope(leaf_cat, s);
     leaf<<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
   }
-  TimerScope scope(kTsqrMerge, s);
-  double* in = ws_a;
-  double* out = ws_b;
-  int n = (int)L;
-  while (n > 1) {
-    const int m = (n + 1) / 2;
-    k_tsqr_merge<T, MBR><<<m, threads, msmem, s>>>(lp, n, in, out); count_launch();
-    double* t = in;
-    in = out;
-    out = t;
-    n = m;
-  }
-  *Rfinal = in;
-  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  return merge_tree<T>(s, lp, (int)L, ws_a, ws_b, Rfinal);
 }
 
 // Leaves needed for a TSQR of nrows rows (bounds workspace sizing).
@@ -633,3 +620,6 @@ inline long update_grid(int num_sms, int ncap, int kcap, long nrows) {
 }
 
 }  // namespace ttk
+
+// the row-split kernels and the merge tree
+#include "tsqr_rs.cuh"

@@ -122,4 +122,43 @@ static __global__ void k_cross_reduce(int l, int R, int nsplit, int nbi, int nbj
   RZ[idx] = s;
 }
 
+// Mixed precision: Q = Y R_Y^{-1} with R_Y from an FP32 TSQR is orthonormal only to about
+// kappa(Y) FP32 epsilon, and C = Q^T A then misses the projection onto span(Q).  With the FP64
+// Gram G = Q^T Q = L L^T the projection is Q G^{-1} Q^T A, whose Gram in the A-columns equals
+// that of L^{-1} C: the first l rows of RZ become L^{-1} C.  Columns of Q that the solve zeroed
+// (no sketch direction) have a zero pivot here and keep zero rows.  One CTA (l <= 64).
+static __global__ void __launch_bounds__(128) k_rand_correct(int l, int R, const double* __restrict__ G,
+                                                             double* __restrict__ RZ) {
+  __shared__ double Ls[64 * 64];
+  __shared__ int ok[64];
+  for (int i = threadIdx.x; i < l * l; i += blockDim.x) Ls[i] = G[i];
+  __syncthreads();
+  double gmax = 0.0;
+  for (int j = 0; j < l; ++j) gmax = fmax(gmax, Ls[j * l + j]);
+  for (int j = 0; j < l; ++j) {
+    if (threadIdx.x == 0) {
+      double d = Ls[j * l + j];
+      for (int k = 0; k < j; ++k) d -= Ls[j * l + k] * Ls[j * l + k];
+      ok[j] = d > 1e-12 * gmax;
+      Ls[j * l + j] = ok[j] ? sqrt(d) : 0.0;
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < l; i += blockDim.x) {
+      double v = Ls[i * l + j];
+      for (int k = 0; k < j; ++k) v -= Ls[i * l + k] * Ls[j * l + k];
+      Ls[i * l + j] = ok[j] ? v / Ls[j * l + j] : 0.0;
+    }
+    __syncthreads();
+  }
+  for (int b = threadIdx.x; b < R; b += blockDim.x) {
+    double y[64];
+    for (int j = 0; j < l; ++j) {
+      double v = RZ[(size_t)j * R + b];
+      for (int k = 0; k < j; ++k) v -= Ls[j * l + k] * y[k];
+      y[j] = ok[j] ? v / Ls[j * l + j] : 0.0;
+    }
+    for (int j = 0; j < l; ++j) RZ[(size_t)j * R + b] = y[j];
+  }
+}
+
 }  // namespace ttk

@@ -280,6 +280,9 @@ static tt_status randomized_factor(tt_context* ctx, cudaStream_t s, const Src& s
   if (nsplit < 1) nsplit = 1;
   double* part = ws.take<double>((size_t)nsplit * nbi * nbj * 64 * 64);
   double* RZ = ws.take<double>((size_t)R * R);
+  constexpr bool kCorrect = sizeof(T) == 4;  // FP32 TSQR of the sketch: project with Q's own Gram
+  double* G = kCorrect ? ws.take<double>((size_t)l * l) : nullptr;
+  double* partG = kCorrect ? ws.take<double>((size_t)nsplit * 64 * 64) : nullptr;
   *RZ_out = RZ;
   if (ws.dry) return TT_OK;
   small_gemm<double, double>(s, R, l, nang, B0, nang, 1, ctx->sketch, ctx->sketch_ell, 1, Op, l, nullptr, nullptr);
@@ -296,6 +299,13 @@ static tt_status randomized_factor(tt_context* ctx, cudaStream_t s, const Src& s
       SrcRows<S>{Y, l}, l, src, lp, N, rps, nbj, part); count_launch();
   k_cross_reduce<<<(unsigned)(((long)R * R + 255) / 256), 256, 0, s>>>(l, R, (int)nsplit, nbi, nbj, part, RZ);
   count_launch();
+  if (kCorrect) {
+    k_cross_tiles<SrcRows<S>, SrcRows<S>><<<dim3((unsigned)nsplit, 1u), 256, 0, s>>>(
+        SrcRows<S>{Y, l}, l, SrcRows<S>{Y, l}, LivePattern{nullptr, l, 1, 0}, N, rps, 1, partG); count_launch();
+    k_cross_reduce<<<(unsigned)(((long)l * l + 255) / 256), 256, 0, s>>>(l, l, (int)nsplit, 1, 1, partG, G);
+    count_launch();
+    k_rand_correct<<<1, 128, 0, s>>>(l, R, G, RZ); count_launch();
+  }
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 

@@ -205,9 +205,7 @@ tt_status run_tsqr_rs(cudaStream_t s, int num_sms, const Src& src, LivePattern l
   const int threads = tsqr_rs_threads<QS>(ncap);
   if (threads > 1024) return TT_ERR_UNSUPPORTED;
   auto leaf = k_tsqr_leaf_rs<T, BR, QS, Src>;
-  auto merge = k_tsqr_merge_rs<T, BR, QS>;
   cudaFuncSetAttribute(leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  cudaFuncSetAttribute(merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf, threads, smem) != cudaSuccess) return TT_ERR_CUDA;
   if (per_sm < 1) return TT_ERR_UNSUPPORTED;
@@ -226,13 +224,42 @@ tt_status run_tsqr_rs(cudaStream_t s, int num_sms, const Src& src, LivePattern l
     TimerScope scope(leaf_cat, s);
     leaf<<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
   }
+  return merge_tree<T>(s, lp, (int)L, ws_a, ws_b, Rfinal);
+}
+
+// Merge tree of the TSQR: levels of pairwise QRs of stacked R factors, the last one in ws_a or
+// ws_b.  Every leaf kernel merges with the row-split merge (measured faster than the
+// column-owner merge for every pass shape tried) where 4 ncap <= 1024 lanes, else with the
+// column-owner merge.
+template <typename T>
+tt_status merge_tree(cudaStream_t s, LivePattern lp, int nleaves, double* ws_a, double* ws_b, double** Rfinal) {
+  constexpr int MBR = sizeof(T) == 4 ? 64 : 32;  // rows of the second factor absorbed at a time
+  const int ncap = lp.ncap();
+  const int rs_threads = tsqr_rs_threads<4>(ncap);
+  const bool rs = rs_threads <= 1024 && tsqr_rs_smem_bytes<T, MBR, 4>(ncap) <= 227 * 1024;
+  size_t smem;
+  int threads;
+  if (rs) {
+    smem = tsqr_rs_smem_bytes<T, MBR, 4>(ncap);
+    threads = rs_threads;
+    cudaFuncSetAttribute(k_tsqr_merge_rs<T, MBR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  } else {
+    smem = tsqr_smem_bytes<T, MBR>(ncap);
+    threads = ((ncap + 31) / 32) * 32;
+    if (smem > 227 * 1024 || threads > 256) return TT_ERR_UNSUPPORTED;
+    cudaFuncSetAttribute(k_tsqr_merge<T, MBR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
   TimerScope scope(kTsqrMerge, s);
   double* in = ws_a;
   double* out = ws_b;
-  int n = (int)L;
+  int n = nleaves;
   while (n > 1) {
     const int m = (n + 1) / 2;
-    merge<<<m, threads, smem, s>>>(lp, n, in, out); count_launch();
+    if (rs)
+      k_tsqr_merge_rs<T, MBR, 4><<<m, threads, smem, s>>>(lp, n, in, out);
+    else
+      k_tsqr_merge<T, MBR><<<m, threads, smem, s>>>(lp, n, in, out);
+    count_launch();
     double* t = in;
     in = out;
     out = t;
