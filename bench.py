@@ -186,21 +186,23 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     x = tt.initial_state(plan, rcap, dtype)
     stream = ctx.stream
     energy = torch.zeros(4, dtype=torch.float64, device="cuda")
-    for _ in range(args.warmup):
-        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
-    ctx.sync()
-    tune = None
+    pinned = None
     if rounding == "tsqr" and args.tsqr:
-        # pinned choice (e.g. the autotuner's, to profile the same kernels without timing trials)
+        # pinned choice (e.g. the autotuner's, to profile the same kernels without timing
+        # trials), in force from the first warm-up step on
         ncaps = {"transport": (2 * wl.ndim + 1) * wl.rmax, "source": wl.rmax + 1}
-        tune = {}
+        pinned = {}
         for item in args.tsqr.split(","):
             role, spec = item.split("=")
             variant, leaves = spec.split(":")
             ctx.set_tsqr(precision, ncaps[role], variant, int(leaves))
-            tune[role] = ctx.get_tsqr(precision, ncaps[role])
-        tune["pinned"] = True
-    elif rounding == "tsqr" and not args.no_autotune:
+            pinned[role] = ctx.get_tsqr(precision, ncaps[role])
+        pinned["pinned"] = True
+    for _ in range(args.warmup):
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
+    ctx.sync()
+    tune = pinned
+    if tune is None and rounding == "tsqr" and not args.no_autotune:
         # TSQR kernels and leaf counts for this state's shape, timed on a copy of it
         tune = ctx.autotune(plan, x, wl.tol, wl.rmax, precision, steps=2)
     ranks = [x.ranks()]

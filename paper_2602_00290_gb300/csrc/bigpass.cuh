@@ -261,11 +261,12 @@ __device__ __forceinline__ void write_R(const T* Rs, int ncap, double* Ro) {
   }
 }
 
-// packed R, then the double-buffered reflector (16-byte aligned) and its two scalars
+// packed R, then the double-buffered reflector (16-byte aligned), its two scalars and the row
+// flags of the current block
 __host__ __device__ inline size_t tsqr_r_elems(int ncap) { return (((size_t)ncap * (ncap + 1) / 2) + 3) & ~(size_t)3; }
 template <typename T, int BR>
 __host__ __device__ inline size_t tsqr_smem_bytes(int ncap) {
-  return sizeof(T) * (tsqr_r_elems(ncap) + 2 * BR + 4);
+  return sizeof(T) * (tsqr_r_elems(ncap) + 2 * BR + 4) + sizeof(unsigned) * BR;
 }
 
 template <typename T, int BR, class Src, int MAXT = 256, int MINB = 1>
@@ -276,19 +277,23 @@ __global__ void __launch_bounds__(MAXT, MINB) k_tsqr_leaf(Src src, LivePattern l
   T* Rs = reinterpret_cast<T*>(tsqr_smem);
   T* vbuf = Rs + tsqr_r_elems(ncap);
   T* taub = vbuf + 2 * BR;
+  unsigned* flags = reinterpret_cast<unsigned*>(taub + 4);
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
   for (int i = threadIdx.x; i < ncap * (ncap + 1) / 2; i += blockDim.x) Rs[i] = T(0);
   const int c = threadIdx.x;
   const bool mycol = (c < ncap) && lp.live(c, r);
   const auto cc = src.col(c < ncap ? c : 0);
-  __syncthreads();
   const long beg = (long)blockIdx.x * rpc;
   const long end = (beg + rpc < nrows) ? beg + rpc : nrows;
   int buf = 0;
   for (long r0 = beg; r0 < end; r0 += BR) {
+    // neighbour flags once per row of the block, shared by all columns; values in arithmetic T
+    __syncthreads();  // the previous block's loads of `flags` are done
+    for (int i = threadIdx.x; i < BR; i += blockDim.x) flags[i] = (r0 + i < end) ? src.row_flags(r0 + i) : 0u;
+    __syncthreads();
     T B[BR];
 #pragma unroll
-    for (int i = 0; i < BR; ++i) B[i] = (mycol && r0 + i < end) ? (T)src.load(cc, r0 + i) : T(0);
+    for (int i = 0; i < BR; ++i) B[i] = (mycol && r0 + i < end) ? src.template loadT<T>(cc, r0 + i, flags[i]) : T(0);
     hh_absorb<T, BR>(Rs, ncap, B, vbuf, taub, buf, 0, lp, r, mycol);
   }
   __syncthreads();
