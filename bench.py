@@ -26,12 +26,14 @@ sys.path.insert(0, ROOT)
 METRIC = "TT transport steps/s and core-contraction TFLOP/s at fixed tol, FP64 vs mixed"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12    # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2070 MHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2070 MHz
-# DRAM bytes (read + write) of one transport-sum TSQR leaf launch at r = 32: ncu capture of the
-# same kernel on the 96 x 96 x 64-group workload (589,824 rows), scaled to 1,048,576 rows.
-LEAF_TRAFFIC = {"mixed": (78.895360e6 + 29.995008e6) * 1048576 / 589824,
-                "fp64": (203.504640e6 + 5.422080e6) * 1048576 / 589824}
-LEAF_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of k_tsqr_leaf on the 96x96 "
-                       "workload, scaled by rows to 128x128")
+# DRAM bytes (read + write) of one transport-sum TSQR leaf launch at r = 32, per (precision, leaf
+# kernel): ncu captures of the same kernels on the 96 x 96 x 64-group workload (589,824 rows,
+# 595 leaves FP32 / 303 FP64), reads scaled by rows to 1,048,576 and writes (the leaves' R
+# factors) by leaves to the 608 / 304 of the full workload.
+LEAF_TRAFFIC = {("mixed", "column_dense"): 77.771264e6 * 1048576 / 589824 + 60.823296e6 * 608 / 595,
+                ("fp64", "column"): 202.651136e6 * 1048576 / 589824 + 5.878528e6 * 304 / 303}
+LEAF_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the leaf kernel on the 96x96 "
+                       "workload; reads scaled by rows, writes by leaves to 128x128")
 
 
 def parse():
@@ -265,7 +267,7 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     kname = {"column": "k_tsqr_leaf", "rowsplit": "k_tsqr_leaf_rs",
              "column_dense": "k_tsqr_leaf (32-row blocks, 4 CTAs/SM)"}[variant]
     # ncu traffic was taken on the column-owner kernel; another kernel has no counters yet
-    traffic = LEAF_TRAFFIC.get(precision) if (args.size == "full" and variant == "column") else None
+    traffic = LEAF_TRAFFIC.get((precision, variant)) if args.size == "full" else None
     out["roofline"] = {"kernel": kname + " over the transport sum (one launch per step, R1 = 5r columns)",
                        "bound": bound, "achieved": leaf_tf, "peak": peak, "unit": "TFLOP/s",
                        "frac": (leaf_tf / peak) if leaf_tf else None,
