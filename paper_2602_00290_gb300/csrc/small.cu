@@ -205,8 +205,9 @@ __global__ void __launch_bounds__(1024) k_cgs2_sigma(int nv, int ldv, double* __
 // ---- CholeskyQR2 of the first K columns of V (FP64) ----------------------------------------
 // The same factorisation V[:, :K] = Q T as Gram-Schmidt in column order, computed as two passes
 // of: Gram matrix G = V^T V (row chunks spread over many CTAs), upper Cholesky factor
-// G = T^T T (one CTA), V <- V T^{-1} (one thread per row).  Column j of T depends on columns
-// 0..j of V only, so leading columns are unaffected by what follows them.  The columns here are
+// G = T^T T (one CTA), V <- V T^{-1} (explicit triangular inverse in one CTA, then a row-parallel
+// product over many CTAs).  Column j of T depends on columns 0..j of V only, so leading columns
+// are unaffected by what follows them.  The columns here are
 // P = A U for nearly orthogonal U, i.e. graded: V = W D with D the column norms and W of
 // condition near 1 on the columns that matter; Cholesky and triangular solves are invariant
 // under that scaling, so two passes give FP64-orthonormal Q and |T_jj| to FP64 relative
@@ -216,7 +217,6 @@ __global__ void __launch_bounds__(1024) k_cgs2_sigma(int nv, int ldv, double* __
 constexpr int kGramTileRows = 32;   // rows staged in shared memory per step
 constexpr int kGramChunkRows = 64;  // rows per CTA (one partial Gram matrix each)
 constexpr int kGramEntries = 2048;  // Gram entries per CTA (8 per thread)
-constexpr int kTrsmRows = 64;       // rows per CTA in the triangular solve
 
 __global__ void __launch_bounds__(256) k_gram_chunks(int nv, int ldv, const double* __restrict__ V, int K,
                                                      double* __restrict__ part) {
@@ -292,33 +292,54 @@ __global__ void __launch_bounds__(256) k_chol_upper(int K, const double* __restr
   }
 }
 
-// V[row][:K] <- V[row][:K] T^{-1} (forward substitution along the row; dead columns give 0).
-__global__ void __launch_bounds__(kTrsmRows) k_trsm_rows(int nv, int ldv, double* __restrict__ V, int K,
-                                                         const double* __restrict__ T) {
-  extern __shared__ double trs[];
-  double* Ts = trs;              // [K][K]
-  double* Rw = trs + K * K;      // [kTrsmRows][K + 1]
-  const int row0 = blockIdx.x * kTrsmRows;
-  const int nr = min(kTrsmRows, nv - row0);
-  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Ts[idx] = T[idx];
-  for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
-    const int rr = idx / K, c = idx - (idx / K) * K;
-    Rw[rr * (K + 1) + c] = V[(size_t)(row0 + rr) * ldv + c];
+// M = T^{-1} for the upper-triangular T restricted to its live pivots (T_jj > 0), with zero rows
+// and columns at dead pivots, so that v M equals the forward substitution v T^{-1} over the live
+// pivots (dead columns give 0).  One thread per column of M, back substitution up the column.  One CTA.
+__global__ void __launch_bounds__(128) k_tri_inv(int K, const double* __restrict__ T, double* __restrict__ M) {
+  extern __shared__ double tis[];
+  double* Ts = tis;          // [K][K]
+  double* Ms = tis + K * K;  // [K][K]
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
+    Ts[idx] = T[idx];
+    Ms[idx] = 0.0;
   }
   __syncthreads();
-  if (threadIdx.x < nr) {
-    double* q = Rw + threadIdx.x * (K + 1);
-    for (int j = 0; j < K; ++j) {
-      const double tjj = Ts[j * K + j];
-      double v = q[j];
-      for (int i = 0; i < j; ++i) v -= q[i] * Ts[i * K + j];
-      q[j] = (tjj > 0.0) ? v / tjj : 0.0;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    if (!(Ts[j * K + j] > 0.0)) continue;
+    Ms[j * K + j] = 1.0 / Ts[j * K + j];
+    for (int i = j - 1; i >= 0; --i) {
+      const double tii = Ts[i * K + i];
+      if (!(tii > 0.0)) continue;
+      double acc = 0.0;
+      for (int k = i + 1; k <= j; ++k) acc += Ts[i * K + k] * Ms[k * K + j];
+      Ms[i * K + j] = -acc / tii;
     }
   }
   __syncthreads();
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) M[idx] = Ms[idx];
+}
+
+// V[row][:K] <- V[row][:K] M for upper-triangular M (K x K): rows staged kRowsTile per CTA in
+// shared memory, one thread per output entry (no dependent chain), spread over many CTAs.
+constexpr int kRowsTile = 16;
+__global__ void __launch_bounds__(256) k_rows_times_upper(int nv, int ldv, double* __restrict__ V, int K,
+                                                          const double* __restrict__ M) {
+  extern __shared__ double rtu[];
+  double* Ms = rtu;          // [K][K]
+  double* Vs = rtu + K * K;  // [kRowsTile][K]
+  const int row0 = blockIdx.x * kRowsTile;
+  const int nr = min(kRowsTile, nv - row0);
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Ms[idx] = M[idx];
   for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
     const int rr = idx / K, c = idx - (idx / K) * K;
-    V[(size_t)(row0 + rr) * ldv + c] = Rw[rr * (K + 1) + c];
+    Vs[rr * K + c] = V[(size_t)(row0 + rr) * ldv + c];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
+    const int rr = idx / K, j = idx - (idx / K) * K;
+    double acc = 0.0;
+    for (int i = 0; i <= j; ++i) acc += Vs[rr * K + i] * Ms[i * K + j];
+    V[(size_t)(row0 + rr) * ldv + j] = acc;
   }
 }
 
@@ -985,22 +1006,28 @@ static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K
   double* G = ws.take<double>(KK);
   double* T1 = ws.take<double>(KK);
   double* T2 = ws.take<double>(KK);
+  double* Minv = ws.take<double>(KK);
   if (ws.dry) return TT_OK;
   if (K > 128 || nv < 1) {
     k_cgs2_sigma<<<1, 1024, 0, s>>>(nv, ldv, V, K, sig); count_launch();
     return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
   const size_t chol_smem = sizeof(double) * ((size_t)KK + K);
-  const size_t trsm_smem = sizeof(double) * ((size_t)KK + (size_t)kTrsmRows * (K + 1));
+  const size_t inv_smem = sizeof(double) * 2 * (size_t)KK;
+  const size_t rtu_smem = sizeof(double) * ((size_t)KK + (size_t)kRowsTile * K);
   cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem);
-  cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem);
+  cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
+  cudaFuncSetAttribute(k_rows_times_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rtu_smem);
   for (int pass = 0; pass < 2; ++pass) {
     double* T = pass ? T2 : T1;
     k_gram_chunks<<<dim3((unsigned)nchunks, (unsigned)((KK + kGramEntries - 1) / kGramEntries)), 256, 0, s>>>(
         nv, ldv, V, K, part); count_launch();
     k_gram_sum<<<(KK + 255) / 256, 256, 0, s>>>(nchunks, KK, part, G); count_launch();
     k_chol_upper<<<1, 256, chol_smem, s>>>(K, G, T); count_launch();
-    k_trsm_rows<<<(nv + kTrsmRows - 1) / kTrsmRows, kTrsmRows, trsm_smem, s>>>(nv, ldv, V, K, T); count_launch();
+    // V <- V T^{-1} as a product with the explicit inverse: row-parallel without a dependent chain
+    k_tri_inv<<<1, 128, inv_smem, s>>>(K, T, Minv); count_launch();
+    k_rows_times_upper<<<(nv + kRowsTile - 1) / kRowsTile, 256, rtu_smem, s>>>(nv, ldv, V, K, Minv);
+    count_launch();
   }
   k_sig_from_chol<<<(K + 127) / 128, 128, 0, s>>>(K, T1, T2, sig); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
