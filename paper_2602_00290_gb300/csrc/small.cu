@@ -146,10 +146,13 @@ __global__ void __launch_bounds__(1024) k_orthonormalise(int nv, int ldv, double
           if (lane == 0) h[i2] = sacc;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < nv; i += blockDim.x) {
-          double v = V[(size_t)i * ldv + j];
-          for (int i2 = 0; i2 < j; ++i2) v -= h[i2] * V[(size_t)i * ldv + i2];
-          V[(size_t)i * ldv + j] = v;
+        // warp per row: the sum over the earlier columns is split across lanes and reduced by
+        // shuffles, instead of one dependent FP64 chain of length j per row
+        for (int i = warp; i < nv; i += nwarps) {
+          double part = 0.0;
+          for (int i2 = lane; i2 < j; i2 += 32) part += h[i2] * V[(size_t)i * ldv + i2];
+          part = warp_sum(part);
+          if (lane == 0) V[(size_t)i * ldv + j] -= part;
         }
         __syncthreads();
       }
