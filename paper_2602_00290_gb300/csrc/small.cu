@@ -843,6 +843,86 @@ __global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restr
   }
 }
 
+// The same FP32 one-sided Jacobi on R^T for n <= 32 in one warp: lane c holds column c of R^T
+// (row c of R) in registers, a round exchanges columns between the two lanes of each pair by
+// shuffles, and both lanes compute the rotation from the pair in the same order (x = the lower
+// column), so they agree bit for bit.  No barriers.  Same outputs as k_jacobi_rt.
+__global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restrict__ R, double* __restrict__ U,
+                                                    double* __restrict__ raw, int maxsweep, DevCtrl* ctrl) {
+  const int lane = threadIdx.x;
+  float col[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) col[i] = (lane < n && i < n) ? (float)R[(size_t)lane * n + i] : 0.f;
+  float fro = 0.f;
+#pragma unroll
+  for (int i = 0; i < 32; ++i) fro += col[i] * col[i];
+  fro = warp_sum(fro);
+  const float rel_tol = 4.f * sqrtf((float)n) * 1.1920929e-7f;
+  const float floor_abs = 1e-14f * fro;
+  const int np = n + (n & 1);
+  int sweeps = 0;
+  for (int sweep = 0; sweep < maxsweep; ++sweep) {
+    int rotated = 0;
+    for (int round = 0; round < np - 1; ++round) {
+      // round-robin partner: (round, np - 1), else p + q = 2 round (mod np - 1)
+      int partner;
+      if (lane == np - 1) partner = round;
+      else if (lane == round) partner = np - 1;
+      else {
+        partner = 2 * round - lane;
+        if (partner < 0) partner += np - 1;
+        if (partner >= np - 1) partner -= np - 1;
+      }
+      if (lane >= np) partner = lane;
+      float other[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) other[i] = __shfl_sync(0xffffffffu, col[i], partner);
+      const bool pair = lane < n && partner < n && partner != lane;
+      const bool low = lane < partner;
+      float a = 0.f, b = 0.f, g = 0.f;
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float x = low ? col[i] : other[i], y = low ? other[i] : col[i];
+        a += x * x;
+        b += y * y;
+        g += x * y;
+      }
+      if (pair && fabsf(g) > floor_abs && fabsf(g) > rel_tol * sqrtf(a) * sqrtf(b)) {
+        const float zeta = (b - a) / (2.f * g);
+        float t;
+        if (fabsf(zeta) > 1e18f)
+          t = 0.5f / zeta;
+        else  // the divisor lies in [1, 2e18]
+          t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+        const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float x = low ? col[i] : other[i], y = low ? other[i] : col[i];
+          col[i] = low ? (cs * x - sn * y) : (sn * x + cs * y);
+        }
+        rotated = 1;
+      }
+    }
+    sweeps = sweep + 1;
+    if (!__any_sync(0xffffffffu, rotated)) break;
+  }
+  if (ctrl && lane == 0) {
+    atomicMax(&ctrl->jac_sweeps_max, sweeps);
+    atomicAdd(&ctrl->jac_calls, 1);
+    atomicAdd(&ctrl->jac_sweeps_sum, sweeps);
+  }
+  if (lane < n) {
+    double s2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i) s2 += (double)col[i] * (double)col[i];
+    const double inv = (s2 > 0.0) ? 1.0 / sqrt(s2) : 0.0;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < n) U[(size_t)i * n + lane] = (double)col[i] * inv;
+    raw[lane] = sqrt(s2);
+  }
+}
+
 // perm[r] = the column of rank r by decreasing vals (ties by index)
 __global__ void __launch_bounds__(1024) k_rank_perm(int n, const double* __restrict__ vals, int* __restrict__ perm) {
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
@@ -1059,7 +1139,9 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   tt_status st = run_tsqr<float, 64>(s, num_sms, src, lp, rows, 8, a, b, &R);
   if (st != TT_OK) return st;
   const size_t smem = in_smem ? at_bytes : 0;
-  if (in_smem) {
+  if (cols <= 32) {
+    k_jacobi_warp<<<1, 32, 0, s>>>(cols, R, U, raw, 40, ctrl); count_launch();
+  } else if (in_smem) {
     cudaFuncSetAttribute(k_jacobi_rt<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_jacobi_rt<float, true><<<1, 1024, smem, s>>>(cols, R, U, raw, 40, nullptr, ctrl); count_launch();
   } else {
