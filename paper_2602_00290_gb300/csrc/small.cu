@@ -168,6 +168,63 @@ __global__ void __launch_bounds__(1024) k_orthonormalise(int nv, int ldv, double
   }
 }
 
+// k_orthonormalise for nv <= 32 rows and ldv <= 32 columns in one warp, V staged in shared
+// memory: column dots with one lane per earlier column, the update with one lane per row, warp
+// shuffles for norms; no block-wide barriers.  Same algorithm and outputs.
+__global__ void __launch_bounds__(32) k_orthonormalise_warp(int nv, int ldv, double* __restrict__ Vg,
+                                                            const int* kptr, int rowmod, const int* rowlive_ptr) {
+  __shared__ double V[32 * 33];  // row i at V[i * 33 + c]
+  __shared__ double h[32];
+  const int lane = threadIdx.x;
+  const int k = *kptr;
+  const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
+  for (int idx = lane; idx < nv * ldv; idx += 32) {
+    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+    V[i * 33 + c] = Vg[idx];
+  }
+  __syncwarp();
+  for (int j = 0; j < k; ++j) {
+    int cand = -1;
+    for (int attempt = 0; attempt <= nv; ++attempt) {
+      if (attempt > 0) {
+        do {
+          ++cand;
+        } while (cand < nv && (cand % rowmod) >= rowlive);
+        if (cand >= nv) break;
+        if (lane < nv) V[lane * 33 + j] = (lane == cand) ? 1.0 : 0.0;
+        __syncwarp();
+      }
+      double x = (lane < nv) ? V[lane * 33 + j] : 0.0;
+      const double n0 = sqrt(warp_sum(x * x));
+      for (int pass = 0; pass < 2; ++pass) {
+        double hc = 0.0;
+        if (lane < j)
+          for (int i = 0; i < nv; ++i) hc += V[i * 33 + lane] * V[i * 33 + j];
+        h[lane] = hc;
+        __syncwarp();
+        if (lane < nv) {
+          double v = V[lane * 33 + j];
+          for (int c = 0; c < j; ++c) v -= h[c] * V[lane * 33 + c];
+          V[lane * 33 + j] = v;
+        }
+        __syncwarp();
+      }
+      x = (lane < nv) ? V[lane * 33 + j] : 0.0;
+      const double n1 = sqrt(warp_sum(x * x));
+      if (n1 > 1e-12 * n0 && n1 > 0.0) {
+        if (lane < nv) V[lane * 33 + j] = x / n1;
+        __syncwarp();
+        break;
+      }
+    }
+  }
+  __syncwarp();
+  for (int idx = lane; idx < nv * ldv; idx += 32) {
+    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+    Vg[idx] = V[i * 33 + c];
+  }
+}
+
 // Classical Gram-Schmidt applied twice (FP64) to the first K columns of V (nv x ldv), in
 // column order: V[:, :K] becomes Q of V[:, :K] = Q T and sig[j] = |T_jj|.  With the columns in
 // order of decreasing norm and P = A U for nearly orthogonal U, T is upper triangular with
@@ -1186,7 +1243,11 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
     k_sort_cols<<<1, 1024, 0, s>>>(n2, n2, n2, sig2, V2, tmp2); count_launch();
     k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
                               j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
-    k_orthonormalise<<<1, 1024, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr); count_launch();
+    if (n2 <= 32)
+      k_orthonormalise_warp<<<1, 32, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
+    else
+      k_orthonormalise<<<1, 1024, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
+    count_launch();
     small_gemm<double, double>(s, R * n1, K2, n2, Y, n2, 1, V2, n2, 1, Y2, K2, &j.ctrl->k[1], nullptr);
     small_gemm<double, double>(s, R * n1, K2, n2, j.B0, n2, 1, V2, n2, 1, B0p, K2, &j.ctrl->k[1], nullptr);
   }
