@@ -1138,7 +1138,7 @@ tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const double* M, 
 }
 
 // V[:, :K] (nv x ldv, row-major) <- Q and sig[j] = |T_jj| of V[:, :K] = Q T, by CholeskyQR2
-// in FP64 for K <= 128, by one-CTA Gram-Schmidt beyond.
+// in FP64 for K <= 112, by one-CTA Gram-Schmidt beyond.
 static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K, double* sig, Bump& ws) {
   const int KK = K * K;
   const int nchunks = (nv + kGramChunkRows - 1) / kGramChunkRows;
@@ -1148,7 +1148,7 @@ static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K
   double* T2 = ws.take<double>(KK);
   double* Minv = ws.take<double>(KK);
   if (ws.dry) return TT_OK;
-  if (K > 128 || nv < 1) {
+  if (K > 112 || nv < 1) {  // the inverse kernel holds 2 K^2 doubles in shared memory
     k_cgs2_sigma<<<1, 1024, 0, s>>>(nv, ldv, V, K, sig); count_launch();
     return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
