@@ -257,3 +257,22 @@ def test_step_rejects_mismatched_plan(tt, ctx):
     with pytest.raises(tt.TTError) as e:
         tt.tt_step(ctx, plan, x, 1e-6, 4)
     assert e.value.status == tt.TT_ERR_SHAPE
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_step_too_wide_for_tsqr_is_refused_cleanly(tt, ctx, prec):
+    """Rank capacity 52 makes the transport sum 5 x 52 = 260 columns, beyond the 256 the TSQR
+    kernels take: TT_ERR_UNSUPPORTED before the state is touched, and the context stays usable."""
+    wl = small_plane()
+    plan = tt.Plan(ctx, wl)
+    x = tt.initial_state(plan, [52, 52], "f64")
+    before = [c.cpu().numpy().copy() for c in x.cores]
+    with pytest.raises(tt.TTError) as e:
+        tt.tt_step(ctx, plan, x, 1e-6, 52, prec)
+    assert e.value.status == tt.TT_ERR_UNSUPPORTED
+    ctx.sync()
+    for a, b in zip(before, x.cores):
+        assert np.array_equal(a, b.cpu().numpy())
+    y = tt.initial_state(plan, [8, 8], "f64")
+    tt.tt_step(ctx, plan, y, 1e-6, 8, prec)
+    ctx.sync()
