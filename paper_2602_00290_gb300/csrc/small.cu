@@ -444,6 +444,15 @@ __global__ void k_tail_from_fro(int K, const double* __restrict__ sig, const dou
   *tail = t > 0.0 ? t : 0.0;
 }
 
+// Energy beyond the first K of n sorted singular values that are accurate to FP64 (the squared
+// tail, like k_tail_from_fro, but without the cancellation of ||A||^2 - sum sigma^2).
+__global__ void k_tail_from_sigma(int n, int K, const double* __restrict__ sig, double* __restrict__ tail) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s2 = 0.0;
+  for (int j = n - 1; j >= K; --j) s2 += sig[j] * sig[j];
+  *tail = s2;
+}
+
 __global__ void k_copy_cols(int nv, int ncols, const double* __restrict__ A, int lda, double* __restrict__ B, int ldb) {
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)nv * ncols;
        idx += (long)gridDim.x * blockDim.x) {
@@ -1208,11 +1217,53 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
-// d = 3 small-core sweep with FP32 rotations and FP64 singular values/vectors: for each bond
-// an FP32 Jacobi on R^T gives nearly orthogonal right vectors U; P = A U in FP64, sorted by
-// column norm; Gram-Schmidt of the leading columns gives FP64 singular values |T_jj| and
-// orthonormal left vectors; the energy beyond them comes from Pythagoras.  Same outputs as
-// the FP64 sweep.
+__global__ void k_iota(int n, int* __restrict__ p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+// The same outputs as svd_right_mixed in FP64: FP64 Householder TSQR of the small matrix, then
+// the cooperative FP64 one-sided Jacobi on R^T (row p of R is column p of R^T, contiguous),
+// which converges in fewer sweeps than Jacobi on the matrix itself (Drmac-Veselic) and works on
+// columns of length cols instead of rows.  U comes sorted by decreasing singular value, so perm is
+// the identity; raw holds the FP64 singular values.
+template <class Src>
+static tt_status svd_right_f64pre(cudaStream_t s, int num_sms, const Src& src, long rows, int cols, Bump& ws,
+                                  double** U_out, double** P_out, double* raw, int* perm, DevCtrl* ctrl,
+                                  int grid_max) {
+  LivePattern lp{nullptr, cols, 1, 0};
+  const long L = tsqr_max_leaves<double, 32>(num_sms, cols, rows, 8);
+  double* a = ws.take<double>((size_t)L * cols * cols);
+  double* b = ws.take<double>((size_t)((L + 1) / 2) * cols * cols);
+  double* U = ws.take<double>((size_t)cols * cols);
+  double* P = ws.take<double>((size_t)rows * cols);
+  double* tmp = ws.take<double>(cols);
+  int* perm_j = ws.take<int>(cols);
+  *U_out = U;
+  *P_out = P;
+  if (ws.dry) return TT_OK;
+  double* R = nullptr;
+  tt_status st = run_tsqr<double, 32>(s, num_sms, src, lp, rows, 8, a, b, &R);
+  if (st != TT_OK) return st;
+  st = coop_jacobi(s, num_sms, cols, cols, R, nullptr, raw, U, cols, cols, nullptr, perm_j, tmp, ctrl, grid_max);
+  if (st != TT_OK) return st;
+  k_iota<<<(cols + 255) / 256, 256, 0, s>>>(cols, perm); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+template <bool F64, class Src>
+static tt_status svd_right_pre(cudaStream_t s, int num_sms, const Src& src, long rows, int cols, Bump& ws,
+                               double** U_out, double** P_out, double* raw, int* perm, DevCtrl* ctrl, int grid_max) {
+  if (F64) return svd_right_f64pre(s, num_sms, src, rows, cols, ws, U_out, P_out, raw, perm, ctrl, grid_max);
+  return svd_right_mixed(s, num_sms, src, rows, cols, ws, U_out, P_out, raw, perm, ctrl);
+}
+
+// d = 3 small-core sweep.  For each bond a TSQR of the small matrix A and a one-sided Jacobi on
+// R^T give right vectors U (mixed path: FP32 TSQR and one-CTA FP32 Jacobi, U nearly orthogonal;
+// F64: FP64 TSQR and the cooperative FP64 Jacobi).  P = A U in FP64, sorted by column norm;
+// CholeskyQR2 of the leading columns gives FP64 singular values |T_jj| and orthonormal left
+// vectors; the energy beyond them comes from the FP64 Jacobi singular values (F64) or from
+// Pythagoras (mixed).
+template <bool F64>
 static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws, const double* Y) {
   const int R = j.lp.ncap();
   const int n1 = j.n1, n2 = j.n2, nang = n1 * n2;
@@ -1224,8 +1275,8 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   double* V2 = ws.take<double>((size_t)n2 * n2);
   double* tmp2 = ws.take<double>((size_t)n2 * n2);
   double *U2 = nullptr, *P2 = nullptr;
-  tt_status st = svd_right_mixed(s, num_sms, SrcRows<double>{Y, n2}, (long)R * n1, n2, ws, &U2, &P2, sigc2, perm2,
-                                 j.ctrl);
+  tt_status st = svd_right_pre<F64>(s, num_sms, SrcRows<double>{Y, n2}, (long)R * n1, n2, ws, &U2, &P2, sigc2,
+                                   perm2, j.ctrl, j.coop_grid_max);
   if (st != TT_OK) return st;
   double* P2s = ws.take<double>((size_t)R * n1 * n2);
   const int nv = n1 * K2;
@@ -1262,7 +1313,8 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   double* tmpK = ws.take<double>((size_t)nv * Kr);
   double* V1 = ws.take<double>((size_t)nv * K1);
   double *U1 = nullptr, *P1 = nullptr;
-  st = svd_right_mixed(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &U1, &P1, sigc1, perm1, j.ctrl);
+  st = svd_right_pre<F64>(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &U1, &P1, sigc1, perm1, j.ctrl,
+                          j.coop_grid_max);
   if (st != TT_OK) return st;
   if (!ws.dry) {
     small_gemm<double, double>(s, nv, R, R, Y2, 1, nv, U1, R, 1, P1, R, nullptr, nullptr);  // P1 = A1 U1
@@ -1271,9 +1323,14 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   }
   st = cholqr2_sigma(s, nv, R, P1s, Kr, sig1, ws);
   if (st != TT_OK || ws.dry) return st;
-  // energy beyond the Kr refined values: ||A1||_F^2 - sum sigma_j^2 (FP64)
-  k_fro2<<<1, 1024, 0, s>>>((long)R * nv, Y2, fro1); count_launch();
-  k_tail_from_fro<<<1, 32, 0, s>>>(Kr, sig1, fro1, tailK); count_launch();
+  // energy beyond the Kr refined values: from the FP64 Jacobi singular values (FP64 path), or
+  // ||A1||_F^2 - sum sigma_j^2 (mixed path; accurate to about sqrt(eps_64) ||A1||)
+  if (F64) {  // the FP64 Jacobi singular values resolve the whole tail
+    k_tail_from_sigma<<<1, 32, 0, s>>>(R, Kr, sigc1, tailK); count_launch();
+  } else {
+    k_fro2<<<1, 1024, 0, s>>>((long)R * nv, Y2, fro1); count_launch();
+    k_tail_from_fro<<<1, 32, 0, s>>>(Kr, sig1, fro1, tailK); count_launch();
+  }
   k_sort_cols<<<1, 1024, 0, s>>>(nv, R, Kr, sig1, P1s, tmpK); count_launch();
   k_decide<<<1, 32, 0, s>>>(sig1, Kr, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
                             nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, tailK); count_launch();
@@ -1310,43 +1367,7 @@ tt_status small_round(cudaStream_t s, int num_sms, const SmallJob& j, Bump& ws) 
   }
   // ---- d = 3 ----
   const int K1 = j.K1cap, K2 = j.K2cap;
-  if (j.mixed) return small_round_mixed3(s, num_sms, j, ws, Y);
-  // bond 2: SVD of Y viewed as (R n1) x n2
-  double* sig2 = ws.take<double>(n2);
-  double* V2 = ws.take<double>((size_t)n2 * n2);
-  st = svd_right(s, num_sms, R * n1, n2, Y, ws, sig2, V2, j.ctrl, j.coop_grid_max);
-  if (st != TT_OK) return st;
-  const int nv = n1 * K2;
-  double* Y2 = ws.take<double>((size_t)R * nv);
-  double* B0p = ws.take<double>((size_t)R * nv);
-  if (!ws.dry) {
-    k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
-                              j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
-    small_gemm<double, double>(s, R * n1, K2, n2, Y, n2, 1, V2, n2, 1, Y2, K2, &j.ctrl->k[1], nullptr);
-    small_gemm<double, double>(s, R * n1, K2, n2, j.B0, n2, 1, V2, n2, 1, B0p, K2, &j.ctrl->k[1], nullptr);
-  }
-  // bond 1: one-sided Jacobi directly on Y2^T (its columns are the rows of Y2, length
-  // n1 K2); the normalised converged columns are the right singular vectors V1 of the
-  // unfolding R x (n1 K2), so no Q factor, no accumulated rotations and no division by
-  // small singular values are needed.
-  double* sig1 = ws.take<double>(R);
-  double* tmp1 = ws.take<double>(R);
-  int* perm1 = ws.take<int>(R);
-  double* V1 = ws.take<double>((size_t)nv * K1);
-  if (ws.dry) return TT_OK;
-  st = coop_jacobi(s, num_sms, nv, R, Y2, nullptr, sig1, V1, K1, K1 < R ? K1 : R, nullptr, perm1, tmp1, j.ctrl,
-                   j.coop_grid_max);
-  if (st != TT_OK) return st;
-  k_decide<<<1, 32, 0, s>>>(sig1, R, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
-                            nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, nullptr); count_launch();
-  k_fix_zero_columns<<<1, 1024, 0, s>>>(nv, K1, V1, sig1, &j.ctrl->k[0], K2, &j.ctrl->k[1]); count_launch();
-  k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2); count_launch();
-  // W = B0p (R x nv) V1 (nv x K1)
-  small_gemm<double, double>(s, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], nullptr);
-  // Bnew = core1 (K1 n1 x K2) core2 (K2 x n2); vJ
-  small_gemm<double, double>(s, K1 * n1, n2, K2, j.core1, K2, 1, j.core2, n2, 1, j.Bnew, n2, nullptr, nullptr);
-  k_vj<<<K1, 128, 0, s>>>(K1, nang, j.Bnew, j.domega, j.vJ); count_launch();
-  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+  return j.mixed ? small_round_mixed3<false>(s, num_sms, j, ws, Y) : small_round_mixed3<true>(s, num_sms, j, ws, Y);
 }
 
 }  // namespace ttk
