@@ -63,12 +63,16 @@ typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_precision;
 
 typedef enum { TT_QUAD_GAUSS_LEGENDRE_MU = 0, TT_QUAD_LATLONG_MIDPOINT = 1 } tt_quadrature;
 
-/* Numerical flux of the transport operator (Appendix A, 'Value of n'; both give n = 2 d_X rank-1
- * terms).  UPWIND: per axis the two one-sided differences times n_a 1[n_a >= 0] and n_a 1[n_a < 0].
- * RUSANOV: per axis the central difference (I_{i+1} - I_{i-1})/2 times n_a and the isotropic
- * diffusion term -(I_{i+1} - 2 I_i + I_{i-1})/2 (largest speed alpha = c), read with vacuum
- * ghost cells: a Rusanov problem with an inflow face is TT_ERR_UNSUPPORTED. */
-typedef enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1 } tt_flux;
+/* Numerical flux of the transport operator (Appendix A, 'Value of n').
+ * UPWIND: n = 2 d_X rank-1 terms, per axis the two one-sided differences times n_a 1[n_a >= 0]
+ *   and n_a 1[n_a < 0].
+ * RUSANOV: n = 2 d_X, per axis the central difference (I_{i+1} - I_{i-1})/2 times n_a and the
+ *   isotropic diffusion term -(I_{i+1} - 2 I_i + I_{i-1})/2 (largest speed alpha = c).
+ * CENTRAL: n = d_X, the Rusanov flux with wavespeed S+ = 0 (the pure central difference the
+ *   Gaussian-diffusion test of Sec. 4.3 uses): per axis the central-difference term only.
+ * RUSANOV and CENTRAL are read with vacuum ghost cells: a problem with an inflow face is
+ * TT_ERR_UNSUPPORTED. */
+typedef enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_CENTRAL = 2 } tt_flux;
 
 typedef struct {
   int32_t d;                       /* number of cores, 2 or 3                               */

@@ -73,7 +73,7 @@ class DenseSolver:
         p.acoef, p.scoef, p.eps = _ptr(self._keep[4]), _ptr(self._keep[5]), _ptr(self._keep[6])
         for f in range(6):
             p.inflow[f] = _ptr(self._inflow[f])
-        p.flux = 1 if c.flux == "rusanov" else 0
+        p.flux = {"upwind": 0, "rusanov": 1, "central": 2}[c.flux]
         p.alpha_local = 1 if c.alpha_local else 0
         self._p = p
         self._lib = _load()

@@ -18,7 +18,8 @@
  * F_{i+1/2} = n (I_i + I_{i+1}) / 2 - alpha (I_{i+1} - I_i) / 2 with alpha = 1 (the largest
  * speed, c |n| <= c), i.e. T I_i = lam [ n (I_{i+1} - I_{i-1}) / 2 - (I_{i+1} - 2 I_i + I_{i-1}) / 2 ],
  * read with vacuum ghost cells (0) on every face.  alpha_local = 1 takes alpha = |n| per direction
- * instead, which is the upwind flux again (a consistency check of the two schemes).
+ * instead, which is the upwind flux again (a consistency check of the two schemes).  flux = 2 is
+ * the Rusanov flux with wavespeed S+ = alpha = 0, the pure central difference of Sec. 4.3.
  * Layout: I[k * nang + q], merged row k = g + G*(ix + nx*(iy + ny*iz)), angle q.
  */
 #include <math.h>
@@ -37,7 +38,7 @@ typedef struct {
     const double *scoef;    /* per row: c dt rho kappa_s */
     const double *eps;      /* per row: emission epsilon_f(T) */
     const double *inflow[6];/* per face (x-,x+,y-,y+,z-,z+): G-spectrum or NULL (vacuum) */
-    int flux;               /* 0 upwind, 1 Rusanov (vacuum ghost cells) */
+    int flux;               /* 0 upwind, 1 Rusanov, 2 central (vacuum ghost cells) */
     int alpha_local;        /* Rusanov with alpha = |n| (reduces to upwind) */
 } dense_params;
 
@@ -74,10 +75,10 @@ int dense_step(const dense_params *p, const double *I, double *Iout, double *Ist
                 double acc = 0.0;
                 for (int ax = 0; ax < p->ndim; ++ax) {
                     double n = p->dir[ax][q];
-                    if (p->flux == 1) {
+                    if (p->flux == 1 || p->flux == 2) {
                         const double lo = (idx[ax] > 0) ? I[(k - stride[ax]) * nang + q] : 0.0;
                         const double hi = (idx[ax] < extent[ax] - 1) ? I[(k + stride[ax]) * nang + q] : 0.0;
-                        const double alpha = p->alpha_local ? fabs(n) : 1.0;
+                        const double alpha = (p->flux == 2) ? 0.0 : (p->alpha_local ? fabs(n) : 1.0);
                         acc += p->lam[ax] * (0.5 * n * (hi - lo) - 0.5 * alpha * (hi - 2.0 * v + lo));
                         continue;
                     }

@@ -188,19 +188,24 @@ def angular_terms(coef):
     Returns a list of (axis, w, factors) where factors is one diagonal per angular core
     such that n_axis * 1[n_axis (>=|<) 0] = prod of the factors over the angular nodes (upwind,
     w = +1 / -1).  For the Rusanov flux the two terms of an axis are w = +2 (the central
-    difference, factors of the full n_axis) and w = -2 (the diffusion term, factors 1)."""
+    difference, factors of the full n_axis) and w = -2 (the diffusion term, factors 1); the
+    central flux (Rusanov with wavespeed S+ = 0, Sec. 4.3) keeps the w = +2 term only."""
     d = coef.dirs
     terms = []
-    if getattr(coef, "flux", "upwind") == "rusanov":
+    flux = getattr(coef, "flux", "upwind")
+    if flux in ("rusanov", "central"):
+        diffusion = flux == "rusanov"
         if coef.ntheta > 0 and coef.nphi == 1 and "w" in d:
             terms.append((0, +2, [d["mu"]]))
-            terms.append((0, -2, [np.ones_like(d["mu"])]))
+            if diffusion:
+                terms.append((0, -2, [np.ones_like(d["mu"])]))
             return terms
         mu, phi, st = d["mu"], d["phi"], d["sintheta"]
         full = {0: [st, np.cos(phi)], 1: [st, np.sin(phi)], 2: [mu, np.ones(coef.nphi)]}
         for ax in range(coef.ndim):
             terms.append((ax, +2, full[ax]))
-            terms.append((ax, -2, [np.ones(coef.ntheta), np.ones(coef.nphi)]))
+            if diffusion:
+                terms.append((ax, -2, [np.ones(coef.ntheta), np.ones(coef.nphi)]))
         return terms
     if coef.ntheta > 0 and coef.nphi == 1 and "w" in d:   # planar slab, single mu core
         mu = d["mu"]

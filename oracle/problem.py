@@ -37,7 +37,8 @@ class StepCoefficients:
     dA: np.ndarray             # face area per axis (3,)
     c: float
     dt: float
-    flux: str = "upwind"       # "upwind" or "rusanov" (Appendix A, 'Value of n')
+    flux: str = "upwind"       # "upwind", "rusanov" or "central" (Appendix A, 'Value of n';
+                               # "central" is the Rusanov flux with wavespeed S+ = 0, Sec. 4.3)
     alpha_local: bool = False  # Rusanov with the local speed |n_a| (reduces to upwind; a pin)
 
     @property
@@ -67,9 +68,9 @@ def build(wl) -> StepCoefficients:
     dV = float(np.prod(dx[:wl.ndim]))
     dA = np.array([dV / dx[a] for a in range(3)])
     flux = getattr(wl, "flux", "upwind")
-    if flux not in ("upwind", "rusanov"):
+    if flux not in ("upwind", "rusanov", "central"):
         raise ValueError(f"unknown flux {flux!r}")
-    if flux == "rusanov" and any(b is not None for b in inflow):
+    if flux in ("rusanov", "central") and any(b is not None for b in inflow):
         raise ValueError("the Rusanov flux is read with vacuum ghost cells only")
     return StepCoefficients(wl.ndim, wl.nx, wl.ny, wl.nz, wl.ngroup, wl.ntheta, wl.nphi,
                             lam, acoef, scoef, eps, inflow, quadrature.directions(wl),

@@ -314,7 +314,7 @@ class Plan:
         for f in range(6):
             t = wl.inflow_temperature[f] if f < len(wl.inflow_temperature) else None
             p.inflow_temperature[f] = -1.0 if t is None else float(t)
-        p.flux = {"upwind": 0, "rusanov": 1}[getattr(wl, "flux", "upwind")]
+        p.flux = {"upwind": 0, "rusanov": 1, "central": 2}[getattr(wl, "flux", "upwind")]
         rcv = getattr(wl, "rho_cv", None)
         if rcv is not None:
             self._arrays.append(torch.as_tensor(np.asarray(rcv, dtype=np.float64), device=dev).contiguous())

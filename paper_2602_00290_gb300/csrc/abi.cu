@@ -238,8 +238,9 @@ tt_status tt_plan_create(tt_context* ctx, const tt_problem* prob, tt_plan** out)
   if (!(prob->c > 0) || !(prob->dt > 0) || !(prob->dx > 0)) return TT_ERR_ARG;
   if (prob->ndim_x >= 2 && !(prob->dy > 0)) return TT_ERR_ARG;
   if (prob->ndim_x >= 3 && !(prob->dz > 0)) return TT_ERR_ARG;
-  if (prob->flux != TT_FLUX_UPWIND && prob->flux != TT_FLUX_RUSANOV) return TT_ERR_ARG;
-  if (prob->flux == TT_FLUX_RUSANOV)
+  if (prob->flux != TT_FLUX_UPWIND && prob->flux != TT_FLUX_RUSANOV && prob->flux != TT_FLUX_CENTRAL)
+    return TT_ERR_ARG;
+  if (prob->flux != TT_FLUX_UPWIND)
     for (int f = 0; f < 2 * prob->ndim_x; ++f)
       if (prob->inflow_temperature[f] >= 0.0) return TT_ERR_UNSUPPORTED;
   set_device(ctx);

@@ -111,7 +111,7 @@ struct tt_plan {
   int n1, n2;     // angular mode sizes (n2 = 1 when d = 2)
   long nrow;      // N_Z
   double lam[3], c, dt, dV;
-  int nterm;                    // 2 d_X
+  int nterm;                    // 2 d_X (upwind, Rusanov) or d_X (central)
   int term_axis[ttk::kMaxTerms], term_w[ttk::kMaxTerms];
   int nbc;                      // operators whose upwind face has inflow
   int bc_term[ttk::kMaxTerms];  // operator index of each inflow column

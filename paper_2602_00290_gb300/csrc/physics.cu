@@ -59,8 +59,9 @@ __global__ void k_quadrature(int quad, int ntheta, int nphi, double* mu, double*
   }
 }
 
-// Angular factors of the 2 d_X rank-1 transport operators (Appendix A, 'Value of n'):
-// n_a * 1[n_a >= 0] (w = +) or n_a * 1[n_a < 0] (w = -), split over the angular cores.
+// Angular factors of the rank-1 transport operators (Appendix A, 'Value of n'), split over the
+// angular cores: upwind n_a * 1[n_a >= 0] (w = +1) or n_a * 1[n_a < 0] (w = -1); Rusanov and
+// central n_a (w = +2) and, Rusanov only, 1 (w = -2).
 __global__ void k_angular_factors(int d, int nterm, const int* axis, const int* w, int n1,
                                   int n2, const double* mu, const double* phi, double* fac1,
                                   double* fac2) {
@@ -317,17 +318,20 @@ tt_status physics_setup(tt_context* ctx, const tt_problem* p, tt_plan* plan) {
   plan->stride[0] = G;
   plan->stride[1] = (long)G * p->nx;
   plan->stride[2] = (long)G * p->nx * p->ny;
-  plan->nterm = 2 * p->ndim_x;
+  // upwind and Rusanov: two terms per axis; central (Rusanov with wavespeed 0): one per axis
+  const bool central = (p->flux == TT_FLUX_CENTRAL);
+  const bool upwind = (p->flux == TT_FLUX_UPWIND);
+  plan->nterm = (central ? 1 : 2) * p->ndim_x;
   int faces[kMaxTerms];
   double sgnlam[kMaxTerms];
   plan->nbc = 0;
-  const bool rusanov = (p->flux == TT_FLUX_RUSANOV);
   for (int t = 0; t < plan->nterm; ++t) {
-    plan->term_axis[t] = t / 2;
-    // upwind: +1 / -1 (one-sided differences); Rusanov: +2 (central) / -2 (diffusion)
-    plan->term_w[t] = ((t % 2 == 0) ? +1 : -1) * (rusanov ? 2 : 1);
+    // upwind: +1 / -1 (one-sided differences); Rusanov: +2 (central) / -2 (diffusion);
+    // central: +2 only
+    plan->term_axis[t] = central ? t : t / 2;
+    plan->term_w[t] = central ? 2 : ((t % 2 == 0) ? +1 : -1) * (upwind ? 1 : 2);
     const int face = 2 * (t / 2) + (t % 2);  // w=+ reads the minus-face ghost
-    if (!rusanov && p->inflow_temperature[face] >= 0.0) {
+    if (upwind && p->inflow_temperature[face] >= 0.0) {
       plan->bc_term[plan->nbc] = t;
       faces[plan->nbc] = face;
       sgnlam[plan->nbc] = (t % 2 == 0 ? 1.0 : -1.0) * plan->lam[t / 2];

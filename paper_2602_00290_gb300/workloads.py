@@ -55,7 +55,7 @@ class Workload:
     rho_kappa_a: np.ndarray        # (N_X*G,) per merged row
     rho_kappa_s: np.ndarray        # (N_X*G,) per merged row
     rho_cv: Optional[np.ndarray] = None  # per cell: couples the material temperature
-    flux: str = "upwind"            # "upwind" or "rusanov" (vacuum boundaries only)
+    flux: str = "upwind"            # "upwind", "rusanov" or "central" (vacuum boundaries only)
     inflow_temperature: Tuple[Optional[float], ...] = (None,) * 6
     initial_temperature: Optional[np.ndarray] = None  # radiation temperature per cell for I^0
     tol: float = 1e-6
@@ -206,6 +206,25 @@ def batch_config3(nprob: int = 256, seed: int = 3, scale: int = 1, tol: float = 
         out.append(replace(wl, name=f"batch{i}_{n}x{n}_g{G}_{nth}x{nph}_r{rmax}",
                            inflow_temperature=(Tb, None, None, None, None, None)))
     return out
+
+
+def gaussian_diffusion_config(nx: int = 128, G: int = 8, kappa_max: float = 2000.0, ntheta: int = 16,
+                              rmax: int = 16, tol: float = 1e-6, steps: int = 4000,
+                              seed: int = 4) -> Workload:
+    """The multigroup Gaussian-diffusion slab of Sec. 4.3 at reduced size: nx cells on [-5, 5],
+    rho = c = 1, pure scattering with rho*kappa_s[f] ~ U[1000, kappa_max] (seeded, the same in
+    every cell), no absorption, CFL = 1 (dt = dx), vacuum faces, the central flux (Rusanov with
+    wavespeed 0).  The temperature is irrelevant (kappa_a = 0) and set to 1.  The initial field
+    (an isotropic Gaussian per group) is built by the consumer, not here."""
+    rng = np.random.default_rng(seed)
+    ks = rng.uniform(1000.0, kappa_max, G)
+    L = 10.0
+    return Workload(
+        name=f"diffusion1d_nx{nx}_g{G}_mu{ntheta}_kmax{int(kappa_max)}", ndim=1, nx=nx, ny=1, nz=1,
+        ngroup=G, quad="gauss_legendre_mu", ntheta=ntheta, nphi=1, extent=(L, 1.0, 1.0),
+        c=1.0, dt=L / nx, group_edges=group_edges(G), temperature=np.ones(nx),
+        rho_kappa_a=np.zeros(nx * G), rho_kappa_s=np.tile(ks, nx), flux="central",
+        tol=tol, rmax=rmax, steps=steps, seed=seed)
 
 
 def sketch_matrix(nang: int, ell: int, seed: int = 11) -> np.ndarray:

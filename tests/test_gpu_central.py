@@ -1,0 +1,175 @@
+"""The central flux (Rusanov with wavespeed S+ = 0, the flux of the Gaussian-diffusion test of
+Sec. 4.3) on the GPU: the transport sum against the oracle's explicit sum (1e-13), rounded FP64
+steps against the naive TT oracle (1e-10, identical ranks away from ties), the mixed path in
+energy density (1e-6), and the CUDA path's multigroup Gaussian diffusion after 4000 steps against
+the closed form of Eq. (diffusion) (0.5 % of each group's peak; t_0 = 0.25 / D_f so that the
+initial Gaussian is resolved on 128 cells) and against the naive TT oracle's run of the same steps."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import naive_tt as nt, problem  # noqa: E402
+from paper_2602_00290_gb300.workloads import (gaussian_diffusion_config, plane_config1,  # noqa: E402
+                                              random_tt, slab_config0)
+
+TIE = 1e-9
+DT0 = 0.25
+
+
+@pytest.fixture(scope="module")
+def tt():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2602_00290_gb300 as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def ctx(tt):
+    return tt.Context(0)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b)))) / max(float(np.max(np.abs(np.asarray(b)))), 1e-300)
+
+
+def _plane(**kw):
+    args = dict(nx=12, ny=10, G=5, ntheta=4, nphi=8, rmax=8, tol=1e-6)
+    args.update(kw)
+    return plane_config1(**args).with_(flux="central")
+
+
+def diffusion_energy(wl, t):
+    """E_f(t, x; t_0) of Eq. (diffusion), A = 1, at the cell centres of [-5, 5], per merged row."""
+    G = wl.ngroup
+    dx = wl.extent[0] / wl.nx
+    x = -0.5 * wl.extent[0] + (np.arange(wl.nx) + 0.5) * dx
+    D = wl.c / (3.0 * np.asarray(wl.rho_kappa_s[:G]))
+    s = 4.0 * D[None, :] * (DT0 / D[None, :] + t)
+    return (np.exp(-x[:, None] ** 2 / s) / np.sqrt(math.pi * s)).reshape(-1)
+
+
+def diffusion_initial_cores(wl):
+    """Rank-1 isotropic TT I_f(0) = E_f(0, x) / (4 pi): Z = the rows, the mu core all ones."""
+    return [(diffusion_energy(wl, 0.0) / (4.0 * np.pi)).reshape(1, -1, 1), np.ones((1, wl.ntheta, 1))]
+
+
+@pytest.mark.parametrize("wl", [_plane(), slab_config0().with_(flux="central")], ids=["plane", "slab"])
+def test_central_apply_transport_matches_explicit_sum(tt, ctx, wl):
+    coef = problem.build(wl)
+    plan = tt.Plan(ctx, wl)
+    n = plan.n
+    r = [3] if len(n) == 2 else [3, 2]
+    a = random_tt(n, r, seed=6)
+    x = tt.TT.from_cores(a, rcap=[q + 1 for q in r])
+    want = nt.transport_sum(a, coef)
+    R = nt.ranks(want)[1:-1]
+    assert R[0] == (wl.ndim + 1) * r[0]
+    out = tt.TT(n, [q + 2 for q in R])
+    tt.tt_apply_transport(ctx, plan, x, out)
+    ctx.sync()
+    assert out.ranks()[1:-1] == R
+    assert rel(nt.full(out.to_cores()), nt.full(want)) < 1e-13
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(tol=1e-8, rmax=12), dict(nx=7, ny=9, G=3, ntheta=6, nphi=12, rmax=10)])
+def test_central_step_matches_naive_tt(tt, ctx, kw):
+    wl = _plane(**kw)
+    coef = problem.build(wl)
+    plan = tt.Plan(ctx, wl)
+    x = tt.initial_state(plan, [wl.rmax, wl.rmax], "f64")
+    ref = nt.initial_tt(problem.initial_rows(wl, coef), coef)
+    for s in range(4):
+        info = {}
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64")
+        ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
+        ctx.sync()
+        if all(b["gap"] > TIE for k in ("transport_round", "source_round") for b in info[k]["bonds"]):
+            assert x.ranks() == nt.ranks(ref), s
+        assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
+
+
+def test_central_diffusion_steps_match_naive_tt(tt, ctx):
+    wl = gaussian_diffusion_config(nx=64, G=6, ntheta=8, rmax=8)
+    coef = problem.build(wl)
+    plan = tt.Plan(ctx, wl)
+    a = diffusion_initial_cores(wl)
+    x = tt.TT.from_cores(a, rcap=[wl.rmax])
+    ref = a
+    for s in range(60):
+        info = {}
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64")
+        ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
+        if s % 10 == 9:
+            ctx.sync()
+            if all(b["gap"] > TIE for k in ("transport_round", "source_round") for b in info[k]["bonds"]):
+                assert x.ranks() == nt.ranks(ref), s
+            assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
+
+
+def test_central_mixed_energy_within_1e6(tt, ctx):
+    wl = _plane()
+    coef = problem.build(wl)
+    plan = tt.Plan(ctx, wl)
+    x = tt.initial_state(plan, [wl.rmax, wl.rmax], "f32")
+    ref = nt.initial_tt(problem.initial_rows(wl, coef), coef)
+    for s in range(4):
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "mixed")
+        ref = nt.step(ref, coef, wl.tol, wl.rmax)
+        ctx.sync()
+        E = tt.tt_energy_density(ctx, plan, x).cpu().numpy()
+        Er = nt.energy_density_rows(ref, coef)
+        assert np.linalg.norm(E - Er) <= 1e-6 * np.linalg.norm(Er), s
+
+
+@pytest.fixture(scope="module")
+def diffusion_ref():
+    """The naive TT oracle over the 4000 steps of the 128-cell, 8-group diffusion slab (a few
+    seconds on the host), once for both precisions."""
+    wl = gaussian_diffusion_config()
+    coef = problem.build(wl)
+    ref = diffusion_initial_cores(wl)
+    gaps = []
+    for _ in range(wl.steps):
+        info = {}
+        ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
+        gaps += [b["gap"] for k in ("transport_round", "source_round") for b in info[k]["bonds"]]
+    return wl, coef, ref, min(gaps)
+
+
+@pytest.mark.parametrize("prec,dtype", [("fp64", "f64"), ("mixed", "f32")])
+def test_central_gaussian_diffusion_closed_form(tt, ctx, diffusion_ref, prec, dtype):
+    """4000 tt_steps of the diffusion slab: every group within 0.5 % of its peak of Eq. (diffusion),
+    and the same run of the naive TT oracle within 1e-10 with the same ranks (FP64) or within 1e-5
+    in energy density (mixed: FP32 state, 4000 accumulated FP32 roundings)."""
+    wl, coef, ref, mingap = diffusion_ref
+    plan = tt.Plan(ctx, wl)
+    x = tt.TT.from_cores(diffusion_initial_cores(wl), rcap=[wl.rmax], dtype=dtype)
+    for _ in range(wl.steps):
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, prec)
+    ctx.sync()
+    E = tt.tt_energy_density(ctx, plan, x).cpu().numpy()
+    t = wl.steps * wl.dt
+    want = diffusion_energy(wl, t).reshape(wl.nx, wl.ngroup)
+    err = np.max(np.abs(E.reshape(wl.nx, wl.ngroup) - want), axis=0) / np.max(want, axis=0)
+    assert np.max(err) < 5e-3, err
+    Er = nt.energy_density_rows(ref, coef)
+    if prec == "fp64":
+        assert mingap > TIE
+        assert x.ranks() == nt.ranks(ref)
+        assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10
+    else:
+        assert np.linalg.norm(E - Er) <= 1e-5 * np.linalg.norm(Er)
+
+
+def test_central_plan_refuses_inflow(tt, ctx):
+    wl = _plane().with_(inflow_temperature=(0.8, None, None, None, None, None))
+    with pytest.raises(tt.TTError) as e:
+        tt.Plan(ctx, wl)
+    assert e.value.status == tt.TT_ERR_UNSUPPORTED
