@@ -64,6 +64,8 @@ struct SrcStencil {
   int w[kMaxTerms];
   int bc_term[kMaxTerms];  // operator of each inflow column
   const double* bcval;     // [nbc][G] signed lambda * inflow
+  int nax;                 // spatial axes d_X (every operator's axis is below it)
+  int staged;              // update pass: stage the tile's row blocks in shared memory (host choice)
   struct Col {
     int kind;  // 0: Z, 1: upwind image, 2: inflow column, 3: none, 4/5: Rusanov central/diffusion
     int q, ax, w, b;
@@ -133,6 +135,40 @@ struct SrcStencil {
       f |= (idx < ext[a] - 1 ? 1u : 0u) << (2 * a + 1);
     }
     return f | ((unsigned)(k % G) << 8);
+  }
+  // Staged form for a tile of TM rows starting at row0: block 0 holds Z rows row0.., block
+  // 1 + 2a rows row0 - s_a.., block 2 + 2a rows row0 + s_a.. (TM x ldz each, rows outside
+  // [0, nrows) zero).  Bytes of the staging buffer:
+  __host__ __device__ size_t stage_bytes(int TM) const { return sizeof(S) * (size_t)TM * ldz * (1 + 2 * nax); }
+  // The value of loadT(cc, row0 + m, fl) read from the staged blocks (same arithmetic).
+  template <typename T>
+  __device__ __forceinline__ T stagedT(const S* raw, int TM, const Col& cc, int m, unsigned fl) const {
+    const S* C = raw + (size_t)m * ldz + cc.q;
+    if (cc.kind == 0) return (T)*C;
+    if (cc.kind == 3) return T(0);
+    if (cc.kind == 2) {
+      const bool at_face = (cc.w > 0) ? !((fl >> (2 * cc.ax)) & 1u) : !((fl >> (2 * cc.ax + 1)) & 1u);
+      return at_face ? (T)bcval[cc.b * G + (int)(fl >> 8)] : T(0);
+    }
+    const S* L = C + (size_t)(1 + 2 * cc.ax) * TM * ldz;
+    const S* H = L + (size_t)TM * ldz;
+    const T lamT = (sizeof(T) == 8) ? (T)cc.lam : (T)cc.lamf;
+    if (cc.kind >= 4) {
+      const T lo = ((fl >> (2 * cc.ax)) & 1u) ? (T)*L : T(0);
+      const T hi = ((fl >> (2 * cc.ax + 1)) & 1u) ? (T)*H : T(0);
+      if (cc.kind == 4) return T(-0.5) * lamT * (hi - lo);
+      return T(0.5) * lamT * (hi - T(2) * (T)*C + lo);
+    }
+    const T zk = (T)*C;
+    T diff;
+    if (cc.w > 0) {
+      const T up = ((fl >> (2 * cc.ax)) & 1u) ? (T)*L : T(0);
+      diff = zk - up;
+    } else {
+      const T dn = ((fl >> (2 * cc.ax + 1)) & 1u) ? (T)*H : T(0);
+      diff = dn - zk;
+    }
+    return -lamT * diff;
   }
   // The value of load() in arithmetic T, from the row's flags.
   template <typename T>
@@ -207,9 +243,91 @@ struct LiveWalk {
   }
 };
 
+// FP32 form of the reflector loop on the packed two-lane FMA of sm_100+ (__ffma2_rn: each lane
+// rounds as one fmaf): the column owner's norm, the dot of the reflector with a column and the
+// column update each run BR/2 packed FMAs, and the reflector is read from shared memory in
+// 16-byte vectors.  Same arithmetic as the generic loop below up to the order of the partial sums.
+template <int BR>
+__device__ __forceinline__ void hh_absorb_x2(float* Rs, int ncap, float (&B)[BR], float* vbuf, float* taub,
+                                             int& buf, int jbeg, const LivePattern& lp, int r, bool mycol) {
+  static_assert(BR % 4 == 0, "block rows in float4 groups");
+  const int c = threadIdx.x;
+  LiveWalk walk(lp, jbeg);
+  for (int j = jbeg; j < ncap; ++j) {
+    if (!walk.next(lp, r)) continue;
+    float* vb = vbuf + buf * BR;
+    if (c == j) {
+      float2 xp0 = make_float2(0.f, 0.f), xp1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < BR; i += 4) {
+        xp0 = __ffma2_rn(make_float2(B[i], B[i + 1]), make_float2(B[i], B[i + 1]), xp0);
+        xp1 = __ffma2_rn(make_float2(B[i + 2], B[i + 3]), make_float2(B[i + 2], B[i + 3]), xp1);
+      }
+      const float x2 = (xp0.x + xp0.y) + (xp1.x + xp1.y);
+      float tau = 0.f;
+      if (x2 > 0.f) {
+        float* rjj = Rs + tri_off(j, ncap);
+        const float alpha = *rjj;
+        const float nrm = sqrtf(alpha * alpha + x2);
+        const float beta = (alpha >= 0.f) ? -nrm : nrm;
+        const float sc = chain_div<float>(1.f, alpha - beta);
+#pragma unroll
+        for (int i = 0; i < BR; i += 4)
+          *reinterpret_cast<float4*>(vb + i) = make_float4(B[i] * sc, B[i + 1] * sc, B[i + 2] * sc, B[i + 3] * sc);
+        tau = chain_div<float>(beta - alpha, beta);
+        *rjj = beta;
+#pragma unroll
+        for (int i = 0; i < BR; ++i) B[i] = 0.f;
+      }
+      taub[buf] = tau;
+    }
+    __syncthreads();
+    const float tau = taub[buf];
+    if (tau != 0.f && c > j && mycol) {
+      float* rjc = Rs + tri_off(j, ncap) + (c - j);
+      // up to 32 block rows the reflector stays in registers between the dot and the update;
+      // wider blocks read it again (their B already fills the register budget)
+      constexpr bool kKeep = BR <= 32;
+      float2 w0 = make_float2(*rjc, 0.f), w1 = make_float2(0.f, 0.f);
+      float v[kKeep ? BR : 1];
+#pragma unroll
+      for (int i = 0; i < BR; i += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(vb + i);
+        if constexpr (kKeep) {
+          v[i] = t.x; v[i + 1] = t.y; v[i + 2] = t.z; v[i + 3] = t.w;
+        }
+        w0 = __ffma2_rn(make_float2(t.x, t.y), make_float2(B[i], B[i + 1]), w0);
+        w1 = __ffma2_rn(make_float2(t.z, t.w), make_float2(B[i + 2], B[i + 3]), w1);
+      }
+      const float wv = ((w0.x + w0.y) + (w1.x + w1.y)) * tau;
+      *rjc -= wv;
+      const float2 nw = make_float2(-wv, -wv);
+#pragma unroll
+      for (int i = 0; i < BR; i += 4) {
+        float4 t;
+        if constexpr (kKeep) {
+          t = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+        } else {
+          t = *reinterpret_cast<const float4*>(vb + i);
+        }
+        const float2 u0 = __ffma2_rn(nw, make_float2(t.x, t.y), make_float2(B[i], B[i + 1]));
+        const float2 u1 = __ffma2_rn(nw, make_float2(t.z, t.w), make_float2(B[i + 2], B[i + 3]));
+        B[i] = u0.x; B[i + 1] = u0.y; B[i + 2] = u1.x; B[i + 3] = u1.y;
+      }
+    }
+    buf ^= 1;
+  }
+}
+
 template <typename T, int BR>
 __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, T* taub, int& buf,
                                           int jbeg, const LivePattern& lp, int r, bool mycol) {
+  // the packed form measured faster for 64-row blocks (5.57 against 5.76 ms for the bench's
+  // transport-sum leaf) and slower for 32-row blocks (5.51 against 5.39 ms)
+  if constexpr (sizeof(T) == 4 && BR % 4 == 0 && BR > 32) {
+    hh_absorb_x2<BR>(Rs, ncap, B, vbuf, taub, buf, jbeg, lp, r, mycol);
+    return;
+  }
   const int c = threadIdx.x;
   LiveWalk walk(lp, jbeg);
   for (int j = jbeg; j < ncap; ++j) {
@@ -397,6 +515,29 @@ inline long tsqr_max_leaves(int num_sms, int ncap, long nrows, int max_leaves) {
 // The per-row epilogue (the dot with vJ, scale, extra column, two energy partials) runs one
 // warp per row; per-CTA energy partials go to partials[2*cta + {0,1}] in a fixed order.
 
+// Bytes the update pass stages per tile: the stencil source's row blocks when the host chose
+// staging and its rows are 16-byte multiples at a 16-byte aligned base (cp.async granules),
+// else nothing.
+template <class Src>
+__host__ __device__ inline size_t update_stage_bytes(const Src&, int) { return 0; }
+template <typename S>
+__host__ __device__ inline size_t update_stage_bytes(const SrcStencil<S>& src, int TM) {
+  const bool ok = src.staged && ((size_t)src.ldz * sizeof(S)) % 16 == 0 && ((size_t)src.Z % 16) == 0 &&
+                  src.nax >= 1;
+  return ok ? src.stage_bytes(TM) : 0;
+}
+
+template <class Src>
+inline void set_staged(Src&, int) {}
+template <typename S>
+inline void set_staged(SrcStencil<S>& src, int on) { src.staged = on; }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename SO>
 struct EpiPlain {
   SO* out;
@@ -465,14 +606,62 @@ __device__ __forceinline__ const double* epi_vj(const Epi& e) {
 // Output columns of the update GEMM: kcap rounded up to a multiple of 4.
 template <class Epi>
 __host__ __device__ inline int update_kpad(int kcap) { return (kcap + 3) & ~3; }
+// Output tile bytes; the staged source rows share that region (they are consumed before the
+// GEMM writes it).
+template <typename T, int TM>
+__host__ __device__ inline size_t update_out_bytes(int kpad, size_t stage) {
+  const size_t o = sizeof(T) * (size_t)TM * kpad;
+  return ((o > stage ? o : stage) + 15) & ~(size_t)15;
+}
+// A tile bytes; after the last tile the region holds the 256 threads' energy partial pairs.
+template <typename T, int TM>
+__host__ __device__ inline size_t update_a_bytes(int ncap) {
+  const size_t a = sizeof(T) * (size_t)TM * (ncap + 1), red = sizeof(double) * 2 * 256;
+  return a > red ? a : red;
+}
 template <typename T, int TM, class Src, class Epi>
-__host__ __device__ inline size_t update_smem_bytes(int ncap, int kcap) {
+__host__ __device__ inline size_t update_smem_bytes(int ncap, int kcap, size_t stage = 0) {
   const int kpad = update_kpad<Epi>(kcap);
-  size_t b = sizeof(T) * ((size_t)ncap * kpad + (size_t)TM * (ncap + 1) + (size_t)TM * kpad);
+  size_t b = sizeof(T) * (size_t)ncap * kpad + update_a_bytes<T, TM>(ncap);
   b = (b + 15) & ~(size_t)15;
+  b += update_out_bytes<T, TM>(kpad, stage);
   b += sizeof(typename Src::Col) * (size_t)ncap;
   b = (b + 15) & ~(size_t)15;
-  return b + sizeof(double) * (3 * TM + 2 * 256) + sizeof(T) * (size_t)kpad + sizeof(unsigned) * TM + (size_t)ncap;
+  return b + sizeof(double) * (3 * TM) + sizeof(T) * (size_t)kpad + sizeof(unsigned) * TM + (size_t)ncap;
+}
+
+// Issue the cp.async copies of a tile's stencil row blocks (a no-op for other sources).
+template <int TM, class Src, typename T>
+__device__ __forceinline__ void stage_rows(const Src&, long, long, T*, int) {}
+template <int TM, typename S, typename T>
+__device__ __forceinline__ void stage_rows(const SrcStencil<S>& src, long row0, long nrows, T* buf, int tid) {
+  S* raw = reinterpret_cast<S*>(buf);
+  constexpr int kPer = 16 / (int)sizeof(S);  // elements per granule
+  const int gpr = src.ldz / kPer;            // granules per row
+  const int per_block = TM * gpr;
+  const int total = (1 + 2 * src.nax) * per_block;
+  for (int i = tid; i < total; i += (int)blockDim.x) {
+    const int b = i / per_block, rem = i - b * per_block;
+    const int m = rem / gpr, g = rem - m * gpr;
+    long k = row0 + m;
+    if (b > 0) {
+      const long sa = src.stride[(b - 1) >> 1];
+      k += ((b - 1) & 1) ? sa : -sa;
+    }
+    const bool ok = (k >= 0 && k < nrows);
+    S* dst = raw + ((size_t)b * TM + m) * src.ldz + (size_t)g * kPer;
+    const S* from = ok ? src.Z + k * src.ldz + (size_t)g * kPer : src.Z;
+    cp_async16(dst, from, ok ? 16 : 0);
+  }
+}
+template <typename T, int TM, class Src, typename B>
+__device__ __forceinline__ T staged_value(const Src& src, const B* buf, const typename Src::Col& cc, int m, unsigned f) {
+  return T(0);
+}
+template <typename T, int TM, typename S, typename B>
+__device__ __forceinline__ T staged_value(const SrcStencil<S>& src, const B* buf, const typename SrcStencil<S>::Col& cc,
+                                          int m, unsigned f) {
+  return src.template stagedT<T>(reinterpret_cast<const S*>(buf), TM, cc, m, f);
 }
 
 template <typename T, int TM, class Src, class Epi>
@@ -486,17 +675,20 @@ __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nr
   const int kpad = update_kpad<Epi>(kcap);
   const int lda = ncap + 1;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
+  const size_t stage = update_stage_bytes(src, TM);
   T* Ws = reinterpret_cast<T*>(upd_smem);    // [ncap][kpad]: W, then W vJ
   T* As = Ws + (size_t)ncap * kpad;          // [TM][ncap + 1]
-  T* Os = As + (size_t)TM * lda;             // [TM][kpad]
-  size_t off = sizeof(T) * ((size_t)ncap * kpad + (size_t)TM * lda + (size_t)TM * kpad);
+  size_t off = sizeof(T) * (size_t)ncap * kpad + update_a_bytes<T, TM>(ncap);
   off = (off + 15) & ~(size_t)15;
+  T* Os = reinterpret_cast<T*>(upd_smem + off);  // [TM][kpad], or the staged source rows
+  off += update_out_bytes<T, TM>(kpad, stage);
   Col* cols = reinterpret_cast<Col*>(upd_smem + off);
   off += sizeof(Col) * (size_t)ncap;
   off = (off + 15) & ~(size_t)15;
   double* rowv = reinterpret_cast<double*>(upd_smem + off);  // [3][TM]: J*, scale, extra
-  double* red = rowv + 3 * TM;                                // [blockDim][2] energy partials
-  T* vJs = reinterpret_cast<T*>(red + 2 * 256);               // [kpad] vJ in arithmetic T
+  // [blockDim][2] energy partials, after the last tile: in the A tile's region
+  double* red = reinterpret_cast<double*>(As);
+  T* vJs = reinterpret_cast<T*>(rowv + 3 * TM);               // [kpad] vJ in arithmetic T
   unsigned* fl = reinterpret_cast<unsigned*>(vJs + kpad);
   unsigned char* livec = reinterpret_cast<unsigned char*>(fl + TM);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
@@ -518,15 +710,33 @@ __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nr
     __syncthreads();  // previous tile's buffers are free (and the staging above is done)
     for (int m = tid; m < TM; m += blockDim.x) fl[m] = (row0 + m < nrows) ? src.row_flags(row0 + m) : 0u;
     __syncthreads();
-    // tile of A: one warp per row, lanes over columns (coalesced row reads)
+    if (stage > 0) {
+      // every 16-byte granule of the tile's source row blocks in flight at once (cp.async),
+      // rows outside [0, nrows) zero-filled; then the stencil columns from shared memory
+      stage_rows<TM>(src, row0, nrows, Os, tid);
+      cp_async_wait_all();
+      __syncthreads();
 #pragma unroll
-    for (int q = 0; q < TM / 8; ++q) {
-      const int m = warp + 8 * q;
-      if (m < TM) {
-        const long k = row0 + m;
-        const unsigned f = fl[m];
-        for (int c = lane; c < ncap; c += 32)
-          As[(size_t)m * lda + c] = (k < nrows && livec[c]) ? src.template loadT<T>(cols[c], k, f) : T(0);
+      for (int q = 0; q < TM / 8; ++q) {
+        const int m = warp + 8 * q;
+        if (m < TM) {
+          const long k = row0 + m;
+          const unsigned f = fl[m];
+          for (int c = lane; c < ncap; c += 32)
+            As[(size_t)m * lda + c] = (k < nrows && livec[c]) ? staged_value<T, TM>(src, Os, cols[c], m, f) : T(0);
+        }
+      }
+    } else {
+      // tile of A: one warp per row, lanes over columns (coalesced row reads)
+#pragma unroll
+      for (int q = 0; q < TM / 8; ++q) {
+        const int m = warp + 8 * q;
+        if (m < TM) {
+          const long k = row0 + m;
+          const unsigned f = fl[m];
+          for (int c = lane; c < ncap; c += 32)
+            As[(size_t)m * lda + c] = (k < nrows && livec[c]) ? src.template loadT<T>(cols[c], k, f) : T(0);
+        }
       }
     }
     __syncthreads();
@@ -539,15 +749,30 @@ __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nr
 #pragma unroll
           for (int u = 0; u < 4; ++u) acc[q][u] = T(0);
         const T* arow = As + (size_t)(mp * RPT) * lda;
+        if constexpr (sizeof(T) == 4) {
+          // packed two-lane FMAs: each lane rounds as one fmaf, same sums as the generic loop
 #pragma unroll 4
-        for (int c = 0; c < ncap; ++c) {
-          T w[4];
-          ld4(Ws + (size_t)c * kpad + j0, w);
+          for (int c = 0; c < ncap; ++c) {
+            const float4 w = *reinterpret_cast<const float4*>(Ws + (size_t)c * kpad + j0);
 #pragma unroll
-          for (int q = 0; q < RPT; ++q) {
-            const T a = arow[(size_t)q * lda + c];
+            for (int q = 0; q < RPT; ++q) {
+              const float a = arow[(size_t)q * lda + c];
+              const float2 lo = __ffma2_rn(make_float2(a, a), make_float2(w.x, w.y), make_float2(acc[q][0], acc[q][1]));
+              const float2 hi = __ffma2_rn(make_float2(a, a), make_float2(w.z, w.w), make_float2(acc[q][2], acc[q][3]));
+              acc[q][0] = lo.x; acc[q][1] = lo.y; acc[q][2] = hi.x; acc[q][3] = hi.y;
+            }
+          }
+        } else {
+#pragma unroll 4
+          for (int c = 0; c < ncap; ++c) {
+            T w[4];
+            ld4(Ws + (size_t)c * kpad + j0, w);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[q][u] += a * w[u];
+            for (int q = 0; q < RPT; ++q) {
+              const T a = arow[(size_t)q * lda + c];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[q][u] += a * w[u];
+            }
           }
         }
 #pragma unroll
@@ -612,8 +837,8 @@ __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nr
 
 // Persistent grid of the update pass (also the number of energy partials it writes).
 template <typename T, int TM, class Src, class Epi>
-inline long update_grid(int num_sms, int ncap, int kcap, long nrows) {
-  const size_t smem = update_smem_bytes<T, TM, Src, Epi>(ncap, kcap);
+inline long update_grid(int num_sms, int ncap, int kcap, long nrows, size_t stage = 0) {
+  const size_t smem = update_smem_bytes<T, TM, Src, Epi>(ncap, kcap, stage);
   cudaFuncSetAttribute(k_update<T, TM, Src, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update<T, TM, Src, Epi>, 256, smem) != cudaSuccess ||

@@ -223,6 +223,7 @@ tt_status apply_transport_impl(tt_context* ctx, const tt_plan* p, const tt_tenso
     src.bc_term[t] = (t < p->nbc) ? p->bc_term[t] : 0;
   }
   src.bcval = p->bcval;
+  src.nax = p->ndim;
   const long N = in->n[0];
   const int rcapo2 = (d == 3) ? out->rcap[2] : 1;
   k_transport_Z<S><<<1024, 256, 0, s>>>(N, src, in->rank, (S*)out->core[0], out->rcap[1], p->nbc,

@@ -172,6 +172,7 @@ static void fill_stencil(SrcStencil<S>& src, const tt_plan* p, const S* Z, int r
     src.bc_term[t] = (t < p->nbc) ? p->bc_term[t] : 0;
   }
   src.bcval = p->bcval;
+  src.nax = p->ndim;
 }
 
 // Launches the persistent update pass; *grid_out (if given) receives the number of CTAs, i.e.
@@ -180,12 +181,26 @@ template <typename T, class Src, class Epi>
 static tt_status launch_update(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows,
                                const double* W, int kcap, const Epi& epi, double* partials, long* grid_out) {
   constexpr int TM = UpdTM<T>::value;
-  const size_t smem = update_smem_bytes<T, TM, Src, Epi>(lp.ncap(), kcap);
+  // Staging the stencil rows takes shared memory: keep it when it costs no resident CTA or
+  // still leaves two per SM.
+  Src src2 = src;
+  set_staged(src2, 1);
+  size_t stage = update_stage_bytes(src2, TM);
+  if (stage > 0) {
+    const size_t s1 = update_smem_bytes<T, TM, Src, Epi>(lp.ncap(), kcap, stage);
+    const size_t s0 = update_smem_bytes<T, TM, Src, Epi>(lp.ncap(), kcap, 0);
+    const int o1 = (int)((228 * 1024) / (s1 + 1024)), o0 = (int)((228 * 1024) / (s0 + 1024));
+    if (s1 > 227 * 1024 || (o1 < o0 && o1 < 2)) {
+      set_staged(src2, 0);
+      stage = 0;
+    }
+  }
+  const size_t smem = update_smem_bytes<T, TM, Src, Epi>(lp.ncap(), kcap, stage);
   if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
-  const long grid = update_grid<T, TM, Src, Epi>(num_sms, lp.ncap(), kcap, nrows);
+  const long grid = update_grid<T, TM, Src, Epi>(num_sms, lp.ncap(), kcap, nrows, stage);
   if (grid_out) *grid_out = grid;
   TimerScope scope(kUpdate, s);
-  k_update<T, TM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials); count_launch();
+  k_update<T, TM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src2, lp, nrows, W, kcap, epi, partials); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 

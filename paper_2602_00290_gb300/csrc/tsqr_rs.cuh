@@ -47,6 +47,43 @@ __device__ __forceinline__ T group_sum(T v, unsigned gm) {
   return v;
 }
 
+// sum_i a[i] b[i] + init with four partial sums; FP32 on the packed two-lane FMA (__ffma2_rn)
+template <typename T, int N>
+__device__ __forceinline__ T dot4(const T* a, const T* b, T init) {
+  static_assert(N % 4 == 0, "multiple of 4");
+  if constexpr (sizeof(T) == 4) {
+    float2 p0 = make_float2(init, 0.f), p1 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+      p0 = __ffma2_rn(make_float2(a[i], a[i + 1]), make_float2(b[i], b[i + 1]), p0);
+      p1 = __ffma2_rn(make_float2(a[i + 2], a[i + 3]), make_float2(b[i + 2], b[i + 3]), p1);
+    }
+    return (p0.x + p0.y) + (p1.x + p1.y);
+  } else {
+    T p[4] = {init, T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i & 3] += a[i] * b[i];
+    return (p[0] + p[1]) + (p[2] + p[3]);
+  }
+}
+
+// B[i] -= w v[i]; FP32 on the packed two-lane FMA
+template <typename T, int N>
+__device__ __forceinline__ void axpy_neg(T w, const T* v, T* B) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 nw = make_float2(-w, -w);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const float2 u = __ffma2_rn(nw, make_float2(v[i], v[i + 1]), make_float2(B[i], B[i + 1]));
+      B[i] = u.x;
+      B[i + 1] = u.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) B[i] -= w * v[i];
+  }
+}
+
 // Absorb a block held as B (rows of this lane's segment, column c) into the packed R.
 // Reflectors jbeg..ncap-1; column j's reflector is formed by its group, lane 0 of the group
 // owning R[.][c]; one barrier per reflector.
@@ -63,10 +100,7 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
     if (!walk.next(lp, r)) continue;
     T* vb = vbuf + buf * (QS * SS);
     if (c == j) {
-      T xp[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) xp[i & 3] += B[i] * B[i];
-      const T x2 = group_sum<T, QS>((xp[0] + xp[1]) + (xp[2] + xp[3]), gm);
+      const T x2 = group_sum<T, QS>(dot4<T, RPT>(B, B, T(0)), gm);
       T tau = T(0);
       if (x2 > T(0)) {
         T sc = T(0);
@@ -103,14 +137,10 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
         v[i + 3] = t4[3];
       }
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
-      T wp[4] = {q == 0 ? *rjc : T(0), T(0), T(0), T(0)};
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) wp[i & 3] += v[i] * B[i];
-      T wv = group_sum<T, QS>((wp[0] + wp[1]) + (wp[2] + wp[3]), gm);
+      T wv = group_sum<T, QS>(dot4<T, RPT>(v, B, q == 0 ? *rjc : T(0)), gm);
       wv *= tau;
       if (q == 0) *rjc -= wv;
-#pragma unroll
-      for (int i = 0; i < RPT; ++i) B[i] -= wv * v[i];
+      axpy_neg<T, RPT>(wv, v, B);
     } else if (tau != T(0) && c > j && mycol) {
       const T* seg = vb + q * SS;
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
