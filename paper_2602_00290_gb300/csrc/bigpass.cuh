@@ -319,9 +319,81 @@ __device__ __forceinline__ void hh_absorb_x2(float* Rs, int ncap, float (&B)[BR]
   }
 }
 
+// FP64 form.  An FP64 warp instruction occupies the SM sub-partition's FP64 pipe for the same
+// time whether one lane or 32 are active, so the pivot thread's serial work (norm, scaling) is
+// moved off single-lane instructions: the pivot's warp takes the column's rows by shuffles (lane
+// l holds rows l, l + 32, ...) and sums their squares by a butterfly, and the reflector is
+// stored unscaled, u = [alpha - beta; B], with sc = 1/(alpha - beta) applied by the other
+// columns (H x = x - tau v (v^T x) with v = sc u).  Needs every lane of the pivot's warp present.
+template <int BR>
+__device__ __forceinline__ void hh_absorb_f64(double* Rs, int ncap, double (&B)[BR], double* vbuf, double* taub,
+                                              int& buf, int jbeg, const LivePattern& lp, int r, bool mycol) {
+  static_assert(BR % 32 == 0, "rows in whole warps");
+  const int c = threadIdx.x, lane = c & 31;
+  LiveWalk walk(lp, jbeg);
+  for (int j = jbeg; j < ncap; ++j) {
+    if (!walk.next(lp, r)) continue;
+    double* vb = vbuf + buf * BR;
+    if ((c >> 5) == (j >> 5)) {
+      const int jl = j & 31;
+      double part = 0.0;
+#pragma unroll
+      for (int h = 0; h < BR / 32; ++h) {
+        double mine = 0.0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const double t = __shfl_sync(0xffffffffu, B[32 * h + i], jl);
+          if (lane == i) mine = t;
+        }
+        part = fma(mine, mine, part);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (lane == jl) {
+        const double x2 = part;
+        double tau = 0.0, sc = 0.0;
+        if (x2 > 0.0) {
+          double* rjj = Rs + tri_off(j, ncap);
+          const double alpha = *rjj;
+          const double nrm = sqrt(alpha * alpha + x2);
+          const double beta = (alpha >= 0.0) ? -nrm : nrm;
+          sc = 1.0 / (alpha - beta);
+#pragma unroll
+          for (int i = 0; i < BR; i += 2) *reinterpret_cast<double2*>(vb + i) = make_double2(B[i], B[i + 1]);
+          tau = (beta - alpha) / beta;
+          *rjj = beta;
+#pragma unroll
+          for (int i = 0; i < BR; ++i) B[i] = 0.0;
+        }
+        taub[buf] = tau;
+        taub[2 + buf] = sc;
+      }
+    }
+    __syncthreads();
+    const double tau = taub[buf];
+    if (tau != 0.0 && c > j && mycol) {
+      const double sc = taub[2 + buf];
+      double* rjc = Rs + tri_off(j, ncap) + (c - j);
+      double wp[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int i = 0; i < BR; ++i) wp[i & 3] += vb[i] * B[i];
+      const double w = tau * fma(sc, (wp[0] + wp[1]) + (wp[2] + wp[3]), *rjc);
+      *rjc -= w;
+      const double ws = w * sc;
+#pragma unroll
+      for (int i = 0; i < BR; ++i) B[i] -= ws * vb[i];
+    }
+    buf ^= 1;
+  }
+}
+
 template <typename T, int BR>
 __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, T* taub, int& buf,
                                           int jbeg, const LivePattern& lp, int r, bool mycol) {
+  if constexpr (sizeof(T) == 8 && BR % 32 == 0) {
+    hh_absorb_f64<BR>(Rs, ncap, B, vbuf, taub, buf, jbeg, lp, r, mycol);
+    return;
+  }
   // the packed form measured faster for 64-row blocks (5.57 against 5.76 ms for the bench's
   // transport-sum leaf) and slower for 32-row blocks (5.51 against 5.39 ms)
   if constexpr (sizeof(T) == 4 && BR % 4 == 0 && BR > 32) {
