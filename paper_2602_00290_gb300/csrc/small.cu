@@ -686,15 +686,15 @@ __global__ void __launch_bounds__(256) k_coop_jacobi(int m, int n, double* __res
           sb = warp_sum(sb);
           sg = warp_sum(sg);
           if (tid == 0) {
+            // One lane forms the rotation, and an FP64 instruction with one active lane holds
+            // the FP64 pipe as long as a full warp: the test compares squares, and the angle is
+            // tan(theta) = sg sign(d) / (|d| + sqrt(d^2 + sg^2)) with d = (sb - sa) / 2, i.e.
+            // sign(zeta) / (|zeta| + sqrt(1 + zeta^2)) with zeta = d / sg, without forming zeta.
             double cs = 1.0, sn = 0.0, flag = 0.0;
-            if (fabs(sg) > floor_abs && fabs(sg) > rel_tol * sqrt(sa) * sqrt(sb)) {
-              const double zeta = (sb - sa) / (2.0 * sg);
-              double t;
-              if (fabs(zeta) > 1e150)
-                t = 0.5 / zeta;
-              else
-                t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-              cs = 1.0 / sqrt(1.0 + t * t);
+            if (fabs(sg) > floor_abs && sg * sg > rel_tol * rel_tol * sa * sb) {
+              const double d = 0.5 * (sb - sa);
+              const double t = (d >= 0.0 ? sg : -sg) / (fabs(d) + sqrt(fma(d, d, sg * sg)));
+              cs = rsqrt(fma(t, t, 1.0));
               sn = cs * t;
               flag = 1.0;
               atomicAdd(&ctrl->jac_rot[sweep], 1);

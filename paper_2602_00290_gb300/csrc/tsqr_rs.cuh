@@ -89,10 +89,114 @@ __device__ __forceinline__ void axpy_neg(T w, const T* v, T* B) {
 // owning R[.][c]; one barrier per reflector.
 // VREG: the lane's reflector segment is held in registers between the dot and the update
 // (else it is read from shared memory twice, which keeps long segments within 64 registers).
+// FP64 form (see hh_absorb_f64 in bigpass.cuh): the pivot's warp gathers the pivot column's
+// rows by shuffles (BR/32 per lane) and sums their squares with a butterfly, and the reflector is
+// stored unscaled, u = [alpha - beta; B], with sc = 1/(alpha - beta) applied by the other columns.
+template <int BR, int QS, bool VREG>
+__device__ __forceinline__ void hh_absorb_rs_f64(double* Rs, int ncap, double (&B)[BR / QS], double* vbuf,
+                                                 double* taub, int& buf, int jbeg, const LivePattern& lp, int r,
+                                                 bool mycol, int c, int q, unsigned gm) {
+  constexpr int RPT = RsGeom<double, BR, QS>::RPT, SS = RsGeom<double, BR, QS>::SS;
+  constexpr int GPW = 32 / QS;  // column groups per warp
+  static_assert(BR % 32 == 0, "rows in whole warps");
+  const int lane = threadIdx.x & 31;
+  LiveWalk walk(lp, jbeg);
+  for (int j = jbeg; j < ncap; ++j) {
+    if (!walk.next(lp, r)) continue;
+    double* vb = vbuf + buf * (QS * SS);
+    if ((int)(threadIdx.x >> 5) == (j * QS) >> 5) {
+      const int src0 = (j * QS) & 31;
+      double mine[BR / 32];
+#pragma unroll
+      for (int k = 0; k < BR / 32; ++k) mine[k] = 0.0;
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) {
+        const double t = __shfl_sync(0xffffffffu, B[i], src0 + (lane % QS));
+        if (lane / QS == i % GPW) mine[i / GPW] = t;
+      }
+      double part = 0.0;
+#pragma unroll
+      for (int k = 0; k < BR / 32; ++k) part = fma(mine[k], mine[k], part);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if (c == j) {
+        const double x2 = part;
+        if (x2 > 0.0) {
+          double* seg = vb + q * SS;
+#pragma unroll
+          for (int i = 0; i < RPT; i += 4) st4<double>(seg + i, B[i], B[i + 1], B[i + 2], B[i + 3]);
+#pragma unroll
+          for (int i = 0; i < RPT; ++i) B[i] = 0.0;
+        }
+        if (q == 0) {
+          double tau = 0.0, sc = 0.0;
+          if (x2 > 0.0) {
+            double* rjj = Rs + tri_off(j, ncap);
+            const double alpha = *rjj;
+            const double nrm = sqrt(alpha * alpha + x2);
+            const double beta = (alpha >= 0.0) ? -nrm : nrm;
+            sc = 1.0 / (alpha - beta);
+            tau = (beta - alpha) / beta;
+            *rjj = beta;
+          }
+          taub[buf] = tau;
+          taub[2 + buf] = sc;
+        }
+      }
+    }
+    __syncthreads();
+    const double tau = taub[buf];
+    if (tau != 0.0 && c > j && mycol) {
+      const double sc = taub[2 + buf];
+      const double* seg = vb + q * SS;
+      double* rjc = Rs + tri_off(j, ncap) + (c - j);
+      double v[VREG ? RPT : 4];
+      double d;
+      if constexpr (VREG) {
+#pragma unroll
+        for (int i = 0; i < RPT; i += 4) ld4(seg + i, *reinterpret_cast<double(*)[4]>(v + i));
+        d = dot4<double, RPT>(v, B, 0.0);
+      } else {
+        double wp[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int i = 0; i < RPT; i += 4) {
+          ld4(seg + i, *reinterpret_cast<double(*)[4]>(v));
+          wp[0] += v[0] * B[i];
+          wp[1] += v[1] * B[i + 1];
+          wp[2] += v[2] * B[i + 2];
+          wp[3] += v[3] * B[i + 3];
+        }
+        d = (wp[0] + wp[1]) + (wp[2] + wp[3]);
+      }
+      d = group_sum<double, QS>(d, gm);
+      const double w = tau * fma(sc, d, *rjc);
+      if (q == 0) *rjc -= w;
+      const double ws = w * sc;
+      if constexpr (VREG) {
+        axpy_neg<double, RPT>(ws, v, B);
+      } else {
+#pragma unroll
+        for (int i = 0; i < RPT; i += 4) {
+          ld4(seg + i, *reinterpret_cast<double(*)[4]>(v));
+          B[i] -= ws * v[0];
+          B[i + 1] -= ws * v[1];
+          B[i + 2] -= ws * v[2];
+          B[i + 3] -= ws * v[3];
+        }
+      }
+    }
+    buf ^= 1;
+  }
+}
+
 template <typename T, int BR, int QS, bool VREG = true>
 __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T* vbuf, T* taub, int& buf,
                                              int jbeg, const LivePattern& lp, int r, bool mycol, int c, int q,
                                              unsigned gm) {
+  if constexpr (sizeof(T) == 8 && BR % 32 == 0) {
+    hh_absorb_rs_f64<BR, QS, VREG>(Rs, ncap, B, vbuf, taub, buf, jbeg, lp, r, mycol, c, q, gm);
+    return;
+  }
   constexpr int RPT = RsGeom<T, BR, QS>::RPT, SS = RsGeom<T, BR, QS>::SS;
   const int lead = (threadIdx.x & 31) & ~(QS - 1);
   LiveWalk walk(lp, jbeg);
