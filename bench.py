@@ -30,8 +30,20 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # 152 SMs x 128 FP32 FMA/clk 
 # kernel): ncu captures of the same kernels on the 96 x 96 x 64-group workload (589,824 rows,
 # 595 leaves FP32 / 303 FP64), reads scaled by rows to 1,048,576 and writes (the leaves' R
 # factors) by leaves to the 608 / 304 of the full workload.
-LEAF_TRAFFIC = {("mixed", "column_dense"): 77.771264e6 * 1048576 / 589824 + 60.823296e6 * 608 / 595,
-                ("fp64", "column"): 202.651136e6 * 1048576 / 589824 + 5.878528e6 * 304 / 303}
+# (dram bytes read, written, leaves) of the transport-sum leaf kernel on the 96x96 workload
+# (589,824 rows), per kernel variant as it stands
+LEAF_TRAFFIC_MEDIUM = {("mixed", "column_dense"): (77.771264e6, 60.823296e6, 595),
+                       ("mixed", "column"): (77.175296e6, 28.29184e6, 439),
+                       ("fp64", "column"): (205.33376e6, 5.611264e6, 303)}
+
+
+def leaf_traffic(precision, variant, leaves, nrows=1048576):
+    """Bytes per launch at nrows: reads scaled by rows, writes (the leaves' R factors) by leaves."""
+    t = LEAF_TRAFFIC_MEDIUM.get((precision, variant))
+    if t is None:
+        return None
+    rd, wr, lm = t
+    return rd * nrows / 589824 + wr * leaves / lm
 LEAF_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the leaf kernel on the 96x96 "
                        "workload; reads scaled by rows, writes by leaves to 128x128")
 
@@ -266,8 +278,9 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     variant = tune["transport"][0] if tune is not None else "column"
     kname = {"column": "k_tsqr_leaf", "rowsplit": "k_tsqr_leaf_rs",
              "column_dense": "k_tsqr_leaf (32-row blocks, 4 CTAs/SM)"}[variant]
-    # ncu traffic was taken on the column-owner kernel; another kernel has no counters yet
-    traffic = LEAF_TRAFFIC.get((precision, variant)) if args.size == "full" else None
+    # ncu traffic exists for the leaf variants in LEAF_TRAFFIC_MEDIUM; another kernel has none yet
+    leaves = int(tune["transport"][1]) if tune is not None else None
+    traffic = leaf_traffic(precision, variant, leaves) if (args.size == "full" and leaves) else None
     out["roofline"] = {"kernel": kname + " over the transport sum (one launch per step, R1 = 5r columns)",
                        "bound": bound, "achieved": leaf_tf, "peak": peak, "unit": "TFLOP/s",
                        "frac": (leaf_tf / peak) if leaf_tf else None,
