@@ -135,6 +135,20 @@ def blob_density(nx: int, ny: int, seed: int, nblob: int = 8, contrast: float = 
     return rho.reshape(-1)
 
 
+def blob_density3(nx: int, ny: int, nz: int, seed: int, nblob: int = 8, contrast: float = 100.0) -> np.ndarray:
+    """3-D counterpart of blob_density on [0,1]^3 cell centres, x fastest: rho[ix + nx*(iy + ny*iz)]."""
+    rng = np.random.default_rng(seed)
+    cb = rng.uniform(0.1, 0.9, size=(nblob, 3))
+    wb = rng.uniform(0.05, 0.15, size=nblob)
+    xc, yc, zc = [(np.arange(n) + 0.5) / n for n in (nx, ny, nz)]
+    Z, Y, X = np.meshgrid(zc, yc, xc, indexing="ij")  # shape (nz, ny, nx)
+    s = np.zeros_like(X)
+    for b in range(nblob):
+        s += np.exp(-((X - cb[b, 0]) ** 2 + (Y - cb[b, 1]) ** 2 + (Z - cb[b, 2]) ** 2) / (2.0 * wb[b] ** 2))
+    rho = 1.0 + (contrast - 1.0) * np.minimum(1.0, s)
+    return rho.reshape(-1)
+
+
 def linear_temperature(nx: int, ny: int = 1, nz: int = 1, t0: float = 1.0, t1: float = 0.1) -> np.ndarray:
     """T linear in x over cell centres from t0 to t1, constant in y and z."""
     xc = (np.arange(nx) + 0.5) / nx
@@ -179,6 +193,24 @@ def plane_config1(nx: int = 128, ny: int = 128, G: int = 64, ntheta: int = 16, n
         name=f"plane2d_{nx}x{ny}_g{G}_{ntheta}x{nphi}_r{rmax}", ndim=2, nx=nx, ny=ny, nz=1,
         ngroup=G, quad="latlong_midpoint", ntheta=ntheta, nphi=nphi, extent=(1.0, 1.0, 1.0),
         c=1.0, dt=cfl * dx, group_edges=edges, temperature=linear_temperature(nx, ny),
+        rho_kappa_a=ka, rho_kappa_s=0.1 * ka, tol=tol, rmax=rmax, steps=steps, seed=seed)
+
+
+def cube_config(nx: int = 6, ny: int = 5, nz: int = 4, G: int = 3, ntheta: int = 4, nphi: int = 8,
+                rmax: int = 8, tol: float = 1e-6, steps: int = 4, seed: int = 5, cfl: float = 0.3) -> Workload:
+    """3-D (x,y,z) on [0,1]^3: the plane workload's recipe in three dimensions (Gaussian-blob
+    density, kappa_s = 0.1 kappa_a, T linear in x 1 -> 0.1), vacuum, lat/long ordinates; the
+    time step dt = cfl * min(dx) keeps the forward-Euler transport step stable (sum over axes of
+    lambda_a <= 3 cfl)."""
+    edges = group_edges(G)
+    lf = line_factors(G, seed=seed + 1000)
+    rho = blob_density3(nx, ny, nz, seed=seed)
+    ka = opacity_rows(rho, edges, lf)
+    h = min(1.0 / nx, 1.0 / ny, 1.0 / nz)
+    return Workload(
+        name=f"cube3d_{nx}x{ny}x{nz}_g{G}_{ntheta}x{nphi}_r{rmax}", ndim=3, nx=nx, ny=ny, nz=nz,
+        ngroup=G, quad="latlong_midpoint", ntheta=ntheta, nphi=nphi, extent=(1.0, 1.0, 1.0),
+        c=1.0, dt=cfl * h, group_edges=edges, temperature=linear_temperature(nx, ny, nz),
         rho_kappa_a=ka, rho_kappa_s=0.1 * ka, tol=tol, rmax=rmax, steps=steps, seed=seed)
 
 
