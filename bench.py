@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gram", action="store_true", help="skip the FP64 leg with Gram rounding")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="step eagerly instead of replaying the captured step graph")
+    ap.add_argument("--breakdown-steps", type=int, default=3,
+                    help="instrumented steps (eager, CUDA events per kernel phase) after the timed ones")
     ap.add_argument("--no-autotune", action="store_true",
                     help="time the default TSQR kernels instead of the autotuned choice (tt_autotune)")
     ap.add_argument("--tsqr", default="",
@@ -212,6 +216,7 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
             ctx.set_tsqr(precision, ncaps[role], variant, int(leaves))
             pinned[role] = ctx.get_tsqr(precision, ncaps[role])
         pinned["pinned"] = True
+    ctx.set_graphs(not args.no_graphs)
     for _ in range(args.warmup):
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
     ctx.sync()
@@ -219,12 +224,14 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     if tune is None and rounding == "tsqr" and not args.no_autotune:
         # TSQR kernels and leaf counts for this state's shape, timed on a copy of it
         tune = ctx.autotune(plan, x, wl.tol, wl.rmax, precision, steps=2)
+        # one more untimed step, which captures the step graph for the tuned kernels
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
+        ctx.sync()
     ranks = [x.ranks()]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     clocks = Clocks(clocks_index)
     ctx.counters(reset=True)
     ctx.diagnostics(reset=True)
-    ctx.set_timing(True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     rank_hist = torch.zeros(args.steps, 4, dtype=torch.int32, device="cuda")
     if dist:
@@ -240,10 +247,22 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     if dist:
         dist.barrier()
     ctx.sync()
-    ctx.set_timing(False)
-    kms, klaunch = ctx.counters(reset=True)
+    _, klaunch = ctx.counters(reset=True)
     diag = ctx.diagnostics(reset=True)
     clk = clocks.stop()
+    # per-phase kernel times: a few more steps, eager, with CUDA events around each kernel phase
+    # (the timed steps above replay the step graph, which carries no per-phase events)
+    nb = max(1, args.breakdown_steps)
+    b_ranks = [x.ranks()]
+    ctx.set_timing(True)
+    for _ in range(nb):
+        flush.zero_()
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
+        b_ranks.append(x.ranks())
+    ctx.sync()
+    ctx.set_timing(False)
+    kms, _ = ctx.counters(reset=True)
+    ctx.diagnostics(reset=True)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     if dist:
@@ -258,12 +277,14 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     for i in range(args.steps):
         rb, ra = r_seq[i][1], r_seq[i + 1][1]
         flops += counted_flops(N, rb, ra, ra)
-        R1 = 5 * rb  # transport-sum columns (Z and its 4 upwind images; vacuum: no inflow columns)
+    for i in range(nb):
+        R1 = 5 * b_ranks[i][1]  # transport-sum columns (Z and its 4 upwind images; vacuum: no inflow columns)
         leaf_flops += 2.0 * N * R1 * R1
     ws = dist.get_world_size() if dist else 1
     out = {"value": ws * args.steps / (total_ms / 1e3), "ms_per_step": total_ms / args.steps,
            "tflops": flops / (total_ms / 1e3) / 1e12,
-           "breakdown_ms_per_step": {k: v / args.steps for k, v in kms.items()},
+           "breakdown_ms_per_step": {k: v / nb for k, v in kms.items()},
+           "breakdown_steps": nb, "step_graphs": not args.no_graphs,
            "gpu_launches": int(sum(klaunch.values())), "clocks": clk, "ranks": r_seq[-1],
            "rank_history": [r[1:-1] for r in r_seq], "jacobi": diag}
     if tune is not None:
@@ -286,7 +307,7 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
                        "frac": (leaf_tf / peak) if leaf_tf else None,
                        "traffic": traffic, "traffic_unit": "bytes per launch" if traffic else None,
                        "traffic_source": LEAF_TRAFFIC_SOURCE if traffic else None,
-                       "peak_source": src, "share": kms["tsqr_leaf"] / total_ms if total_ms else None}
+                       "peak_source": src, "share": (kms["tsqr_leaf"] / nb) / (total_ms / args.steps) if total_ms else None}
     ctx.set_rounding("tsqr")
     return out, x, energy
 
@@ -338,10 +359,11 @@ def run_ours(args):
                                      if head == "mixed" else "fp64"),
                        "state_dtype": "f32" if head == "mixed" else "f64",
                        "l2": "flushed between timed steps (256 MB write)",
+                       "step": ("replay of the captured step graph" if R["step_graphs"] else "eager launches"),
                        "parallelism": "replicas" if ws > 1 else "single"},
             "tflops": R["tflops"], "roofline": R["roofline"],
-            "breakdown_ms_per_step": R["breakdown_ms_per_step"], "gpu_launches": R["gpu_launches"],
-            "clocks": R["clocks"], "ranks": R["ranks"], "rank_history": R["rank_history"],
+            "breakdown_ms_per_step": R["breakdown_ms_per_step"], "breakdown_steps": R["breakdown_steps"],
+            "gpu_launches": R["gpu_launches"], "clocks": R["clocks"], "ranks": R["ranks"], "rank_history": R["rank_history"],
             "jacobi": R["jacobi"]}
     if "tsqr_autotune" in R:
         line["tsqr_autotune"] = R["tsqr_autotune"]
@@ -405,6 +427,9 @@ def run_ours(args):
         d2h = h2d + host_energy.numel() * 8
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        # untimed: captures the step graph for this energy buffer (each timed step starts from
+        # the host copy of the state)
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, head, energy)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.e2e_steps):

@@ -150,6 +150,19 @@ typedef enum {
 #define TT_TIMER_COUNT 6
 tt_status tt_context_set_timing(tt_context *ctx, int enable);
 
+/* Replay tt_step as a CUDA graph (enable != 0; default off).  With it on, tt_step captures its
+ * launch sequence the first time it runs for a given key (plan; state pointers, rank capacities
+ * and dtype; tol, rmax, precision, energy_dev; the context's workspace, rounding method, sketch
+ * and TSQR kernel table) and replays that graph, on the context's stream, while the key stays
+ * the same; a new key drops the old graph and captures again.  Device data (ranks, cores, plan
+ * arrays) may change freely between replays: the host reads none of it.  The capture runs on a
+ * private stream, so the context's stream may be the legacy default stream; tt_step called
+ * while the context's stream is itself being captured runs eagerly (it then becomes part of
+ * the caller's graph).  With kernel timing on (tt_context_set_timing), or when a step cannot be
+ * captured, tt_step runs eagerly with the same results.  Launch counters count each replay's
+ * kernels.  Turning it off releases the graph.  Errors: TT_ERR_ARG (ctx NULL). */
+tt_status tt_context_set_graphs(tt_context *ctx, int enable);
+
 /* Select the rounding method of the context (TT_ERR_ARG for an unknown method).  With
  * TT_ROUND_GRAM the TT_TIMER_TSQR_LEAF(_SOURCE) categories time the Gram pass instead; with
  * TT_ROUND_RANDOMIZED they time the TSQR of the sketch (the sketch itself is an update pass). */

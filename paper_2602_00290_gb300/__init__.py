@@ -35,7 +35,7 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
            "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding",
            "tt_internal_ranks", "tt_context_set_sketch", "tt_context_set_tsqr", "tt_context_get_tsqr",
-           "tt_autotune")
+           "tt_autotune", "tt_context_set_graphs")
 TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2}
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
@@ -96,6 +96,7 @@ def lib():
             "tt_step": [vp, vp, ctypes.POINTER(_Tensor), dbl, i32, ctypes.c_int, vp],
             "tt_energy_density": [vp, vp, ctypes.POINTER(_Tensor), vp],
             "tt_context_set_timing": [vp, ctypes.c_int],
+            "tt_context_set_graphs": [vp, ctypes.c_int],
             "tt_context_counters": [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64), ctypes.c_int],
             "tt_context_diagnostics": [vp, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int],
             "tt_dot_noalloc": [vp, ctypes.POINTER(_Tensor), ctypes.POINTER(_Tensor), vp],
@@ -168,6 +169,10 @@ class Context:
         self._sketch = om
         _check(lib().tt_context_set_sketch(self.handle, ctypes.c_void_p(om.data_ptr()), int(om.shape[0]),
                                            int(om.shape[1])), "tt_context_set_sketch")
+
+    def set_graphs(self, enable: bool = True):
+        """tt_step replays a captured CUDA graph of the step while its arguments stay the same."""
+        _check(lib().tt_context_set_graphs(self.handle, 1 if enable else 0), "tt_context_set_graphs")
 
     def set_rounding(self, method: str):
         """"tsqr" (Householder TSQR, default), "gram" (Gram matrix + pivoted-Cholesky root) or

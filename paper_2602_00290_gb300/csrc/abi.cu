@@ -80,6 +80,77 @@ tt_status with_ws(tt_context* ctx, F&& fn) {
 
 int set_device(tt_context* ctx) { return cudaSetDevice(ctx->device) == cudaSuccess; }
 
+// A captured tt_step and everything its launch sequence depends on: the plan, the state's
+// pointers and capacities, the step arguments, the workspace and the context settings that
+// choose kernels.  Device data (ranks, cores, plan arrays, material temperature) may change
+// between replays; none of it is read by the host.
+struct StepGraph {
+  const tt_plan* plan = nullptr;
+  int d = 0;
+  tt_dtype dtype = TT_F64;
+  void* core[TT_MAX_CORES] = {};
+  int32_t* rank = nullptr;
+  int32_t rcap[TT_MAX_CORES + 1] = {};
+  double tol = 0.0;
+  int32_t rmax = 0;
+  tt_precision prec = TT_PREC_FP64;
+  double* energy = nullptr;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int rounding = 0, sketch_nang = 0, sketch_ell = 0, coop_grid_max = 0, tsqr_leaf_cap = 0;
+  const double* sketch = nullptr;
+  unsigned long tune_epoch = 0;
+  // result of the capture
+  cudaGraphExec_t exec = nullptr;
+  bool failed = false;  // the step could not be captured: run it eagerly
+  long launches[ttk::kNumCat] = {};
+
+  static StepGraph of(const tt_context* ctx, const tt_plan* plan, const tt_tensor* I, double tol, int32_t rmax,
+                      tt_precision prec, double* energy) {
+    StepGraph g;
+    g.plan = plan;
+    g.d = I->d;
+    g.dtype = I->dtype;
+    for (int j = 0; j < TT_MAX_CORES; ++j) g.core[j] = (j < I->d) ? I->core[j] : nullptr;
+    g.rank = I->rank;
+    for (int j = 0; j <= TT_MAX_CORES; ++j) g.rcap[j] = (j <= I->d) ? I->rcap[j] : 0;
+    g.tol = tol;
+    g.rmax = rmax;
+    g.prec = prec;
+    g.energy = energy;
+    g.ws = ctx->ws;
+    g.ws_bytes = ctx->ws_bytes;
+    g.rounding = ctx->rounding;
+    g.sketch = ctx->sketch;
+    g.sketch_nang = ctx->sketch_nang;
+    g.sketch_ell = ctx->sketch_ell;
+    g.coop_grid_max = ctx->coop_grid_max;
+    g.tsqr_leaf_cap = ctx->tsqr_leaf_cap;
+    g.tune_epoch = ttk::tune_of(ctx)->epoch;
+    return g;
+  }
+  bool same(const StepGraph& o) const {
+    if (plan != o.plan || d != o.d || dtype != o.dtype || rank != o.rank || tol != o.tol || rmax != o.rmax ||
+        prec != o.prec || energy != o.energy || ws != o.ws || ws_bytes != o.ws_bytes || rounding != o.rounding ||
+        sketch != o.sketch || sketch_nang != o.sketch_nang || sketch_ell != o.sketch_ell ||
+        coop_grid_max != o.coop_grid_max || tsqr_leaf_cap != o.tsqr_leaf_cap || tune_epoch != o.tune_epoch)
+      return false;
+    for (int j = 0; j < TT_MAX_CORES; ++j)
+      if (core[j] != o.core[j]) return false;
+    for (int j = 0; j <= TT_MAX_CORES; ++j)
+      if (rcap[j] != o.rcap[j]) return false;
+    return true;
+  }
+};
+
+void drop_step_graph(tt_context* ctx) {
+  StepGraph* g = static_cast<StepGraph*>(ctx->step_graph);
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
+  ctx->step_graph = nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -116,6 +187,8 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->sketch_nang = 0;
   ctx->sketch_ell = 0;
   ctx->tune = new ttk::TsqrTune();
+  ctx->graphs = 0;
+  ctx->step_graph = nullptr;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
@@ -153,7 +226,19 @@ tt_status tt_context_destroy(tt_context* ctx) {
   for (cudaEvent_t e : in->pool) cudaEventDestroy(e);
   delete in;
   delete ttk::tune_of(ctx);
+  drop_step_graph(ctx);
   delete ctx;
+  return TT_OK;
+}
+
+tt_status tt_context_set_graphs(tt_context* ctx, int enable) {
+  if (!ctx) return TT_ERR_ARG;
+  set_device(ctx);
+  ctx->graphs = (enable != 0);
+  if (!ctx->graphs) {
+    cudaStreamSynchronize(ctx->stream);
+    drop_step_graph(ctx);
+  }
   return TT_OK;
 }
 
@@ -357,13 +442,72 @@ tt_status tt_step(tt_context* ctx, const tt_plan* plan, tt_tensor* I, double tol
   if (st == TT_OK) st = check_round_args(I, tol, rmax, prec);
   if (st != TT_OK) return st;
   set_device(ctx);
-  return with_ws(ctx, [&](ttk::Bump& ws) {
+  auto body = [&](ttk::Bump& ws) {
     const bool f64 = (I->dtype == TT_F64), mixed = (prec == TT_PREC_MIXED);
     if (f64) return mixed ? ttk::step_impl<double, float>(ctx, plan, I, tol, rmax, energy_dev, ws)
                           : ttk::step_impl<double, double>(ctx, plan, I, tol, rmax, energy_dev, ws);
     return mixed ? ttk::step_impl<float, float>(ctx, plan, I, tol, rmax, energy_dev, ws)
                  : ttk::step_impl<float, double>(ctx, plan, I, tol, rmax, energy_dev, ws);
-  });
+  };
+  ttk::Instr* in = static_cast<ttk::Instr*>(ctx->instr);
+  if (!ctx->graphs || (in && in->timing) || capturing(ctx->stream)) return with_ws(ctx, body);
+  // Graph replay: size the workspace outside any capture, then replay the step captured for
+  // the same key, or capture it now (the capture runs no kernel; launching the graph does).
+  {
+    InstrGuard guard(ctx);
+    ttk::Bump dry{nullptr, 0, 0, true};
+    st = body(dry);
+    if (st != TT_OK) return st;
+    st = ensure_ws(ctx, dry.off);
+    if (st != TT_OK) return st;
+  }
+  const StepGraph key = StepGraph::of(ctx, plan, I, tol, rmax, prec, energy_dev);
+  StepGraph* g = static_cast<StepGraph*>(ctx->step_graph);
+  if (!g || !g->same(key)) {
+    drop_step_graph(ctx);
+    g = new StepGraph(key);
+    ctx->step_graph = g;
+    long before[ttk::kNumCat] = {};
+    if (in)
+      for (int c = 0; c < ttk::kNumCat; ++c) before[c] = in->launches[c];
+    // capture on a private stream (the context's may be the legacy default stream, which
+    // cannot be captured); the graph is launched on the context's stream
+    cudaGraph_t graph = nullptr;
+    tt_status cst = TT_ERR_CUDA;
+    cudaStream_t own = ctx->stream, cap = nullptr;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess) {
+      ctx->stream = cap;
+      if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        {
+          InstrGuard guard(ctx);
+          ttk::Bump real{static_cast<char*>(ctx->ws), 0, ctx->ws_bytes, false};
+          cst = body(real);
+        }
+        if (cudaStreamEndCapture(cap, &graph) != cudaSuccess) cst = TT_ERR_CUDA;
+      }
+      ctx->stream = own;
+      cudaStreamDestroy(cap);
+    }
+    if (cst == TT_OK && graph && cudaGraphInstantiate(&g->exec, graph, 0) != cudaSuccess) {
+      g->exec = nullptr;
+      cst = TT_ERR_CUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (in)
+      for (int c = 0; c < ttk::kNumCat; ++c) {
+        g->launches[c] = in->launches[c] - before[c];
+        in->launches[c] = before[c];  // counted again below, per launch of the step
+      }
+    if (cst != TT_OK || !g->exec) {
+      (void)cudaGetLastError();  // the refused capture leaves nothing behind; run the step eagerly
+      g->failed = true;
+    }
+  }
+  if (g->failed) return with_ws(ctx, body);
+  if (cudaGraphLaunch(g->exec, ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
+  if (in)
+    for (int c = 0; c < ttk::kNumCat; ++c) in->launches[c] += g->launches[c];
+  return TT_OK;
 }
 
 tt_status tt_internal_ranks(tt_context* ctx, const tt_plan* plan, const tt_tensor* x, double delta_rel,

@@ -102,6 +102,8 @@ struct tt_context {
   const double* sketch;  // randomized rounding: omega (sketch_nang x sketch_ell, device, caller-owned)
   int sketch_nang, sketch_ell;
   void* tune;  // ttk::TsqrTune, TSQR kernel choice per shape (owned; batch views share it)
+  int graphs;        // tt_step replays a captured CUDA graph of the step (tt_context_set_graphs)
+  void* step_graph;  // the captured step and what it depends on (owned; not shared by batch views)
 };
 
 struct tt_plan {

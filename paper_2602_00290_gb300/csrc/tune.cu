@@ -51,10 +51,12 @@ tt_status tt_context_set_tsqr(tt_context* ctx, tt_precision prec, int32_t ncap, 
   ttk::TsqrTune* tab = ttk::tune_of(ctx);
   if (ncap <= 0) {
     tab->m.clear();
+    ++tab->epoch;
     return TT_OK;
   }
   if (variant < 0 || variant >= ttk::kTsqrVariants) return TT_ERR_ARG;
   tab->m[ttk::TsqrTune::key(esize_of(prec), ncap)] = ttk::TsqrCfg{variant, leaves > 0 ? leaves : 0};
+  ++tab->epoch;
   return TT_OK;
 }
 
@@ -133,16 +135,19 @@ tt_status tt_autotune(tt_context* ctx, const tt_plan* plan, const tt_tensor* I, 
   float base = 0.0f, best = 0.0f;
   int pick[2][2] = {{ttk::kTsqrColumn, wave}, {ttk::kTsqrColumn, wave}};
   for (int role = 0; role < 2; ++role) tab->m.erase(ttk::TsqrTune::key(es, ncaps[role]));
+  ++tab->epoch;
   st = trial(&base);
   best = base;
   for (int role = 0; st == TT_OK && role < 2; ++role) {
     const long key = ttk::TsqrTune::key(es, ncaps[role]);
     for (int v = 0; st == TT_OK && v < ttk::kTsqrVariants; ++v) {
       tab->m[key] = ttk::TsqrCfg{v, wave};
+      ++tab->epoch;
       if (ttk::resolve_tsqr(ctx, es, ncaps[role], wave).variant != v) continue;  // shape not taken by v
       for (int l : leaf_opts(v)) {
         if (v == ttk::kTsqrColumn && l == wave) continue;  // the default, timed as `base`
         tab->m[key] = ttk::TsqrCfg{v, l};
+        ++tab->epoch;
         float t = 0.0f;
         st = trial(&t);
         if (st != TT_OK) break;
@@ -154,6 +159,7 @@ tt_status tt_autotune(tt_context* ctx, const tt_plan* plan, const tt_tensor* I, 
       }
     }
     tab->m[key] = ttk::TsqrCfg{pick[role][0], pick[role][1]};
+    ++tab->epoch;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

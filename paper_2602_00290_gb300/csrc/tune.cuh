@@ -24,6 +24,7 @@ struct TsqrCfg {
 
 struct TsqrTune {
   std::map<long, TsqrCfg> m;
+  unsigned long epoch = 0;  // advanced on every change of m (a captured step depends on m)
   static long key(int esize, int ncap) { return (long)esize * 1000000L + ncap; }
   bool find(int esize, int ncap, TsqrCfg* out) const {
     auto it = m.find(key(esize, ncap));
