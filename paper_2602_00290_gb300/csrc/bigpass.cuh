@@ -702,6 +702,67 @@ __host__ __device__ inline size_t update_smem_bytes(int ncap, int kcap, size_t s
   return b + sizeof(double) * (3 * TM) + sizeof(T) * (size_t)kpad + sizeof(unsigned) * TM + (size_t)ncap;
 }
 
+// Epilogue of one output tile (Os: TM x kpad in arithmetic T): (a) one warp per row for
+// J* = o . vJ, (b) one thread per row for the row scalars (FP64), (c) coalesced writes of the
+// output rows.  e0t/e1t accumulate this thread's energy partials.
+template <typename T, int TM, class Epi>
+__device__ __forceinline__ void update_epilogue(const Epi& epi, const T* Os, int kpad, int kcap, const T* vJs,
+                                                bool dot, double* rowv, long row0, long nrows, double& e0t,
+                                                double& e1t) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
+  if (dot) {
+    for (int mm = warp; mm < TM; mm += nwarps) {
+      const T* o = Os + (size_t)mm * kpad;
+      T js = T(0);
+      for (int j = lane; j < kcap; j += 32) js += o[j] * vJs[j];
+      js = warp_sum(js);
+      if (lane == 0) rowv[2 * TM + mm] = (double)js;
+    }
+    __syncthreads();
+  }
+  for (int m = tid; m < TM; m += blockDim.x) {
+    const long k = row0 + m;
+    double sc = 0.0, ex = 0.0, e0 = 0.0, e1 = 0.0;
+    if (k < nrows) epi.prep(k, dot ? rowv[2 * TM + m] : 0.0, sc, ex, e0, e1);
+    rowv[m] = sc;
+    rowv[TM + m] = ex;
+    e0t += e0;
+    e1t += e1;
+  }
+  __syncthreads();
+  const int width = kcap + (Epi::kExtra ? 1 : 0);
+  for (int mm = warp; mm < TM; mm += nwarps) {
+    const long k = row0 + mm;
+    if (k >= nrows) break;
+    const T* o = Os + (size_t)mm * kpad;
+    const T sc = (T)rowv[mm];
+    const double ex = rowv[TM + mm];
+    for (int j = lane; j < width; j += 32) {
+      if (j < kcap) epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))(sc * o[j]);
+      else epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))ex;
+    }
+  }
+}
+
+// Fixed-order reduction of the threads' energy partials into partials[2 cta + {0, 1}] (red:
+// 2 blockDim doubles of shared memory that are free by now).
+__device__ __forceinline__ void update_partials(double* red, double e0t, double e1t, double* partials) {
+  const int tid = threadIdx.x;
+  __syncthreads();
+  red[2 * tid] = e0t;
+  red[2 * tid + 1] = e1t;
+  __syncthreads();
+  if (tid == 0) {
+    double s0 = 0.0, s1 = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      s0 += red[2 * t];
+      s1 += red[2 * t + 1];
+    }
+    partials[2 * (size_t)blockIdx.x] = s0;
+    partials[2 * (size_t)blockIdx.x + 1] = s1;
+  }
+}
+
 // Issue the cp.async copies of a tile's stencil row blocks (a no-op for other sources).
 template <int TM, class Src, typename T>
 __device__ __forceinline__ void stage_rows(const Src&, long, long, T*, int) {}
@@ -763,7 +824,7 @@ __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nr
   T* vJs = reinterpret_cast<T*>(rowv + 3 * TM);               // [kpad] vJ in arithmetic T
   unsigned* fl = reinterpret_cast<unsigned*>(vJs + kpad);
   unsigned char* livec = reinterpret_cast<unsigned char*>(fl + TM);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = (int)(blockDim.x >> 5);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double* vJ = epi_vj(epi);
   for (int c = tid; c < ncap; c += blockDim.x) {
     cols[c] = src.col(c);
@@ -854,57 +915,9 @@ __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nr
       }
     }
     __syncthreads();
-    // epilogue: (a) one warp per row for J* = o . vJ in arithmetic T, (b) one thread per row
-    // for the row scalars (FP64), (c) coalesced writes of the output rows
-    if (vJ) {
-      for (int mm = warp; mm < TM; mm += nwarps) {
-        const T* o = Os + (size_t)mm * kpad;
-        T js = T(0);
-        for (int j = lane; j < kcap; j += 32) js += o[j] * vJs[j];
-        js = warp_sum(js);
-        if (lane == 0) rowv[2 * TM + mm] = (double)js;
-      }
-      __syncthreads();
-    }
-    for (int m = tid; m < TM; m += blockDim.x) {
-      const long k = row0 + m;
-      double sc = 0.0, ex = 0.0, e0 = 0.0, e1 = 0.0;
-      if (k < nrows) epi.prep(k, vJ ? rowv[2 * TM + m] : 0.0, sc, ex, e0, e1);
-      rowv[m] = sc;
-      rowv[TM + m] = ex;
-      e0t += e0;
-      e1t += e1;
-    }
-    __syncthreads();
-    const int width = kcap + (Epi::kExtra ? 1 : 0);
-    for (int mm = warp; mm < TM; mm += nwarps) {
-      const long k = row0 + mm;
-      if (k >= nrows) break;
-      const T* o = Os + (size_t)mm * kpad;
-      const T sc = (T)rowv[mm];
-      const double ex = rowv[TM + mm];
-      for (int j = lane; j < width; j += 32) {
-        if (j < kcap) epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))(sc * o[j]);
-        else epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))ex;
-      }
-    }
+    update_epilogue<T, TM>(epi, Os, kpad, kcap, vJs, vJ != nullptr, rowv, row0, nrows, e0t, e1t);
   }
-  if (partials) {
-    // fixed-order reduction of the per-thread partials
-    __syncthreads();
-    red[2 * tid] = e0t;
-    red[2 * tid + 1] = e1t;
-    __syncthreads();
-    if (tid == 0) {
-      double s0 = 0.0, s1 = 0.0;
-      for (int t = 0; t < (int)blockDim.x; ++t) {
-        s0 += red[2 * t];
-        s1 += red[2 * t + 1];
-      }
-      partials[2 * (size_t)blockIdx.x] = s0;
-      partials[2 * (size_t)blockIdx.x + 1] = s1;
-    }
-  }
+  if (partials) update_partials(red, e0t, e1t, partials);
 }
 
 // Persistent grid of the update pass (also the number of energy partials it writes).
@@ -925,3 +938,5 @@ inline long update_grid(int num_sms, int ncap, int kcap, long nrows, size_t stag
 
 // the row-split kernels and the merge tree
 #include "tsqr_rs.cuh"
+// the update pass over staged row blocks of the stencil sum
+#include "update_blk.cuh"

@@ -177,10 +177,48 @@ static void fill_stencil(SrcStencil<S>& src, const tt_plan* p, const S* Z, int r
 
 // Launches the persistent update pass; *grid_out (if given) receives the number of CTAs, i.e.
 // of energy partial pairs written.
+template <class Src>
+struct StencilOf {
+  static constexpr bool value = false;
+};
+template <typename S>
+struct StencilOf<SrcStencil<S>> {
+  static constexpr bool value = true;
+};
+
+// FP32 passes over the stencil sum run from staged row blocks with combined weights
+// (k_update_blk) when the rows can be staged (16-byte granules) and the tile fits; returns
+// TT_ERR_UNSUPPORTED (nothing launched) otherwise.
+template <class Epi, typename S>
+static tt_status launch_update_blk(cudaStream_t s, int num_sms, const SrcStencil<S>& src, LivePattern lp,
+                                   long nrows, const double* W, int kcap, const Epi& epi, double* partials,
+                                   long* grid_out) {
+  constexpr int TM = UpdTM<float>::value;
+  if (((size_t)src.ldz * sizeof(S)) % 16 != 0 || ((size_t)src.Z % 16) != 0 || src.nax < 1 || src.rcap != lp.rcap)
+    return TT_ERR_UNSUPPORTED;
+  const size_t smem = update_blk_smem_bytes<TM, S>(src, update_kpad<Epi>(kcap), lp.nextra);
+  if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
+  auto kern = k_update_blk<TM, S, Epi>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess || occ < 1) occ = 1;
+  const long ntiles = (nrows + TM - 1) / TM;
+  long grid = (long)num_sms * occ;
+  if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
+  if (grid_out) *grid_out = grid;
+  TimerScope scope(kUpdate, s);
+  kern<<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials); count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
 template <typename T, class Src, class Epi>
 static tt_status launch_update(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows,
                                const double* W, int kcap, const Epi& epi, double* partials, long* grid_out) {
   constexpr int TM = UpdTM<T>::value;
+  if constexpr (sizeof(T) == 4 && StencilOf<Src>::value) {
+    const tt_status bst = launch_update_blk(s, num_sms, src, lp, nrows, W, kcap, epi, partials, grid_out);
+    if (bst != TT_ERR_UNSUPPORTED) return bst;
+  }
   // Staging the stencil rows takes shared memory: keep it when it costs no resident CTA or
   // still leaves two per SM.
   Src src2 = src;
