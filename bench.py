@@ -224,9 +224,10 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     if tune is None and rounding == "tsqr" and not args.no_autotune:
         # TSQR kernels and leaf counts for this state's shape, timed on a copy of it
         tune = ctx.autotune(plan, x, wl.tol, wl.rmax, precision, steps=2)
-        # one more untimed step, which captures the step graph for the tuned kernels
-        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
-        ctx.sync()
+    # one more untimed step in every leg (the legs' states stay step for step comparable), which
+    # captures the step graph for the kernels in force
+    tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, precision, energy)
+    ctx.sync()
     ranks = [x.ranks()]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     clocks = Clocks(clocks_index)
