@@ -161,6 +161,25 @@ def oracle_steps_per_s(wl, x_cores, nsteps_max=3, budget_s=20.0):
     return n / dt, n, dt
 
 
+def dense_dof_rate(wl_full, n=32, reps=5):
+    """DOF-updates/s of the dense FP64 oracle stepper (OpenMP) on an n x n sample of the workload's
+    per-cell structure (same groups and ordinates), the rate the paper quotes for a traditional
+    S_N solver (Sec. 3.2, 'speedup'); returns (rate, unknowns of the sample, threads, seconds)."""
+    from oracle import dense
+    from paper_2602_00290_gb300.workloads import plane_config1
+    wl = plane_config1(nx=n, ny=n, G=wl_full.ngroup, ntheta=wl_full.ntheta, nphi=wl_full.nphi,
+                       rmax=wl_full.rmax, tol=wl_full.tol)
+    S = dense.DenseSolver(wl)
+    I = S.initial()
+    I = S.step(I)  # warm (page-in, thread start-up)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        I = S.step(I)
+    dt = time.perf_counter() - t0
+    unknowns = wl.full_unknowns()
+    return reps * unknowns / dt, unknowns, dense.DenseSolver.threads(), dt
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -456,6 +475,19 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": host_cores(), "kind": "oracle",
                                 "sample": f"{n} naive explicit-sum TT step(s) (numpy, LAPACK QR + SVD) of the "
                                           f"same workload from the GPU state after the timed steps ({dt:.1f} s)"}
+        # the paper's speedup S = t_dense / t_TT (Sec. 3.2), against the dense oracle's rate on
+        # this host (the paper quotes 3.6-5.0e8 DOF-updates/s on its M3 Ultra; context only)
+        try:
+            rate, nu, thr, ddt = dense_dof_rate(wl)
+            t_dense = wl.full_unknowns() / rate
+            line["cpu_baseline"]["dense_oracle"] = {
+                "dof_updates_per_s": rate, "threads": thr,
+                "sample": f"5 dense FP64 steps of a 32x32-cell, {wl.ngroup}-group, {wl.ntheta}x{wl.nphi}-ordinate "
+                          f"grid ({nu} unknowns, {ddt:.1f} s)",
+                "dense_step_s_at_workload": t_dense,
+                "speedup_tt_gpu_over_dense": t_dense / (line["ms_per_step"] / 1e3)}
+        except Exception as e:  # a report beside the baseline, never a reason to lose the line
+            line["cpu_baseline"]["dense_oracle"] = {"error": str(e)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
