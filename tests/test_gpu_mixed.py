@@ -34,7 +34,9 @@ def fro_rel(a, b):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("kw", [dict(), dict(nx=20, ny=16, G=8, ntheta=8, nphi=16, rmax=12)])
+@pytest.mark.parametrize("kw", [dict(), dict(nx=20, ny=16, G=8, ntheta=8, nphi=16, rmax=12),
+                                dict(nx=16, ny=12, G=6, ntheta=8, nphi=16, rmax=48)],
+                         ids=["small", "medium", "rank_capacity_48"])
 def test_mixed_step_energy_density_within_1e6(tt, ctx, dtype, kw):
     args = dict(nx=12, ny=10, G=5, ntheta=4, nphi=8, rmax=8, tol=1e-6)
     args.update(kw)
