@@ -180,6 +180,16 @@ def dense_dof_rate(wl_full, n=32, reps=5):
     return reps * unknowns / dt, unknowns, dense.DenseSolver.threads(), dt
 
 
+def max_over_ranks(x, dist, device):
+    """The largest x over all ranks (the job's time is its slowest rank's); x itself alone."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -285,10 +295,7 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     ctx.diagnostics(reset=True)
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, "cuda")
     hist = rank_hist.cpu().numpy()
     r_seq = [ranks[0]] + [list(map(int, h)) for h in hist]
     N = wl.nrow
