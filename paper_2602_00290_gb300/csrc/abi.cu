@@ -4,6 +4,8 @@
 #include <cstdlib>
 #include <cstring>
 
+#include <atomic>
+
 #include "common.cuh"
 #include "instr.cuh"
 #include "small.cuh"
@@ -80,12 +82,15 @@ tt_status with_ws(tt_context* ctx, F&& fn) {
 
 int set_device(tt_context* ctx) { return cudaSetDevice(ctx->device) == cudaSuccess; }
 
+std::atomic<unsigned long long> g_plan_serial{0};
+
 // A captured tt_step and everything its launch sequence depends on: the plan, the state's
 // pointers and capacities, the step arguments, the workspace and the context settings that
 // choose kernels.  Device data (ranks, cores, plan arrays, material temperature) may change
 // between replays; none of it is read by the host.
 struct StepGraph {
   const tt_plan* plan = nullptr;
+  unsigned long long plan_serial = 0;  // the plan's device arrays belong to this serial
   int d = 0;
   tt_dtype dtype = TT_F64;
   void* core[TT_MAX_CORES] = {};
@@ -109,6 +114,7 @@ struct StepGraph {
                       tt_precision prec, double* energy) {
     StepGraph g;
     g.plan = plan;
+    g.plan_serial = plan->serial;
     g.d = I->d;
     g.dtype = I->dtype;
     for (int j = 0; j < TT_MAX_CORES; ++j) g.core[j] = (j < I->d) ? I->core[j] : nullptr;
@@ -130,7 +136,7 @@ struct StepGraph {
     return g;
   }
   bool same(const StepGraph& o) const {
-    if (plan != o.plan || d != o.d || dtype != o.dtype || rank != o.rank || tol != o.tol || rmax != o.rmax ||
+    if (plan != o.plan || plan_serial != o.plan_serial || d != o.d || dtype != o.dtype || rank != o.rank || tol != o.tol || rmax != o.rmax ||
         prec != o.prec || energy != o.energy || ws != o.ws || ws_bytes != o.ws_bytes || rounding != o.rounding ||
         sketch != o.sketch || sketch_nang != o.sketch_nang || sketch_ell != o.sketch_ell ||
         coop_grid_max != o.coop_grid_max || tsqr_leaf_cap != o.tsqr_leaf_cap || tune_epoch != o.tune_epoch)
@@ -332,6 +338,7 @@ tt_status tt_plan_create(tt_context* ctx, const tt_problem* prob, tt_plan** out)
   tt_plan* p = new tt_plan();
   std::memset(p, 0, sizeof(tt_plan));
   p->ctx = ctx;
+  p->serial = g_plan_serial.fetch_add(1) + 1;
   tt_status st = ttk::physics_setup(ctx, prob, p);
   if (st != TT_OK) {
     tt_plan_destroy(p);

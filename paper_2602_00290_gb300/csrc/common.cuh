@@ -108,6 +108,7 @@ struct tt_context {
 
 struct tt_plan {
   tt_context* ctx;
+  unsigned long long serial;  // unique per created plan (a plan at a reused address differs)
   int ndim, nx, ny, nz, G, quad, ntheta, nphi;
   int d;          // TT cores: 2 (slab) or 3
   int n1, n2;     // angular mode sizes (n2 = 1 when d = 2)
