@@ -151,7 +151,8 @@ typedef enum {
 tt_status tt_context_set_timing(tt_context *ctx, int enable);
 
 /* Replay tt_step as a CUDA graph (enable != 0; default off).  With it on, tt_step captures its
- * launch sequence the first time it runs for a given key (plan; state pointers, rank capacities
+ * launch sequence the first time it runs for a given key (the plan, by its creation, so that a
+ * plan made at a destroyed plan's address is a new key; state pointers, rank capacities
  * and dtype; tol, rmax, precision, energy_dev; the context's workspace, rounding method, sketch
  * and TSQR kernel table) and replays that graph, on the context's stream, while the key stays
  * the same; a new key drops the old graph and captures again.  Device data (ranks, cores, plan
