@@ -5,7 +5,7 @@
  * "Multigroup Thermal Radiation Transport with Tensor Trains" (arXiv 2602.00290):
  * the solution I_{k l p} = Z_k Theta_l Phi_p with a merged spatio-spectral core Z
  * (Sec. 3.1, Eq. tensor_decomp_mer), advanced by step-then-truncate (end of Sec. 3.1):
- * forward-Euler upwind transport as a sum of n = 2 d_X rank-1 TT operators
+ * forward-Euler transport (upwind, Rusanov or central flux) as a sum of n rank-1 TT operators
  * (Appendix A, 'Value of n'), SVD-based rounding (Sec. 3.1 footnote), the
  * backward-Euler operator-split source of Eq. (discRTsource) at fixed material
  * temperature, and rounding again.
