@@ -14,6 +14,7 @@ planck      group emission coefficients epsilon_f(T), Eqs. (Ttoeps1)-(Ttoeps2)
 problem     derived per-row coefficients of the operator-split update, Eq. (discRTsource)
 dense       dense full-grid FP64 S_N stepper (plain C with OpenMP, loaded by ctypes)
 naive_tt    explicit-sum TT arithmetic and SVD-based rounding (numpy / LAPACK)
+naive_tt_nux  the same step in the split topology [Z(nu x)][y][theta][phi] (Sec. 5.2)
 
 Parity status: every function is pinned by tests in ``tests/test_oracle_*.py``
 (closed forms, invariants, brute force); none is marked "parity unpinned".

@@ -214,6 +214,35 @@ def cube_config(nx: int = 6, ny: int = 5, nz: int = 4, G: int = 3, ntheta: int =
         rho_kappa_a=ka, rho_kappa_s=0.1 * ka, tol=tol, rmax=rmax, steps=steps, seed=seed)
 
 
+def nux_config(nx: int = 8, ny: int = 6, G: int = 6, ntheta: int = 4, nphi: int = 8, rmax: int = 16,
+               tol: float = 1e-6, steps: int = 4, seed: int = 7, cfl: float = 0.5,
+               contrast: float = 1000.0) -> Workload:
+    """2-D problem on [0,1]^2 whose density, temperature and opacities depend on x only (so that
+    the source step is a row scaling of a core over (group, x), the topology [Z(nu x)][y][theta]
+    [phi]): rho(x) = 1 + 99 min(1, sum_b exp(-(x - c_b)^2 / (2 w_b^2))) with 4 blobs,
+    c_b ~ U[0.1, 0.9], w_b ~ U[0.03, 0.1]; rho*kappa_a = rho(x) kappa0 (nu_f/nu0)^-3 (1 + contrast
+    1[f is a line group]) with min(16, G/2) seeded line groups; kappa_s = 0.1 kappa_a; T linear in
+    x 1 -> 0.1; vacuum; lat/long ordinates; dt = cfl dx."""
+    rng = np.random.default_rng(seed)
+    cb = rng.uniform(0.1, 0.9, 4)
+    wb = rng.uniform(0.03, 0.1, 4)
+    xc = (np.arange(nx) + 0.5) / nx
+    s_ = np.zeros(nx)
+    for b in range(4):
+        s_ += np.exp(-(xc - cb[b]) ** 2 / (2.0 * wb[b] ** 2))
+    rho_x = 1.0 + 99.0 * np.minimum(1.0, s_)
+    edges = group_edges(G)
+    lines = np.zeros(G)
+    nl = max(1, min(16, G // 2))
+    lines[rng.choice(G, nl, replace=False)] = contrast
+    ka = opacity_rows(np.tile(rho_x, ny), edges, 1.0 + lines)
+    return Workload(
+        name=f"nux2d_{nx}x{ny}_g{G}_{ntheta}x{nphi}_r{rmax}", ndim=2, nx=nx, ny=ny, nz=1,
+        ngroup=G, quad="latlong_midpoint", ntheta=ntheta, nphi=nphi, extent=(1.0, 1.0, 1.0),
+        c=1.0, dt=cfl / max(nx, ny), group_edges=edges, temperature=linear_temperature(nx, ny),
+        rho_kappa_a=ka, rho_kappa_s=0.1 * ka, tol=tol, rmax=rmax, steps=steps, seed=seed)
+
+
 def batch_config3(nprob: int = 256, seed: int = 3, scale: int = 1, tol: float = 1e-6,
                   steps: int = 20) -> list:
     """Independent 2-D problems of uneven shape stepped as one batch: Nx = Ny ~ U{32, 64, ..., 192},
