@@ -150,8 +150,10 @@ typedef enum {
 #define TT_TIMER_COUNT 6
 tt_status tt_context_set_timing(tt_context *ctx, int enable);
 
-/* Replay tt_step as a CUDA graph (enable != 0; default off).  With it on, tt_step captures its
- * launch sequence the first time it runs for a given key (the plan, by its creation, so that a
+/* Replay tt_step as a CUDA graph (enable != 0; default off).  With it on, the first tt_step for a
+ * given key runs eagerly (so every kernel of the step is loaded and configured outside any
+ * capture), the second captures the step's launch sequence, and later ones replay it; the key is
+ * (the plan, by its creation, so that a
  * plan made at a destroyed plan's address is a new key; state pointers, rank capacities
  * and dtype; tol, rmax, precision, energy_dev; the context's workspace, rounding method, sketch
  * and TSQR kernel table) and replays that graph, on the context's stream, while the key stays
@@ -161,7 +163,8 @@ tt_status tt_context_set_timing(tt_context *ctx, int enable);
  * while the context's stream is itself being captured runs eagerly (it then becomes part of
  * the caller's graph).  With kernel timing on (tt_context_set_timing), or when a step cannot be
  * captured, tt_step runs eagerly with the same results.  Launch counters count each replay's
- * kernels.  Turning it off releases the graph.  Errors: TT_ERR_ARG (ctx NULL). */
+ * kernels; tt_context_diagnostics reports replays, captures and refused captures.  Turning it
+ * off releases the graph.  Errors: TT_ERR_ARG (ctx NULL). */
 tt_status tt_context_set_graphs(tt_context *ctx, int enable);
 
 /* Select the rounding method of the context (TT_ERR_ARG for an unknown method).  With
@@ -192,6 +195,22 @@ tt_status tt_context_set_tsqr(tt_context *ctx, tt_precision prec, int32_t ncap, 
 tt_status tt_context_get_tsqr(const tt_context *ctx, tt_precision prec, int32_t ncap, int32_t *variant,
                               int32_t *leaves);
 
+/* Launch geometry of the tall-skinny QR over the merged core (the first sweep of the rounding,
+ * Sec. 3.1 footnote) for a pass of ncap columns and nrows rows at precision prec with TSQR
+ * variant `variant` (as tt_context_set_tsqr; variants that cannot take the shape are reported as
+ * the one that runs), max_leaves the leaf cap in force (<= 0: none), on a device with num_sms
+ * SMs where per_sm leaf CTAs are resident at once (what the occupancy query reports for the leaf
+ * kernel).  A host computation by the functions the launches use: it needs no GPU and touches
+ * no device.  out[0..nout) (nout <= 11): [0] leaves, [1] rows per leaf (the last leaf takes the
+ * ragged rest), [2] rows per block, [3] leaf threads per CTA, [4] leaf dynamic shared-memory
+ * bytes, [5] merge threads per CTA, [6] merge dynamic shared-memory bytes, [7] merge levels,
+ * [8] and [9] doubles of the two R-factor buffers the step's workspace holds (leaf output and
+ * merge levels alternate between them), [10] the variant that runs.  TT_ERR_UNSUPPORTED for a
+ * shape no kernel takes (too many columns, or per_sm < 1 for the row-split leaf).  The paper has
+ * no counterpart: these are launch-shape choices. */
+tt_status tt_tsqr_geometry(tt_precision prec, int32_t variant, int32_t ncap, int64_t nrows, int32_t num_sms,
+                           int32_t per_sm, int32_t max_leaves, int64_t *out, int32_t nout);
+
 /* Autotune the TSQR choice (tt_context_set_tsqr) of the two passes of tt_step for state I with
  * this plan, tolerance and precision: the transport-sum pass ((2 d_X + 1) rcap_1 + n_b columns)
  * and the source pass (rcap_1 + 1 columns).  Each candidate (variant x leaf cap, one pass at a
@@ -211,9 +230,11 @@ tt_status tt_autotune(tt_context *ctx, const tt_plan *plan, const tt_tensor *I, 
  * (launches[TT_TIMER_COUNT], nullable) since the last reset; reset != 0 clears both. */
 tt_status tt_context_counters(tt_context *ctx, double *ms, int64_t *launches, int reset);
 
-/* Synchronise the context stream and copy device-side iteration statistics since the last
- * reset into out[0..n) (n <= 3): [0] the largest number of Jacobi sweeps of one SVD,
- * [1] the number of Jacobi SVDs, [2] their total number of sweeps.  reset != 0 clears them. */
+/* Synchronise the context stream and copy iteration statistics since the last reset into
+ * out[0..n) (n <= 6): [0] the largest number of Jacobi sweeps of one SVD, [1] the number of
+ * Jacobi SVDs, [2] their total number of sweeps (device-side counts); [3] tt_step graph replays,
+ * [4] graph captures, [5] captures that failed, after which the step ran eagerly (host-side
+ * counts of tt_context_set_graphs).  reset != 0 clears them. */
 tt_status tt_context_diagnostics(tt_context *ctx, int64_t *out, int n, int reset);
 
 /* Synchronise the context stream, then return and clear the latched device status. */
@@ -305,14 +326,15 @@ tt_status tt_batch_create(tt_context *ctx, int32_t nprob, const tt_plan *const *
                           const double *tol, const int32_t *rmax, tt_precision prec, int32_t nstreams,
                           tt_batch **out);
 /* Advance every problem of the batch by nsteps time steps, asynchronously on the context stream.
- * The first call captures one batched step as a CUDA graph (so it must not itself be made under
- * an outer stream capture); every step is a replay of that graph.  Device-detected errors are
+ * The first batched step runs eagerly (every kernel loaded and configured outside any capture),
+ * the next one is captured as a CUDA graph (so neither may be made under an outer stream
+ * capture), and every later step is a replay of that graph.  Device-detected errors are
  * latched per problem and reported by tt_batch_sync. */
 tt_status tt_batch_step(tt_batch *b, int32_t nsteps);
 /* Synchronise the context stream; status_out[nprob] (nullable) receives each problem's latched
  * status; returns the first non-OK one. */
 tt_status tt_batch_sync(tt_batch *b, int32_t *status_out);
-/* Kernel launches in one captured batched step (-1 before the first tt_batch_step), total
+/* Kernel launches in one captured batched step (-1 before the graph is captured), total
  * workspace bytes, streams used.  Each pointer is nullable. */
 tt_status tt_batch_info(const tt_batch *b, int64_t *launches_per_step, size_t *workspace_bytes, int32_t *nstreams);
 tt_status tt_batch_destroy(tt_batch *b);

@@ -35,7 +35,7 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
            "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding",
            "tt_internal_ranks", "tt_context_set_sketch", "tt_context_set_tsqr", "tt_context_get_tsqr",
-           "tt_autotune", "tt_context_set_graphs")
+           "tt_autotune", "tt_context_set_graphs", "tt_tsqr_geometry")
 TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2}
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
@@ -114,6 +114,8 @@ def lib():
             "tt_context_get_tsqr": [vp, ctypes.c_int, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "tt_autotune": [vp, vp, ctypes.POINTER(_Tensor), dbl, i32, ctypes.c_int, i32, ctypes.POINTER(i32),
                             ctypes.POINTER(ctypes.c_float)],
+            "tt_tsqr_geometry": [ctypes.c_int, i32, i32, ctypes.c_int64, i32, i32, i32,
+                                 ctypes.POINTER(ctypes.c_int64), i32],
             "tt_internal_ranks": [vp, vp, ctypes.POINTER(_Tensor), ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
                                   ctypes.c_int64],
@@ -124,6 +126,19 @@ def lib():
             f.argtypes = args
         _lib = L
     return _lib
+
+
+GEOMETRY_KEYS = ("leaves", "rows_per_leaf", "block_rows", "leaf_threads", "leaf_smem", "merge_threads",
+                 "merge_smem", "merge_levels", "ws_a_doubles", "ws_b_doubles", "variant")
+
+
+def tsqr_geometry(precision, variant, ncap, nrows, num_sms, per_sm, max_leaves=0):
+    """Launch geometry of the TSQR over the merged core (tt_tsqr_geometry; host only, no GPU)."""
+    out = (ctypes.c_int64 * len(GEOMETRY_KEYS))()
+    v = TSQR_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    _check(lib().tt_tsqr_geometry(PRECISIONS[precision], v, ncap, nrows, num_sms, per_sm, max_leaves, out,
+                                  len(GEOMETRY_KEYS)), "tt_tsqr_geometry")
+    return dict(zip(GEOMETRY_KEYS, list(out)))
 
 
 def status_string(st):
@@ -211,10 +226,12 @@ class Context:
         _check(lib().tt_context_set_timing(self.handle, 1 if enable else 0), "tt_context_set_timing")
 
     def diagnostics(self, reset: bool = False):
-        """Jacobi statistics since the last reset: max sweeps, SVD count, total sweeps."""
-        out = (ctypes.c_int64 * 3)()
-        _check(lib().tt_context_diagnostics(self.handle, out, 3, 1 if reset else 0), "tt_context_diagnostics")
-        return {"jacobi_sweeps_max": out[0], "jacobi_svds": out[1], "jacobi_sweeps_total": out[2]}
+        """Statistics since the last reset: Jacobi max sweeps, SVD count, total sweeps; tt_step
+        graph replays, captures and refused captures (tt_context_diagnostics)."""
+        out = (ctypes.c_int64 * 6)()
+        _check(lib().tt_context_diagnostics(self.handle, out, 6, 1 if reset else 0), "tt_context_diagnostics")
+        return {"jacobi_sweeps_max": out[0], "jacobi_svds": out[1], "jacobi_sweeps_total": out[2],
+                "graph_replays": out[3], "graph_captures": out[4], "graph_failures": out[5]}
 
     def counters(self, reset: bool = False):
         """(ms per category, launches per category) since the last reset (tt_context_counters)."""

@@ -107,6 +107,7 @@ struct StepGraph {
   unsigned long tune_epoch = 0;
   // result of the capture
   cudaGraphExec_t exec = nullptr;
+  bool warmed = false;  // one eager step ran with this key (captured on the next call)
   bool failed = false;  // the step could not be captured: run it eagerly
   long launches[ttk::kNumCat] = {};
 
@@ -195,6 +196,7 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->tune = new ttk::TsqrTune();
   ctx->graphs = 0;
   ctx->step_graph = nullptr;
+  ctx->graph_replays = ctx->graph_captures = ctx->graph_failures = 0;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
@@ -293,14 +295,17 @@ tt_status tt_context_counters(tt_context* ctx, double* ms, int64_t* launches, in
 }
 
 tt_status tt_context_diagnostics(tt_context* ctx, int64_t* out, int n, int reset) {
-  if (!ctx || (n > 0 && !out) || n < 0 || n > 3) return TT_ERR_ARG;
+  if (!ctx || (n > 0 && !out) || n < 0 || n > 6) return TT_ERR_ARG;
   set_device(ctx);
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
   int v[3] = {0, 0, 0};
   if (cudaMemcpy(v, &ctx->ctrl->jac_sweeps_max, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return TT_ERR_CUDA;
-  const int64_t w[3] = {v[0], v[1], v[2]};
+  const int64_t w[6] = {v[0], v[1], v[2], ctx->graph_replays, ctx->graph_captures, ctx->graph_failures};
   for (int i = 0; i < n; ++i) out[i] = w[i];
-  if (reset && cudaMemset(&ctx->ctrl->jac_sweeps_max, 0, sizeof(v)) != cudaSuccess) return TT_ERR_CUDA;
+  if (reset) {
+    if (cudaMemset(&ctx->ctrl->jac_sweeps_max, 0, sizeof(v)) != cudaSuccess) return TT_ERR_CUDA;
+    ctx->graph_replays = ctx->graph_captures = ctx->graph_failures = 0;
+  }
   return TT_OK;
 }
 
@@ -471,9 +476,16 @@ tt_status tt_step(tt_context* ctx, const tt_plan* plan, tt_tensor* I, double tol
   const StepGraph key = StepGraph::of(ctx, plan, I, tol, rmax, prec, energy_dev);
   StepGraph* g = static_cast<StepGraph*>(ctx->step_graph);
   if (!g || !g->same(key)) {
+    // A new key steps eagerly once: every kernel of the step is then loaded and has its
+    // shared-memory limit set outside any capture, and the capture (next call) records only
+    // launches whose configuration already launched successfully.
     drop_step_graph(ctx);
     g = new StepGraph(key);
     ctx->step_graph = g;
+    return with_ws(ctx, body);
+  }
+  if (!g->warmed) {
+    g->warmed = true;
     long before[ttk::kNumCat] = {};
     if (in)
       for (int c = 0; c < ttk::kNumCat; ++c) before[c] = in->launches[c];
@@ -505,13 +517,16 @@ tt_status tt_step(tt_context* ctx, const tt_plan* plan, tt_tensor* I, double tol
         g->launches[c] = in->launches[c] - before[c];
         in->launches[c] = before[c];  // counted again below, per launch of the step
       }
+    ++ctx->graph_captures;
     if (cst != TT_OK || !g->exec) {
       (void)cudaGetLastError();  // the refused capture leaves nothing behind; run the step eagerly
       g->failed = true;
+      ++ctx->graph_failures;
     }
   }
   if (g->failed) return with_ws(ctx, body);
   if (cudaGraphLaunch(g->exec, ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
+  ++ctx->graph_replays;
   if (in)
     for (int c = 0; c < ttk::kNumCat; ++c) in->launches[c] += g->launches[c];
   return TT_OK;

@@ -528,6 +528,28 @@ __global__ void __launch_bounds__(256) k_tsqr_merge(LivePattern lp, int nin, con
   write_R<T, BR>(Rs, ncap, Ro);
 }
 
+// Leaves of a TSQR leaf launch over nrows rows in blocks of BR rows: at most one wave of
+// resident CTAs (num_sms x per_sm), the caller's cap max_leaves (> 0) and cap2 (> 0); every leaf
+// takes rpc rows, a whole number of blocks, and the last one the ragged rest.  The workspace of
+// the R factors is sized by tsqr_max_leaves<T, 32>, which bounds every launch this returns.
+struct LeafSplit {
+  long leaves, rpc;
+};
+inline LeafSplit tsqr_split(long nrows, int BR, int num_sms, int per_sm, int max_leaves, long cap2) {
+  long L = (nrows + BR - 1) / BR;
+  long cap = (long)num_sms * (per_sm > 0 ? per_sm : 1);
+  if (max_leaves > 0 && cap > max_leaves) cap = max_leaves;
+  if (cap2 > 0 && cap > cap2) cap = cap2;
+  if (L > cap) L = cap;
+  if (L < 1) L = 1;
+  long rpc = (nrows + L - 1) / L;
+  rpc = ((rpc + BR - 1) / BR) * BR;
+  if (rpc < BR) rpc = BR;
+  L = (nrows + rpc - 1) / rpc;
+  if (L < 1) L = 1;
+  return {L, rpc};
+}
+
 // Merge tree over the leaves' R factors (defined with the row-split kernels in tsqr_rs.cuh).
 template <typename T>
 tt_status merge_tree(cudaStream_t s, LivePattern lp, int nleaves, double* ws_a, double* ws_b, double** Rfinal);
@@ -547,18 +569,11 @@ tt_status run_tsqr(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, 
   if (threads > MAXT || threads > 256) return TT_ERR_UNSUPPORTED;
   static_assert(BR > 0, "block rows");
   auto leaf = k_tsqr_leaf<T, BR, Src, MAXT, MINB>;
-  cudaFuncSetAttribute(leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (const tt_status a = smem_optin(leaf, smem); a != TT_OK) return a;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf, threads, smem) != cudaSuccess) return TT_ERR_CUDA;
-  long L = (nrows + BR - 1) / BR;
-  long cap = (long)num_sms * (per_sm > 0 ? per_sm : 1);
-  if (max_leaves > 0 && cap > max_leaves) cap = max_leaves;
-  if (L > cap) L = cap;
-  if (L < 1) L = 1;
-  long rpc = (nrows + L - 1) / L;
-  rpc = ((rpc + BR - 1) / BR) * BR;
-  L = (nrows + rpc - 1) / rpc;
-  if (L < 1) L = 1;
+  const LeafSplit sp = tsqr_split(nrows, BR, num_sms, per_sm, max_leaves, 0);
+  const long L = sp.leaves, rpc = sp.rpc;
   {
     TimerScope scope(leaf_cat, s);
     leaf<<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
@@ -920,11 +935,12 @@ __global__ void __launch_bounds__(256) k_update(Src src, LivePattern lp, long nr
   if (partials) update_partials(red, e0t, e1t, partials);
 }
 
-// Persistent grid of the update pass (also the number of energy partials it writes).
+// Persistent grid of the update pass (also the number of energy partials it writes); 0 when the
+// runtime refuses the kernel's shared memory.
 template <typename T, int TM, class Src, class Epi>
 inline long update_grid(int num_sms, int ncap, int kcap, long nrows, size_t stage = 0) {
   const size_t smem = update_smem_bytes<T, TM, Src, Epi>(ncap, kcap, stage);
-  cudaFuncSetAttribute(k_update<T, TM, Src, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (smem_optin(k_update<T, TM, Src, Epi>, smem) != TT_OK) return 0;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_update<T, TM, Src, Epi>, 256, smem) != cudaSuccess ||
       occ < 1)

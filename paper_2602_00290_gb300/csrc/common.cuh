@@ -84,6 +84,18 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <typename S>
 __device__ __forceinline__ double to_d(S x) { return (double)x; }
 
+// Unique id of the CUDA context current on the calling thread (0 when none is current).
+unsigned long long current_context_id();
+// Allow `bytes` of dynamic shared memory per CTA for kernel `func` (the opt-in above 48 KB),
+// never lowering an earlier setting.  TT_ERR_CUDA if the runtime refuses, TT_ERR_UNSUPPORTED
+// above the device's opt-in maximum.  Every launch site above 48 KB calls it and returns its
+// status, so a refused attribute never reaches a launch (or a captured graph node).
+tt_status smem_optin_impl(const void* func, size_t bytes);
+template <class F>
+inline tt_status smem_optin(F* func, size_t bytes) {
+  return smem_optin_impl(reinterpret_cast<const void*>(func), bytes);
+}
+
 }  // namespace ttk
 
 // Host-side context and plan (defined here so every translation unit sees one layout).
@@ -104,6 +116,7 @@ struct tt_context {
   void* tune;  // ttk::TsqrTune, TSQR kernel choice per shape (owned; batch views share it)
   int graphs;        // tt_step replays a captured CUDA graph of the step (tt_context_set_graphs)
   void* step_graph;  // the captured step and what it depends on (owned; not shared by batch views)
+  long graph_replays, graph_captures, graph_failures;  // since the last diagnostics reset
 };
 
 struct tt_plan {

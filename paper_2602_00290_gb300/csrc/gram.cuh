@@ -219,7 +219,7 @@ tt_status gram_matrix(cudaStream_t s, int num_sms, const Src& src, LivePattern l
   double* G = ws.take<double>((size_t)ncap * ncap);
   *G_out = G;
   if (ws.dry) return TT_OK;
-  cudaFuncSetAttribute(k_gram_tiles<Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (const tt_status a = smem_optin(k_gram_tiles<Src>, smem); a != TT_OK) return a;
   TimerScope scope(timer_cat, s);
   k_gram_tiles<Src><<<dim3((unsigned)nsplit, (unsigned)npairs), 256, smem, s>>>(src, lp, nrows, rps, part);
   count_launch();

@@ -1079,9 +1079,16 @@ void reduce_partials(cudaStream_t s, const double* partials, long nblocks, int s
   k_reduce_partials<<<1, 1024, 0, s>>>(partials, nblocks, stride, out, scale); count_launch();
 }
 
+// grid: the CTAs wanted, capped here by the CTAs of this instantiation that are resident at once
+// (a cooperative launch beyond that is refused).
 template <int E>
-static cudaError_t launch_coop(int grid, int m, int n, double* A, double* V, DevCtrl* ctrl, int maxsweep,
-                               cudaStream_t s) {
+static cudaError_t launch_coop(int grid, int num_sms, int m, int n, double* A, double* V, DevCtrl* ctrl,
+                               int maxsweep, cudaStream_t s) {
+  int occ = 0;
+  const cudaError_t oe = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coop_jacobi<E>, 256, 0);
+  if (oe != cudaSuccess) return oe;
+  const int resident = num_sms * (occ > 0 ? occ : 1);
+  if (grid > resident) grid = resident;
   // a single CTA is always co-resident with itself: plain launch (capturable in any graph)
   if (grid == 1) {
     k_coop_jacobi<E><<<1, 256, 0, s>>>(m, n, A, V, ctrl, maxsweep);
@@ -1102,21 +1109,17 @@ tt_status coop_jacobi(cudaStream_t s, int num_sms, int m, int n, double* A, doub
   if (V) {
     k_identity<<<(n * n + 255) / 256, 256, 0, s>>>(n, V); count_launch();
   }
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_coop_jacobi<16>, 256, 0);
   const int npairs = (n + 1) / 2;
   int grid = npairs;
-  const int resident = num_sms * (occ > 0 ? occ : 1);
-  if (grid > resident) grid = resident;
   if (grid_max > 0 && grid > grid_max) grid = grid_max;
   if (grid < 1) grid = 1;
   const int maxsweep = 40;
   cudaError_t e;
-  if (m <= 256) e = launch_coop<1>(grid, m, n, A, V, ctrl, maxsweep, s);
-  else if (m <= 512) e = launch_coop<2>(grid, m, n, A, V, ctrl, maxsweep, s);
-  else if (m <= 1024) e = launch_coop<4>(grid, m, n, A, V, ctrl, maxsweep, s);
-  else if (m <= 2048) e = launch_coop<8>(grid, m, n, A, V, ctrl, maxsweep, s);
-  else e = launch_coop<16>(grid, m, n, A, V, ctrl, maxsweep, s);
+  if (m <= 256) e = launch_coop<1>(grid, num_sms, m, n, A, V, ctrl, maxsweep, s);
+  else if (m <= 512) e = launch_coop<2>(grid, num_sms, m, n, A, V, ctrl, maxsweep, s);
+  else if (m <= 1024) e = launch_coop<4>(grid, num_sms, m, n, A, V, ctrl, maxsweep, s);
+  else if (m <= 2048) e = launch_coop<8>(grid, num_sms, m, n, A, V, ctrl, maxsweep, s);
+  else e = launch_coop<16>(grid, num_sms, m, n, A, V, ctrl, maxsweep, s);
   if (e != cudaSuccess) return TT_ERR_CUDA;
   count_launch();
   k_jacobi_sort<<<1, 1024, 0, s>>>(m, n, A, sigma, perm, tmp, &ctrl->status); count_launch();
@@ -1164,9 +1167,10 @@ static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K
   const size_t chol_smem = sizeof(double) * ((size_t)KK + K);
   const size_t inv_smem = sizeof(double) * 2 * (size_t)KK;
   const size_t rtu_smem = sizeof(double) * ((size_t)KK + (size_t)kRowsTile * K);
-  cudaFuncSetAttribute(k_chol_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)chol_smem);
-  cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem);
-  cudaFuncSetAttribute(k_rows_times_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rtu_smem);
+  for (const auto& [f, b] : {std::make_pair((const void*)k_chol_upper, chol_smem),
+                              std::make_pair((const void*)k_tri_inv, inv_smem),
+                              std::make_pair((const void*)k_rows_times_upper, rtu_smem)})
+    if (const tt_status a = smem_optin_impl(f, b); a != TT_OK) return a;
   for (int pass = 0; pass < 2; ++pass) {
     double* T = pass ? T2 : T1;
     k_gram_chunks<<<dim3((unsigned)nchunks, (unsigned)((KK + kGramEntries - 1) / kGramEntries)), 256, 0, s>>>(
@@ -1208,7 +1212,7 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   if (cols <= 32) {
     k_jacobi_warp<<<1, 32, 0, s>>>(cols, R, U, raw, 40, ctrl); count_launch();
   } else if (in_smem) {
-    cudaFuncSetAttribute(k_jacobi_rt<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (const tt_status a = smem_optin(k_jacobi_rt<float, true>, smem); a != TT_OK) return a;
     k_jacobi_rt<float, true><<<1, 1024, smem, s>>>(cols, R, U, raw, 40, nullptr, ctrl); count_launch();
   } else {
     k_jacobi_rt<float, false><<<1, 1024, 0, s>>>(cols, R, U, raw, 40, gwork, ctrl); count_launch();

@@ -199,7 +199,7 @@ static tt_status launch_update_blk(cudaStream_t s, int num_sms, const SrcStencil
   const size_t smem = update_blk_smem_bytes<TM, S>(src, update_kpad<Epi>(kcap), lp.nextra);
   if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
   auto kern = k_update_blk<TM, S, Epi>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (const tt_status a = smem_optin(kern, smem); a != TT_OK) return a;
   int occ = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, smem) != cudaSuccess || occ < 1) occ = 1;
   const long ntiles = (nrows + TM - 1) / TM;
@@ -236,6 +236,7 @@ static tt_status launch_update(cudaStream_t s, int num_sms, const Src& src, Live
   const size_t smem = update_smem_bytes<T, TM, Src, Epi>(lp.ncap(), kcap, stage);
   if (smem > 227 * 1024) return TT_ERR_UNSUPPORTED;
   const long grid = update_grid<T, TM, Src, Epi>(num_sms, lp.ncap(), kcap, nrows, stage);
+  if (grid < 1) return TT_ERR_CUDA;
   if (grid_out) *grid_out = grid;
   TimerScope scope(kUpdate, s);
   k_update<T, TM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src2, lp, nrows, W, kcap, epi, partials); count_launch();

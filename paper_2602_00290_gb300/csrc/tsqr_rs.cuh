@@ -366,21 +366,13 @@ tt_status run_tsqr_rs(cudaStream_t s, int num_sms, const Src& src, LivePattern l
   const int threads = tsqr_rs_threads<QS>(ncap);
   if (threads > 1024) return TT_ERR_UNSUPPORTED;
   auto leaf = k_tsqr_leaf_rs<T, BR, QS, Src>;
-  cudaFuncSetAttribute(leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (const tt_status a = smem_optin(leaf, smem); a != TT_OK) return a;
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, leaf, threads, smem) != cudaSuccess) return TT_ERR_CUDA;
   if (per_sm < 1) return TT_ERR_UNSUPPORTED;
-  long L = (nrows + BR - 1) / BR;
-  long cap = (long)num_sms * per_sm;
-  if (max_leaves > 0 && cap > max_leaves) cap = max_leaves;
   const long colcap = tsqr_max_leaves<T, BR>(num_sms, ncap, nrows, max_leaves);
-  if (cap > colcap) cap = colcap;
-  if (L > cap) L = cap;
-  if (L < 1) L = 1;
-  long rpc = (nrows + L - 1) / L;
-  rpc = ((rpc + BR - 1) / BR) * BR;
-  L = (nrows + rpc - 1) / rpc;
-  if (L < 1) L = 1;
+  const LeafSplit sp = tsqr_split(nrows, BR, num_sms, per_sm, max_leaves, colcap);
+  const long L = sp.leaves, rpc = sp.rpc;
   {
     TimerScope scope(leaf_cat, s);
     leaf<<<(unsigned)L, threads, smem, s>>>(src, lp, nrows, rpc, ws_a); count_launch();
@@ -409,13 +401,12 @@ tt_status merge_tree(cudaStream_t s, LivePattern lp, int nleaves, double* ws_a, 
   if (rs) {
     smem = tsqr_rs_smem_bytes<T, RBR, 4>(ncap);
     threads = rs_threads;
-    cudaFuncSetAttribute(k_tsqr_merge_rs<T, RBR, 4, RVREG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
+    if (const tt_status a = smem_optin(k_tsqr_merge_rs<T, RBR, 4, RVREG>, smem); a != TT_OK) return a;
   } else {
     smem = tsqr_smem_bytes<T, MBR>(ncap);
     threads = ((ncap + 31) / 32) * 32;
     if (smem > 227 * 1024 || threads > 256) return TT_ERR_UNSUPPORTED;
-    cudaFuncSetAttribute(k_tsqr_merge<T, MBR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (const tt_status a = smem_optin(k_tsqr_merge<T, MBR>, smem); a != TT_OK) return a;
   }
   TimerScope scope(kTsqrMerge, s);
   double* in = ws_a;

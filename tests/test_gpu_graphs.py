@@ -60,6 +60,11 @@ def test_graph_steps_equal_eager_steps(tt, wl, prec, dtype):
         for ctx, _, _ in pair:
             ctx.sync()
         _same(pair[0][2], pair[1][2])
+    # the first step ran eagerly, the second captured the graph, every later one replayed it
+    d = pair[1][0].diagnostics()
+    assert (d["graph_captures"], d["graph_failures"], d["graph_replays"]) == (1, 0, 5)
+    d0 = pair[0][0].diagnostics()
+    assert (d0["graph_captures"], d0["graph_replays"]) == (0, 0)
     _close(pair)
 
 
