@@ -14,8 +14,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle import naive_tt as nt, problem  # noqa: E402
 from paper_2602_00290_gb300.workloads import batch_config3  # noqa: E402
+from tie import STEP_KEYS, assert_tie_free  # noqa: E402
 
-TIE = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -70,9 +70,8 @@ def test_batch_fp64_matches_single_steps_and_oracle(tt, ctx, batches):
             xb = nt.to_dense_rows(states[i].to_cores())
             assert states[i].ranks() == singles[i].ranks(), (step, i)
             assert rel(xb, nt.to_dense_rows(singles[i].to_cores())) < 1e-12, (step, i)
-            tie = any(b["gap"] <= TIE for k in ("transport_round", "source_round") for b in info[k]["bonds"])
-            if not tie:
-                assert states[i].ranks() == nt.ranks(refs[i]), (step, i)
+            assert_tie_free(info, STEP_KEYS, where=f"step {step}, problem {i}")
+            assert states[i].ranks() == nt.ranks(refs[i]), (step, i)
             assert rel(xb, nt.to_dense_rows(refs[i])) < 1e-10, (step, i)
     assert batch.info()["launches_per_step"] > 0
     batch.close()

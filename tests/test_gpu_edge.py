@@ -6,8 +6,8 @@
   8, 2 and 6 rows against 5 r columns), where the TSQR leaves are mostly zero rows;
 * a rank cap of 1 (every rounding truncates to rank 1).
 
-FP64 against the naive TT oracle to 1e-10 with identical ranks away from ties; mixed to 1e-6 in
-energy density."""
+FP64 against the naive TT oracle to 1e-10 with identical ranks (every seeded case asserted tie-free);
+mixed to 1e-6 in energy density."""
 import numpy as np
 import pytest
 
@@ -16,8 +16,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle import naive_tt as nt, problem  # noqa: E402
 from paper_2602_00290_gb300.workloads import plane_config1  # noqa: E402
+from tie import STEP_KEYS, assert_tie_free  # noqa: E402
 
-TIE = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -70,8 +70,8 @@ def test_tiny_grid_fp64_matches_naive_tt(tt, ctx, nx, ny):
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64")
         ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
         ctx.sync()
-        if all(b["gap"] > TIE for k in ("transport_round", "source_round") for b in info[k]["bonds"]):
-            assert x.ranks() == nt.ranks(ref), s
+        assert_tie_free(info, STEP_KEYS, where=f"step {s}")
+        assert x.ranks() == nt.ranks(ref), s
         assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
     plan.close()
 

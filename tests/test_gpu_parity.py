@@ -15,8 +15,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle import dense, naive_tt as nt, planck, problem, quadrature  # noqa: E402
 from paper_2602_00290_gb300.workloads import plane_config1, random_tt, slab_config0  # noqa: E402
+from tie import STEP_KEYS, assert_tie_free  # noqa: E402
 
-TIE = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -137,10 +137,6 @@ def test_apply_transport_capacity_overflow(tt, ctx):
 
 # ------------------------------------------------------------------------------------ rounding
 
-def _tie_free(info):
-    return all(b["gap"] > TIE for b in info["bonds"])
-
-
 @pytest.mark.parametrize("n,r", [([300, 6, 7], [5, 4]), ([75, 9], [6]), ([1000, 16, 32], [12, 9])])
 def test_round_exact_reconstruction(tt, ctx, n, r):
     a = random_tt(n, r, seed=8)
@@ -162,9 +158,9 @@ def test_round_sum_matches_oracle(tt, ctx, tol, rmax):
     x = tt.TT.from_cores(a, rcap=[20, 20])
     tt.tt_round(ctx, x, tol, rmax)
     ctx.sync()
-    if _tie_free(info):
-        assert x.ranks() == nt.ranks(want)
-        assert rel(nt.full(x.to_cores()), nt.full(want)) < 1e-10
+    assert_tie_free(info)
+    assert x.ranks() == nt.ranks(want)
+    assert rel(nt.full(x.to_cores()), nt.full(want)) < 1e-10
 
 
 def test_round_x_plus_x_and_zero(tt, ctx):
@@ -201,8 +197,7 @@ def _run_steps(tt, ctx, wl, nsteps, rcap, dtype="f64"):
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64", energy)
         ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
         ctx.sync()
-        tie_free = _tie_free(info["transport_round"]) and _tie_free(info["source_round"])
-        yield s, x, ref, coef, plan, energy.cpu().numpy(), tie_free
+        yield s, x, ref, coef, plan, energy.cpu().numpy(), info
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(tol=1e-8, rmax=12), dict(tol=1e-4, rmax=6),
@@ -214,9 +209,8 @@ def test_step_plane_matches_naive_tt(tt, ctx, kw):
     if infl is not None:
         wl = wl.with_(inflow_temperature=infl)
     rcap = [wl.rmax, wl.rmax]
-    for s, x, ref, coef, plan, energy, tie_free in _run_steps(tt, ctx, wl, 4, rcap):
-        if not tie_free:
-            pytest.skip("rank decision within 1e-9 of the threshold")
+    for s, x, ref, coef, plan, energy, info in _run_steps(tt, ctx, wl, 4, rcap):
+        assert_tie_free(info, STEP_KEYS, where=f"step {s}")
         assert x.ranks() == nt.ranks(ref), (s, x.ranks(), nt.ranks(ref))
         assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10
         E = tt.tt_energy_density(ctx, plan, x).cpu().numpy()

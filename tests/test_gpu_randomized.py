@@ -10,8 +10,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle import naive_tt as nt, problem  # noqa: E402
 from paper_2602_00290_gb300.workloads import plane_config1, random_tt, sketch_matrix  # noqa: E402
+from tie import STEP_KEYS, assert_tie_free  # noqa: E402
 
-TIE = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -46,8 +46,8 @@ def test_randomized_round_matches_oracle(tt, tol, ell):
     x = tt.TT.from_cores(a, rcap=[20, 20])
     tt.tt_round(c, x, tol, 20)
     c.sync()
-    if all(b["gap"] > TIE for b in info["bonds"]):
-        assert x.ranks() == nt.ranks(want)
+    assert_tie_free(info)
+    assert x.ranks() == nt.ranks(want)
     assert rel(nt.full(x.to_cores()), nt.full(want)) < 1e-10
     c.close()
 
@@ -67,8 +67,8 @@ def test_randomized_step_matches_oracle(tt, prec):
         ref = nt.step(ref, coef, wl.tol, wl.rmax, info, rounding="randomized", omega=om)
         c.sync()
         if prec == "fp64":
-            if all(b["gap"] > TIE for k in ("transport_round", "source_round") for b in info[k]["bonds"]):
-                assert x.ranks() == nt.ranks(ref), s
+            assert_tie_free(info, STEP_KEYS, where=f"step {s}")
+            assert x.ranks() == nt.ranks(ref), s
             assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
         E = tt.tt_energy_density(c, plan, x).cpu().numpy()
         Er = nt.energy_density_rows(ref, coef)

@@ -9,8 +9,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle import dense, naive_tt as nt, problem  # noqa: E402
 from paper_2602_00290_gb300.workloads import plane_config1, random_tt, slab_config0  # noqa: E402
+from tie import STEP_KEYS, assert_tie_free  # noqa: E402
 
-TIE = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -67,8 +67,8 @@ def test_rusanov_step_matches_naive_tt(tt, ctx, kw):
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64")
         ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
         ctx.sync()
-        if all(b["gap"] > TIE for k in ("transport_round", "source_round") for b in info[k]["bonds"]):
-            assert x.ranks() == nt.ranks(ref), s
+        assert_tie_free(info, STEP_KEYS, where=f"step {s}")
+        assert x.ranks() == nt.ranks(ref), s
         assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
 
 

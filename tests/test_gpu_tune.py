@@ -15,8 +15,8 @@ pytestmark = pytest.mark.gpu
 
 from oracle import coupled, naive_tt as nt, problem  # noqa: E402
 from paper_2602_00290_gb300.workloads import plane_config1, random_tt, slab_config0  # noqa: E402
+from tie import STEP_KEYS, assert_tie_free  # noqa: E402
 
-TIE = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -45,10 +45,6 @@ def force(ctx, prec, variant, leaves, ncaps=range(1, 257)):
         ctx.set_tsqr(prec, n, variant, leaves)
 
 
-def no_tie(info, keys):
-    return all(b["gap"] > TIE for k in keys for b in info[k]["bonds"])
-
-
 @pytest.mark.parametrize("leaves", [0, 3, 7])
 @pytest.mark.parametrize("tol,rmax", [(1e-6, 20), (1e-3, 4)])
 def test_rowsplit_round_matches_oracle(tt, ctx, leaves, tol, rmax):
@@ -60,8 +56,8 @@ def test_rowsplit_round_matches_oracle(tt, ctx, leaves, tol, rmax):
     x = tt.TT.from_cores(a, rcap=[20, 20])
     tt.tt_round(ctx, x, tol, rmax)
     ctx.sync()
-    if all(b["gap"] > TIE for b in info["bonds"]):
-        assert x.ranks() == nt.ranks(want)
+    assert_tie_free(info)
+    assert x.ranks() == nt.ranks(want)
     assert rel(nt.full(x.to_cores()), nt.full(want)) < 1e-10
 
 
@@ -92,8 +88,8 @@ def test_rowsplit_step_matches_oracle(tt, ctx, leaves, kw):
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64")
         ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
         ctx.sync()
-        if no_tie(info, ("transport_round", "source_round")):
-            assert x.ranks() == nt.ranks(ref), s
+        assert_tie_free(info, STEP_KEYS, where=f"step {s}")
+        assert x.ranks() == nt.ranks(ref), s
         assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
 
 
@@ -126,8 +122,8 @@ def test_rowsplit_slab_step_matches_oracle(tt, ctx):
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "fp64")
         ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
         ctx.sync()
-        if no_tie(info, ("transport_round", "source_round")):
-            assert x.ranks() == nt.ranks(ref), s
+        assert_tie_free(info, STEP_KEYS, where=f"step {s}")
+        assert x.ranks() == nt.ranks(ref), s
         assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
 
 
@@ -191,8 +187,8 @@ def test_autotune_keeps_state_and_parity(tt, ctx, prec, dtype):
         ref = nt.step(ref, coef, wl.tol, wl.rmax, info)
         ctx.sync()
         if prec == "fp64":
-            if no_tie(info, ("transport_round", "source_round")):
-                assert x.ranks() == nt.ranks(ref), s
+            assert_tie_free(info, STEP_KEYS, where=f"step {s}")
+            assert x.ranks() == nt.ranks(ref), s
             assert rel(nt.to_dense_rows(x.to_cores()), nt.to_dense_rows(ref)) < 1e-10, s
         else:
             E = tt.tt_energy_density(ctx, plan, x).cpu().numpy()
