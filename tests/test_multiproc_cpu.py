@@ -34,7 +34,10 @@ dist.init_process_group("gloo")
 rank = dist.get_rank()
 v = bench.max_over_ranks(1.5 + rank, dist, "cpu")
 alone = bench.max_over_ranks(7.0, None, "cpu")
-print(json.dumps({"rank": rank, "world": dist.get_world_size(), "max": v, "alone": alone}), flush=True)
+line = json.dumps({"rank": rank, "world": dist.get_world_size(), "max": v, "alone": alone})
+# each rank writes its own file: the ranks share one stdout pipe, where two lines can interleave
+with open(os.path.join(sys.argv[1], f"rank{rank}.json"), "w") as fh:
+    fh.write(line)
 dist.destroy_process_group()
 """
 
@@ -42,9 +45,9 @@ dist.destroy_process_group()
 def test_max_over_ranks_gloo_world_size_2(tmp_path):
     script = tmp_path / "worker.py"
     script.write_text(WORKER)
-    out = _torchrun([str(script)], str(tmp_path))
+    out = _torchrun([str(script), str(tmp_path)], str(tmp_path))
     assert out.returncode == 0, out.stderr[-2000:]
-    rows = sorted((json.loads(ln) for ln in out.stdout.splitlines() if ln.startswith("{")), key=lambda r: r["rank"])
+    rows = sorted((json.loads((tmp_path / f"rank{r}.json").read_text()) for r in (0, 1)), key=lambda r: r["rank"])
     assert [r["rank"] for r in rows] == [0, 1]
     assert all(r["world"] == 2 and r["max"] == 2.5 and r["alone"] == 7.0 for r in rows)
 
