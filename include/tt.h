@@ -237,6 +237,18 @@ tt_status tt_context_counters(tt_context *ctx, double *ms, int64_t *launches, in
  * counts of tt_context_set_graphs).  reset != 0 clears them. */
 tt_status tt_context_diagnostics(tt_context *ctx, int64_t *out, int n, int reset);
 
+/* Limits of the bounded device-side iterations of a context, for tests of the failure paths (the
+ * paper has no counterpart).  jacobi_sweeps > 0 caps the sweeps of every FP64 one-sided Jacobi
+ * SVD (default 40): an SVD still rotating at the cap latches TT_ERR_TIMEOUT.  barrier_spins > 0
+ * caps the spins of one wait at the grid-wide barrier of a cooperative kernel (default 2^24 spins
+ * of about 64 ns each).  barrier_extra > 0 makes every such barrier wait for that many arrivals
+ * beyond the grid, which never come, so every wait runs out: the kernel latches TT_ERR_TIMEOUT,
+ * all its CTAs leave, and the context stays usable (the next cooperative launch starts a fresh
+ * barrier).  0 restores a default.  Synchronous (one small host-to-device copy); a step graph
+ * captured earlier reads the new limits when it replays. */
+tt_status tt_context_set_limits(tt_context *ctx, int32_t jacobi_sweeps, int64_t barrier_spins,
+                                int32_t barrier_extra);
+
 /* Synchronise the context stream, then return and clear the latched device status. */
 tt_status tt_sync(tt_context *ctx);
 
@@ -346,8 +358,10 @@ tt_status tt_batch_destroy(tt_batch *b);
  * tt_dot.  It takes a stream of the CURRENT device instead of a context and allocates
  * nothing: its scratch is one file-scope device array of 4 MiB (2^19 doubles) per device,
  * held from the first call on that device until the process exits.  The first call on a
- * device looks up the array's device address (make it before any stream capture on that
- * device).  If the row chunking cannot fit in the 4 MiB (rank capacities with
+ * device (in each CUDA context) looks up the array's device address; that look-up loads this part
+ * of the library on the device, which may block and reserves the array there, so make that first
+ * call before any stream capture on the device and outside any region that must not allocate or
+ * block (e.g. one warm-up call at start-up).  If the row chunking cannot fit in the 4 MiB (rank capacities with
  * rcap_1(x)*rcap_1(y)*3 + (rcap_1(x)+rcap_1(y))*n_1*n_2 beyond 2^19 doubles) the call returns
  * TT_ERR_WORKSPACE and launches nothing.  Every call writes all the scratch it reads, so no
  * clearing is needed between calls, but all calls on a device share the one array: calls

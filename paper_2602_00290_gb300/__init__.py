@@ -35,7 +35,7 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
            "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding",
            "tt_internal_ranks", "tt_context_set_sketch", "tt_context_set_tsqr", "tt_context_get_tsqr",
-           "tt_autotune", "tt_context_set_graphs", "tt_tsqr_geometry")
+           "tt_autotune", "tt_context_set_graphs", "tt_tsqr_geometry", "tt_context_set_limits")
 TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2}
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
@@ -114,6 +114,7 @@ def lib():
             "tt_context_get_tsqr": [vp, ctypes.c_int, i32, ctypes.POINTER(i32), ctypes.POINTER(i32)],
             "tt_autotune": [vp, vp, ctypes.POINTER(_Tensor), dbl, i32, ctypes.c_int, i32, ctypes.POINTER(i32),
                             ctypes.POINTER(ctypes.c_float)],
+            "tt_context_set_limits": [vp, i32, ctypes.c_int64, i32],
             "tt_tsqr_geometry": [ctypes.c_int, i32, i32, ctypes.c_int64, i32, i32, i32,
                                  ctypes.POINTER(ctypes.c_int64), i32],
             "tt_internal_ranks": [vp, vp, ctypes.POINTER(_Tensor), ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
@@ -176,6 +177,11 @@ class Context:
 
     def sync(self):
         _check(lib().tt_sync(self.handle), "tt_sync")
+
+    def set_limits(self, jacobi_sweeps: int = 0, barrier_spins: int = 0, barrier_extra: int = 0):
+        """Bounded device-side iterations (tt_context_set_limits; 0 restores a default)."""
+        _check(lib().tt_context_set_limits(self.handle, int(jacobi_sweeps), int(barrier_spins), int(barrier_extra)),
+               "tt_context_set_limits")
 
     def set_sketch(self, omega):
         """Sketch of randomized rounding: omega (n_1...n_{d-1} x l) as a numpy or torch array."""

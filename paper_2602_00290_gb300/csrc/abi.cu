@@ -14,15 +14,6 @@
 
 namespace ttk {
 thread_local Instr* g_instr = nullptr;
-}
-
-namespace {
-
-struct InstrGuard {
-  ttk::Instr* prev;
-  explicit InstrGuard(tt_context* ctx) : prev(ttk::g_instr) { ttk::g_instr = static_cast<ttk::Instr*>(ctx->instr); }
-  ~InstrGuard() { ttk::g_instr = prev; }
-};
 
 tt_status check_tensor(const tt_tensor* x) {
   if (!x || !x->rank) return TT_ERR_ARG;
@@ -41,6 +32,18 @@ tt_status same_modes(const tt_tensor* a, const tt_tensor* b) {
     if (a->n[j] != b->n[j]) return TT_ERR_SHAPE;
   return TT_OK;
 }
+}  // namespace ttk
+
+namespace {
+
+using ttk::check_tensor;
+using ttk::same_modes;
+
+struct InstrGuard {
+  ttk::Instr* prev;
+  explicit InstrGuard(tt_context* ctx) : prev(ttk::g_instr) { ttk::g_instr = static_cast<ttk::Instr*>(ctx->instr); }
+  ~InstrGuard() { ttk::g_instr = prev; }
+};
 
 tt_status check_plan_tensor(const tt_plan* p, const tt_tensor* x) {
   if (!p) return TT_ERR_ARG;
@@ -306,6 +309,23 @@ tt_status tt_context_diagnostics(tt_context* ctx, int64_t* out, int n, int reset
     if (cudaMemset(&ctx->ctrl->jac_sweeps_max, 0, sizeof(v)) != cudaSuccess) return TT_ERR_CUDA;
     ctx->graph_replays = ctx->graph_captures = ctx->graph_failures = 0;
   }
+  return TT_OK;
+}
+
+tt_status tt_context_set_limits(tt_context* ctx, int32_t jacobi_sweeps, int64_t barrier_spins,
+                                int32_t barrier_extra) {
+  if (!ctx || jacobi_sweeps < 0 || barrier_spins < 0 || barrier_extra < 0) return TT_ERR_ARG;
+  set_device(ctx);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return TT_ERR_CUDA;
+  struct {
+    int sweeps, extra;
+    long long spins;
+  } v{jacobi_sweeps, barrier_extra, (long long)barrier_spins};
+  static_assert(offsetof(ttk::DevCtrl, barrier_extra) == offsetof(ttk::DevCtrl, jac_sweep_cap) + sizeof(int),
+                "limit fields are contiguous");
+  static_assert(offsetof(ttk::DevCtrl, spin_limit) == offsetof(ttk::DevCtrl, jac_sweep_cap) + 2 * sizeof(int),
+                "limit fields are contiguous");
+  if (cudaMemcpy(&ctx->ctrl->jac_sweep_cap, &v, sizeof(v), cudaMemcpyHostToDevice) != cudaSuccess) return TT_ERR_CUDA;
   return TT_OK;
 }
 

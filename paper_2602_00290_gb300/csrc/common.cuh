@@ -23,6 +23,9 @@ struct DevCtrl {
   int jac_sweeps_max;  // max sweeps over Jacobi SVDs since the last counter reset
   int jac_calls;       // Jacobi SVDs since the last counter reset
   int jac_sweeps_sum;  // their total sweeps
+  int jac_sweep_cap;   // > 0: cap on the sweeps of one FP64 Jacobi SVD (tt_context_set_limits)
+  int barrier_extra;   // arrivals a grid barrier waits for beyond the grid (> 0: never met)
+  long long spin_limit;  // > 0: spins of one grid-barrier wait before it gives up (else 2^24)
   unsigned bar_count;  // grid barrier of cooperative kernels: arrivals in this generation
   unsigned bar_gen;    // grid barrier generation
   int abort;           // set when a bounded wait gives up; every CTA then leaves
@@ -83,6 +86,16 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 template <typename S>
 __device__ __forceinline__ double to_d(S x) { return (double)x; }
+
+// Sort key of a singular value or column norm: NaN ranks below every number, so that ranks by
+// decreasing key with ties broken by index always form a permutation (a non-finite input then
+// still gives in-range indices; its status is latched where the value is formed).
+__device__ __forceinline__ double rank_key(double v) { return (v == v) ? v : -INFINITY; }
+
+// Argument checks of a tensor descriptor (d, dtype, capacities, non-null cores) and of two
+// descriptors with equal mode sizes and dtype, shared by every entry point.
+tt_status check_tensor(const tt_tensor* x);
+tt_status same_modes(const tt_tensor* a, const tt_tensor* b);
 
 // Unique id of the CUDA context current on the calling thread (0 when none is current).
 unsigned long long current_context_id();

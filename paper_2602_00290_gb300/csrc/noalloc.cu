@@ -6,6 +6,7 @@
 // that must not block.  tt_dot needs a context, and a context owns allocated workspace.  This
 // entry point takes only a stream and keeps its scratch in one file-scope device array of
 // fixed size that lives as long as the library is loaded on each device that uses it.
+#include <map>
 #include <mutex>
 
 #include "common.cuh"
@@ -20,31 +21,28 @@ constexpr size_t kNoAllocScratchDoubles = 1u << 19;  // 4 MiB of FP64 scratch pe
 // is a stand-in, not a device address.  The device address comes from cudaGetSymbolAddress.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::map<unsigned long long, double*> g_scratch_ptr;  // per CUDA context (its unique id)
 
-// Device address of the scratch array on the current device, looked up once per device.
-tt_status scratch_for_current_device(double** out) {
+// Device address of the scratch array in the current CUDA context, looked up once per context
+// (a context created after cudaDeviceReset, or another context made current on the device, has a
+// new id and its own copy of the array).  Without a context id it is looked up on every call.
+tt_status scratch_for_current_context(double** out) {
   int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TT_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return TT_ERR_CUDA;
+  const unsigned long long cid = ttk::current_context_id();
   std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TT_ERR_CUDA;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
+  if (cid != 0) {
+    auto it = g_scratch_ptr.find(cid);
+    if (it != g_scratch_ptr.end()) {
+      *out = it->second;
+      return TT_OK;
+    }
   }
-  *out = g_scratch_ptr[dev];
-  return TT_OK;
-}
-
-tt_status check(const tt_tensor* x) {
-  if (!x || !x->rank) return TT_ERR_ARG;
-  if (x->d != 2 && x->d != 3) return TT_ERR_UNSUPPORTED;
-  if (x->dtype != TT_F64 && x->dtype != TT_F32) return TT_ERR_ARG;
-  if (x->rcap[0] != 1 || x->rcap[x->d] != 1) return TT_ERR_SHAPE;
-  for (int j = 0; j < x->d; ++j)
-    if (x->n[j] <= 0 || x->rcap[j + 1] <= 0 || !x->core[j]) return TT_ERR_SHAPE;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TT_ERR_CUDA;
+  if (cid != 0) g_scratch_ptr[cid] = static_cast<double*>(p);
+  *out = static_cast<double*>(p);
   return TT_OK;
 }
 
@@ -52,14 +50,12 @@ tt_status check(const tt_tensor* x) {
 
 extern "C" tt_status tt_dot_noalloc(void* cuda_stream, const tt_tensor* x, const tt_tensor* y, double* out_dev) {
   if (!out_dev) return TT_ERR_ARG;
-  tt_status st = check(x);
-  if (st == TT_OK) st = check(y);
+  tt_status st = ttk::check_tensor(x);
+  if (st == TT_OK) st = ttk::check_tensor(y);
+  if (st == TT_OK) st = ttk::same_modes(x, y);
   if (st != TT_OK) return st;
-  if (x->d != y->d || x->dtype != y->dtype) return TT_ERR_SHAPE;
-  for (int j = 0; j < x->d; ++j)
-    if (x->n[j] != y->n[j]) return TT_ERR_SHAPE;
   double* scratch = nullptr;
-  st = scratch_for_current_device(&scratch);
+  st = scratch_for_current_context(&scratch);
   if (st != TT_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   return (x->dtype == TT_F64) ? ttk::dot_into<double>(s, x, y, out_dev, scratch, kNoAllocScratchDoubles)

@@ -417,8 +417,12 @@ __global__ void __launch_bounds__(1024) k_sort_cols(int nv, int ldv, int K, doub
   for (int c = threadIdx.x; c < K; c += blockDim.x) sg[c] = sig[c];
   __syncthreads();
   for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const double v = rank_key(sg[c]);
     int r = 0;
-    for (int q = 0; q < K; ++q) r += (sg[q] > sg[c]) || (sg[q] == sg[c] && q < c);
+    for (int q = 0; q < K; ++q) {
+      const double w = rank_key(sg[q]);
+      r += (w > v) || (w == v && q < c);
+    }
     rank_of[c] = r;
   }
   __syncthreads();
@@ -581,8 +585,10 @@ __global__ void k_reduce_partials(const double* __restrict__ partials, long nblo
 }
 
 
-// Grid-wide barrier for cooperative launches, with a bounded spin.  If the wait gives up,
-// the barrier latches TT_ERR_TIMEOUT and raises the abort flag so every CTA leaves.
+// Grid-wide barrier for cooperative launches, with a bounded spin (ctrl->spin_limit, else 2^24
+// spins of about 64 ns).  If the wait gives up, the barrier latches TT_ERR_TIMEOUT and raises
+// the abort flag so every CTA leaves.  ctrl->barrier_extra > 0 (a test setting) makes it wait
+// for arrivals that never come.
 __device__ bool grid_barrier(DevCtrl* ctrl, unsigned nblocks) {
   __shared__ int sh_ok;
   __syncthreads();
@@ -590,16 +596,18 @@ __device__ bool grid_barrier(DevCtrl* ctrl, unsigned nblocks) {
     volatile unsigned* genp = &ctrl->bar_gen;
     volatile int* abortp = &ctrl->abort;
     const unsigned g = *genp;
+    const unsigned target = nblocks + (unsigned)ctrl->barrier_extra;
+    const long long limit = ctrl->spin_limit > 0 ? ctrl->spin_limit : (1LL << 24);
     __threadfence();
     const unsigned arrived = atomicAdd(&ctrl->bar_count, 1u) + 1u;
-    if (arrived == nblocks) {
+    if (arrived == target) {
       atomicExch(&ctrl->bar_count, 0u);
       __threadfence();
       atomicAdd(&ctrl->bar_gen, 1u);
     } else {
-      long spins = 0;
+      long long spins = 0;
       while (*genp == g && *abortp == 0) {
-        if (++spins > (1L << 24)) {
+        if (++spins > limit) {
           atomicExch(&ctrl->abort, 1);
           latch(&ctrl->status, TT_ERR_TIMEOUT);
           break;
@@ -638,6 +646,7 @@ __global__ void __launch_bounds__(256) k_coop_jacobi(int m, int n, double* __res
   const int tid = threadIdx.x;
   const double floor_abs = 1e-32 * ctrl->fro2;
   const double rel_tol = 2.0 * m * 2.220446049250313e-16;  // round-off of a length-m inner product
+  if (ctrl->jac_sweep_cap > 0 && ctrl->jac_sweep_cap < maxsweep) maxsweep = ctrl->jac_sweep_cap;
   int sweeps = 0;
   for (int sweep = 0; sweep < maxsweep; ++sweep) {
     sweeps = sweep + 1;
@@ -992,9 +1001,12 @@ __global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restr
 // perm[r] = the column of rank r by decreasing vals (ties by index)
 __global__ void __launch_bounds__(1024) k_rank_perm(int n, const double* __restrict__ vals, int* __restrict__ perm) {
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    const double v = vals[c];
+    const double v = rank_key(vals[c]);
     int r = 0;
-    for (int q = 0; q < n; ++q) r += (vals[q] > v) || (vals[q] == v && q < c);
+    for (int q = 0; q < n; ++q) {
+      const double w = rank_key(vals[q]);
+      r += (w > v) || (w == v && q < c);
+    }
     perm[r] = c;
   }
 }
@@ -1023,14 +1035,14 @@ __global__ void __launch_bounds__(1024) k_jacobi_sort(int m, int n, const double
   }
   __syncthreads();
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
-    const double sp = tmp[p];
+    const double sp = rank_key(tmp[p]);
     int rank = 0;
     for (int q = 0; q < n; ++q) {
-      const double sq = tmp[q];
+      const double sq = rank_key(tmp[q]);
       rank += (sq > sp) || (sq == sp && q < p);
     }
     perm[rank] = p;
-    sigma[rank] = sp;
+    sigma[rank] = tmp[p];
   }
 }
 
