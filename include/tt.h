@@ -369,6 +369,24 @@ tt_status tt_batch_destroy(tt_batch *b);
  * results.  Same arguments, layout and errors as tt_dot otherwise. */
 tt_status tt_dot_noalloc(void *cuda_stream, const tt_tensor *x, const tt_tensor *y, double *out_dev);
 
+/* D <- A B^T on the tensor cores (tcgen05, kind::tf32 with FP32 accumulation): A (M x K), B (N x K)
+ * and D (M x N), row-major FP32 device arrays owned by the caller, on stream cuda_stream of the
+ * current device.  passes = 3: split TF32 (each operand x = hi + lo, hi = x rounded to TF32, and
+ * hi_a hi_b + hi_a lo_b + lo_a hi_b summed in FP32: products to about 2^-22 relative); passes = 1:
+ * plain TF32 (about 2^-11).  N a multiple of 16 with 16 <= N <= 256; M, K >= 1.  status_dev
+ * (nullable device int32) latches TT_ERR_TIMEOUT if a bounded wait for the tensor cores runs out.
+ * The paper has no counterpart: this is the product the mixed path's tensor-core kernels use, as a
+ * plain call, so that its arithmetic can be checked against an FP64 product. */
+tt_status tt_tc_gemm(void *cuda_stream, int64_t M, int32_t N, int32_t K, const float *A, const float *B, float *D,
+                     int32_t passes, int32_t *status_dev);
+
+/* Peak probe of one arithmetic pipe, timed with CUDA events on cuda_stream (synchronous):
+ * kind 0 = FP64 FMA, 1 = FP32 FMA (8 independent chains per thread, every SM full), 2 = the
+ * tensor pipe in kind::tf32 (one CTA per SM issuing `iters` MMAs of 128 x 256 x 8 on operands
+ * resident in shared memory).  *flops receives the flops counted (2 per FMA), *ms the time.  The
+ * paper has no counterpart: these are the measured denominators of the roofline fractions. */
+tt_status tt_peak_probe(void *cuda_stream, int32_t kind, int64_t iters, double *flops, float *ms);
+
 /* Radiation energy density per merged row, E_f = (4 pi / c) J_f (Sec. 2), into the
  * device array out_dev[N_Z]. */
 tt_status tt_energy_density(tt_context *ctx, const tt_plan *plan, const tt_tensor *x, double *out_dev);

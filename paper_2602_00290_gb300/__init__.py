@@ -35,7 +35,8 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_context_counters", "tt_context_diagnostics", "tt_dot_noalloc", "tt_batch_create",
            "tt_batch_step", "tt_batch_sync", "tt_batch_info", "tt_batch_destroy", "tt_context_set_rounding",
            "tt_internal_ranks", "tt_context_set_sketch", "tt_context_set_tsqr", "tt_context_get_tsqr",
-           "tt_autotune", "tt_context_set_graphs", "tt_tsqr_geometry", "tt_context_set_limits")
+           "tt_autotune", "tt_context_set_graphs", "tt_tsqr_geometry", "tt_context_set_limits",
+           "tt_tc_gemm", "tt_peak_probe")
 TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2}
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
 
@@ -115,6 +116,8 @@ def lib():
             "tt_autotune": [vp, vp, ctypes.POINTER(_Tensor), dbl, i32, ctypes.c_int, i32, ctypes.POINTER(i32),
                             ctypes.POINTER(ctypes.c_float)],
             "tt_context_set_limits": [vp, i32, ctypes.c_int64, i32],
+            "tt_tc_gemm": [vp, ctypes.c_int64, i32, i32, vp, vp, vp, i32, vp],
+            "tt_peak_probe": [vp, i32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)],
             "tt_tsqr_geometry": [ctypes.c_int, i32, i32, ctypes.c_int64, i32, i32, i32,
                                  ctypes.POINTER(ctypes.c_int64), i32],
             "tt_internal_ranks": [vp, vp, ctypes.POINTER(_Tensor), ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
@@ -140,6 +143,35 @@ def tsqr_geometry(precision, variant, ncap, nrows, num_sms, per_sm, max_leaves=0
     _check(lib().tt_tsqr_geometry(PRECISIONS[precision], v, ncap, nrows, num_sms, per_sm, max_leaves, out,
                                   len(GEOMETRY_KEYS)), "tt_tsqr_geometry")
     return dict(zip(GEOMETRY_KEYS, list(out)))
+
+
+def tc_gemm(A, B, passes=3, stream=None, status=None):
+    """D = A B^T on the tensor cores (tt_tc_gemm): A (M x K), B (N x K) FP32 CUDA tensors."""
+    torch = _torch()
+    A = A.contiguous()
+    B = B.contiguous()
+    M, K = A.shape
+    N = B.shape[0]
+    D = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().tt_tc_gemm(ctypes.c_void_p(s.cuda_stream), M, N, K, ctypes.c_void_p(A.data_ptr()),
+                            ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(D.data_ptr()), passes,
+                            ctypes.c_void_p(status.data_ptr() if status is not None else 0)), "tt_tc_gemm")
+    return D
+
+
+PEAK_KINDS = {"fp64": 0, "fp32": 1, "tf32_tensor": 2}
+
+
+def peak_probe(kind, iters, stream=None):
+    """(flops, ms) of one probe of an arithmetic pipe (tt_peak_probe)."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    flops = ctypes.c_double()
+    ms = ctypes.c_float()
+    _check(lib().tt_peak_probe(ctypes.c_void_p(s.cuda_stream), PEAK_KINDS[kind], int(iters), ctypes.byref(flops),
+                               ctypes.byref(ms)), "tt_peak_probe")
+    return flops.value, ms.value
 
 
 def status_string(st):

@@ -625,10 +625,14 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_b
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
+// Every epilogue latches TT_ERR_NONFINITE in *status (nullable) when a value it writes is not
+// finite: a NaN or Inf anywhere in the inputs of a rounding reaches every row it mixes into, even
+// where the factorisation passes over it (a non-finite column norm gives no reflector).
 template <typename SO>
 struct EpiPlain {
   SO* out;
   long ld;
+  int* status;
   static constexpr bool kExtra = false;
   static constexpr bool kDot = false;
   const double* vj() const { return nullptr; }
@@ -651,6 +655,7 @@ struct EpiSource {
   const double* acoef;
   const double* scoef;
   const double* eps;
+  int* status;
   static constexpr bool kExtra = true;
   static constexpr bool kDot = true;
   __device__ __forceinline__ void prep(long k, double js, double& scale, double& extra, double& e0,
@@ -672,6 +677,7 @@ struct EpiFinal {
   long ld;
   const double* vJ;
   double* jout;  // optional: J of every final row (the coupled temperature update reads it)
+  int* status;
   static constexpr bool kExtra = false;
   static constexpr bool kDot = true;
   __device__ __forceinline__ void prep(long k, double js, double& scale, double& extra, double& e0,
@@ -746,6 +752,7 @@ __device__ __forceinline__ void update_epilogue(const Epi& epi, const T* Os, int
   }
   __syncthreads();
   const int width = kcap + (Epi::kExtra ? 1 : 0);
+  bool finite = true;
   for (int mm = warp; mm < TM; mm += nwarps) {
     const long k = row0 + mm;
     if (k >= nrows) break;
@@ -753,10 +760,12 @@ __device__ __forceinline__ void update_epilogue(const Epi& epi, const T* Os, int
     const T sc = (T)rowv[mm];
     const double ex = rowv[TM + mm];
     for (int j = lane; j < width; j += 32) {
-      if (j < kcap) epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))(sc * o[j]);
-      else epi.out[k * epi.ld + j] = (decltype(+epi.out[0]))ex;
+      const auto v = (j < kcap) ? (decltype(+epi.out[0]))(sc * o[j]) : (decltype(+epi.out[0]))ex;
+      finite = finite && isfinite(v);
+      epi.out[k * epi.ld + j] = v;
     }
   }
+  if (!finite) latch(epi.status, TT_ERR_NONFINITE);
 }
 
 // Fixed-order reduction of the threads' energy partials into partials[2 cta + {0, 1}] (red:

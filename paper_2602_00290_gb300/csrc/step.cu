@@ -340,7 +340,7 @@ static tt_status randomized_factor(tt_context* ctx, cudaStream_t s, const Src& s
   *RZ_out = RZ;
   if (ws.dry) return TT_OK;
   small_gemm<double, double>(s, R, l, nang, B0, nang, 1, ctx->sketch, ctx->sketch_ell, 1, Op, l, nullptr, nullptr);
-  tt_status st = launch_update<T>(s, ctx->num_sms, src, lp, N, Op, l, EpiPlain<S>{Y, l}, nullptr, nullptr);
+  tt_status st = launch_update<T>(s, ctx->num_sms, src, lp, N, Op, l, EpiPlain<S>{Y, l, &ctx->ctrl->status}, nullptr, nullptr);
   if (st != TT_OK) return st;
   double* RY = nullptr;
   st = run_tsqr_cfg<T>(ycfg, s, ctx->num_sms, SrcRows<S>{Y, l}, LivePattern{nullptr, l, 1, 0}, N, ta, tb, &RY,
@@ -421,7 +421,7 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   tt_status st = small_round(s, ctx->num_sms, job, ws);
   if (st != TT_OK || ws.dry) return st;
   st = launch_update<T>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
-                        EpiPlain<S>{(S*)x->core[0], K1}, nullptr, nullptr);
+                        EpiPlain<S>{(S*)x->core[0], K1, &ctx->ctrl->status}, nullptr, nullptr);
   if (st != TT_OK) return st;
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
   k_commit<S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(d, n1, n2, K1, K2, b.core1, b.core2,
@@ -537,7 +537,8 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     if (st != TT_OK) return st;
   }
   st = launch_update<T>(s, ctx->num_sms, src1, lp1, N, b1.W, K1,
-                        EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps}, part1, &ngrid1);
+                        EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps, &ctx->ctrl->status}, part1,
+                        &ngrid1);
   if (st != TT_OK) return st;
   k_save_ranks<<<1, 32, 0, s>>>(ctx->ctrl); count_launch();
   lp2.r_ptr = &ctx->ctrl->k[2];
@@ -568,7 +569,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   st = small_round(s, ctx->num_sms, j2, ws);
   if (st != TT_OK) return st;
   st = launch_update<T>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
-                        EpiFinal<S>{(S*)I->core[0], K1, b2.vJ, jnew}, part2, &ngrid2);
+                        EpiFinal<S>{(S*)I->core[0], K1, b2.vJ, jnew, &ctx->ctrl->status}, part2, &ngrid2);
   if (st != TT_OK) return st;
   if (p->coupled) {
     st = coupled_t_update(s, const_cast<tt_plan*>(p), jstar, jnew);

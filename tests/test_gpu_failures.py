@@ -1,10 +1,11 @@
 """Failure paths of the C ABI on the GPU, made on the host or by a bounded wait that runs out; no
 test faults, traps or hangs the GPU.
 
-* A NaN written into a core by the host: the step or rounding latches TT_ERR_NONFINITE (the
-  singular values and the norm are non-finite), every index the kernels form from those values
-  stays in range (ranks of NaN sort last), and the context then steps a clean state exactly as
-  the oracle does.
+* A NaN (or Inf) written into a core by the host: the step or rounding latches TT_ERR_NONFINITE
+  (the update pass that writes the new merged core sees the non-finite rows; a non-finite column
+  norm gives no reflector, so the factorisation itself passes over them), every index the kernels
+  form from non-finite values stays in range (ranks of NaN sort last), and the context then steps a
+  clean state exactly as the oracle does.
 * The FP64 Jacobi sweep cap set to 1 (tt_context_set_limits): the SVD is still rotating when it
   stops, TT_ERR_TIMEOUT is latched, and the default cap restores parity.
 * Every grid-wide barrier of the cooperative Jacobi told to wait for one arrival that never comes,
@@ -82,7 +83,7 @@ def test_nan_in_round_latches_nonfinite(tt):
     ctx = tt.Context(0)
     a = random_tt([300, 6, 7], [5, 4], seed=8)
     x = tt.TT.from_cores(a, rcap=[8, 8])
-    x.cores[2][1, 2] = float("inf")
+    x.cores[2][9, 0] = float("inf")  # the last core is [rcap_2 n_2][1]
     tt.tt_round(ctx, x, 1e-8, 8)
     with pytest.raises(tt.TTError) as e:
         ctx.sync()
