@@ -58,8 +58,14 @@ typedef enum { TT_F64 = 0, TT_F32 = 1 } tt_dtype;
 /* Arithmetic of the rounding and contraction kernels.
  * TT_PREC_FP64  : every step in FP64.
  * TT_PREC_MIXED : bulk passes over the merged core in FP32 (FP32 storage of Z allowed),
- *                 R-factor merges, small-core SVDs, norms and the energy check in FP64. */
-typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1 } tt_precision;
+ *                 small-core SVDs, the rank decisions, norms and the energy check in FP64.
+ * TT_PREC_MIXED_3XTF32 : TT_PREC_MIXED with the dense contractions over the merged core on the
+ *                 tensor cores (tcgen05 kind::tf32) in split precision: each FP32 operand is split
+ *                 into its TF32 part and remainder and three products (hi hi, hi lo, lo hi) are
+ *                 summed in the FP32 accumulator, FP32-level products.  Where a pass cannot take the
+ *                 tensor-core kernel (FP64 storage of Z, rank capacities that are not multiples of
+ *                 8, shared memory) it runs the TT_PREC_MIXED kernel. */
+typedef enum { TT_PREC_FP64 = 0, TT_PREC_MIXED = 1, TT_PREC_MIXED_3XTF32 = 2 } tt_precision;
 
 typedef enum { TT_QUAD_GAUSS_LEGENDRE_MU = 0, TT_QUAD_LATLONG_MIDPOINT = 1 } tt_quadrature;
 
@@ -145,9 +151,11 @@ typedef enum {
   TT_TIMER_SMALL = 2,       /* small-core sweep (QRs, Jacobi SVDs, rank decisions)         */
   TT_TIMER_UPDATE = 3,      /* update pass Z_new = Z_sum W (and the fused source step)     */
   TT_TIMER_OTHER = 4,       /* everything else (counted only)                              */
-  TT_TIMER_TSQR_LEAF_SOURCE = 5  /* leaf pass over the source sum (second rounding of tt_step) */
+  TT_TIMER_TSQR_LEAF_SOURCE = 5, /* leaf pass over the source sum (second rounding of tt_step) */
+  TT_TIMER_UPDATE_SOURCE = 6     /* update pass of the second rounding of tt_step (the source sum);
+                                    TT_TIMER_UPDATE then times the first one alone              */
 } tt_timer;
-#define TT_TIMER_COUNT 6
+#define TT_TIMER_COUNT 7
 tt_status tt_context_set_timing(tt_context *ctx, int enable);
 
 /* Replay tt_step as a CUDA graph (enable != 0; default off).  With it on, the first tt_step for a

@@ -26,7 +26,8 @@ TT_ERR_NONFINITE, TT_ERR_TIMEOUT, TT_ERR_UNSUPPORTED, TT_ERR_WORKSPACE = 5, 6, 7
 TT_F64, TT_F32 = 0, 1
 TT_PREC_FP64, TT_PREC_MIXED = 0, 1
 TT_QUAD_GAUSS_LEGENDRE_MU, TT_QUAD_LATLONG_MIDPOINT = 0, 1
-PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED}
+TT_PREC_MIXED_3XTF32 = 2
+PRECISIONS = {"fp64": TT_PREC_FP64, "mixed": TT_PREC_MIXED, "mixed_3xtf32": TT_PREC_MIXED_3XTF32}
 ROUNDINGS = {"tsqr": 0, "gram": 1, "randomized": 2}
 
 EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sync", "tt_workspace_query",
@@ -38,7 +39,7 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_autotune", "tt_context_set_graphs", "tt_tsqr_geometry", "tt_context_set_limits",
            "tt_tc_gemm", "tt_peak_probe")
 TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2}
-TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source")
+TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source", "update_source")
 
 
 class TTError(RuntimeError):

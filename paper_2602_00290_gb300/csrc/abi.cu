@@ -200,6 +200,7 @@ tt_status tt_context_create(tt_context** out, int device, void* stream, size_t w
   ctx->graphs = 0;
   ctx->step_graph = nullptr;
   ctx->graph_replays = ctx->graph_captures = ctx->graph_failures = 0;
+  ctx->tensor_cores = 0;
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   if (cudaMalloc((void**)&ctx->ctrl, sizeof(ttk::DevCtrl)) != cudaSuccess) {
@@ -431,7 +432,7 @@ tt_status tt_dot(tt_context* ctx, const tt_tensor* x, const tt_tensor* y, double
 static tt_status check_round_args(const tt_tensor* x, double tol, int32_t rmax, tt_precision prec) {
   if (!(tol >= 0.0) || !std::isfinite(tol)) return TT_ERR_ARG;
   if (rmax < 1) return TT_ERR_ARG;
-  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return TT_ERR_ARG;
+  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED && prec != TT_PREC_MIXED_3XTF32) return TT_ERR_ARG;
   for (int j = 1; j < x->d; ++j)
     if (rmax > x->rcap[j]) return TT_ERR_CAPACITY;
   return TT_OK;
@@ -443,8 +444,9 @@ tt_status tt_round(tt_context* ctx, tt_tensor* x, double tol, int32_t rmax, tt_p
   if (st == TT_OK) st = check_round_args(x, tol, rmax, prec);
   if (st != TT_OK) return st;
   set_device(ctx);
+  ctx->tensor_cores = (prec == TT_PREC_MIXED_3XTF32);
   return with_ws(ctx, [&](ttk::Bump& ws) {
-    const bool f64 = (x->dtype == TT_F64), mixed = (prec == TT_PREC_MIXED);
+    const bool f64 = (x->dtype == TT_F64), mixed = (prec != TT_PREC_FP64);
     if (f64) return mixed ? ttk::round_impl<double, float>(ctx, x, tol, rmax, ws)
                           : ttk::round_impl<double, double>(ctx, x, tol, rmax, ws);
     return mixed ? ttk::round_impl<float, float>(ctx, x, tol, rmax, ws)
@@ -474,8 +476,9 @@ tt_status tt_step(tt_context* ctx, const tt_plan* plan, tt_tensor* I, double tol
   if (st == TT_OK) st = check_round_args(I, tol, rmax, prec);
   if (st != TT_OK) return st;
   set_device(ctx);
+  ctx->tensor_cores = (prec == TT_PREC_MIXED_3XTF32);
   auto body = [&](ttk::Bump& ws) {
-    const bool f64 = (I->dtype == TT_F64), mixed = (prec == TT_PREC_MIXED);
+    const bool f64 = (I->dtype == TT_F64), mixed = (prec != TT_PREC_FP64);
     if (f64) return mixed ? ttk::step_impl<double, float>(ctx, plan, I, tol, rmax, energy_dev, ws)
                           : ttk::step_impl<double, double>(ctx, plan, I, tol, rmax, energy_dev, ws);
     return mixed ? ttk::step_impl<float, float>(ctx, plan, I, tol, rmax, energy_dev, ws)
@@ -593,14 +596,14 @@ tt_status tt_workspace_query(tt_context* ctx, const tt_plan* plan, const tt_tens
   if (plan) {
     st = check_plan_tensor(plan, x);
     if (st != TT_OK) return st;
-    if (prec == TT_PREC_MIXED)
+    if (prec != TT_PREC_FP64)
       st = (x->dtype == TT_F64) ? ttk::step_impl<double, float>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry)
                                 : ttk::step_impl<float, float>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry);
     else
       st = (x->dtype == TT_F64) ? ttk::step_impl<double, double>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry)
                                 : ttk::step_impl<float, double>(ctx, plan, &tmp, 1e-6, 1, nullptr, dry);
   } else {
-    if (prec == TT_PREC_MIXED)
+    if (prec != TT_PREC_FP64)
       st = (x->dtype == TT_F64) ? ttk::round_impl<double, float>(ctx, &tmp, 1e-6, 1, dry)
                                 : ttk::round_impl<float, float>(ctx, &tmp, 1e-6, 1, dry);
     else

@@ -39,7 +39,8 @@ namespace {
 
 tt_status step_dispatch(tt_context* c, const tt_plan* p, tt_tensor* I, double tol, int rmax, tt_precision prec,
                         ttk::Bump& ws) {
-  const bool f64 = (I->dtype == TT_F64), mixed = (prec == TT_PREC_MIXED);
+  const bool f64 = (I->dtype == TT_F64), mixed = (prec != TT_PREC_FP64);
+  c->tensor_cores = (prec == TT_PREC_MIXED_3XTF32);
   if (f64) return mixed ? ttk::step_impl<double, float>(c, p, I, tol, rmax, nullptr, ws)
                         : ttk::step_impl<double, double>(c, p, I, tol, rmax, nullptr, ws);
   return mixed ? ttk::step_impl<float, float>(c, p, I, tol, rmax, nullptr, ws)
@@ -89,7 +90,7 @@ tt_status tt_batch_create(tt_context* ctx, int32_t nprob, const tt_plan* const* 
                           const double* tol, const int32_t* rmax, tt_precision prec, int32_t nstreams,
                           tt_batch** out) {
   if (!ctx || !out || nprob < 1 || !plans || !states || !tol || !rmax) return TT_ERR_ARG;
-  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return TT_ERR_ARG;
+  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED && prec != TT_PREC_MIXED_3XTF32) return TT_ERR_ARG;
   *out = nullptr;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return TT_ERR_CUDA;
   for (int i = 0; i < nprob; ++i) {

@@ -130,6 +130,7 @@ struct tt_context {
   int graphs;        // tt_step replays a captured CUDA graph of the step (tt_context_set_graphs)
   void* step_graph;  // the captured step and what it depends on (owned; not shared by batch views)
   long graph_replays, graph_captures, graph_failures;  // since the last diagnostics reset
+  int tensor_cores;  // the call in progress runs TT_PREC_MIXED_3XTF32 (tensor-core contractions)
 };
 
 struct tt_plan {

@@ -70,7 +70,7 @@ extern "C" tt_status tt_tsqr_geometry(tt_precision prec, int32_t variant, int32_
                                       int32_t num_sms, int32_t per_sm, int32_t max_leaves, int64_t* out,
                                       int32_t nout) {
   if (!out || nout < 1 || nout > 11 || ncap < 1 || nrows < 1 || num_sms < 1 || variant < 0 ||
-      variant >= ttk::kTsqrVariants || (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED))
+      variant >= ttk::kTsqrVariants || (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED && prec != TT_PREC_MIXED_3XTF32))
     return TT_ERR_ARG;
   int64_t g[11] = {};
   const tt_status st = (prec == TT_PREC_FP64)

@@ -7,7 +7,8 @@
 
 namespace ttk {
 
-enum TimerCat { kTsqrLeaf = 0, kTsqrMerge = 1, kSmall = 2, kUpdate = 3, kOther = 4, kTsqrLeafSrc = 5, kNumCat = 6 };
+enum TimerCat { kTsqrLeaf = 0, kTsqrMerge = 1, kSmall = 2, kUpdate = 3, kOther = 4, kTsqrLeafSrc = 5, kUpdateSrc = 6,
+                kNumCat = 7 };
 
 struct Instr {
   bool timing = false;

@@ -3,12 +3,14 @@
 // device memory (tensor rank arrays and the context control block).
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 
 #include "bigpass.cuh"
 #include "gram.cuh"
 #include "rand.cuh"
 #include "small.cuh"
 #include "step.cuh"
+#include "tc_update.cuh"
 #include "tsqr_rs.cuh"
 #include "tune.cuh"
 
@@ -192,7 +194,7 @@ struct StencilOf<SrcStencil<S>> {
 template <class Epi, typename S>
 static tt_status launch_update_blk(cudaStream_t s, int num_sms, const SrcStencil<S>& src, LivePattern lp,
                                    long nrows, const double* W, int kcap, const Epi& epi, double* partials,
-                                   long* grid_out) {
+                                   long* grid_out, int cat) {
   constexpr int TM = UpdTM<float>::value;
   if (((size_t)src.ldz * sizeof(S)) % 16 != 0 || ((size_t)src.Z % 16) != 0 || src.nax < 1 || src.rcap != lp.rcap)
     return TT_ERR_UNSUPPORTED;
@@ -206,17 +208,25 @@ static tt_status launch_update_blk(cudaStream_t s, int num_sms, const SrcStencil
   long grid = (long)num_sms * occ;
   if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
   if (grid_out) *grid_out = grid;
-  TimerScope scope(kUpdate, s);
+  TimerScope scope(cat, s);
   kern<<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
+// The update pass of a rounding: the tensor-core kernel (ctx->tensor_cores, FP32 storage of the
+// stencil source) where it takes the pass, else the FP32 kernel over staged row blocks, else the
+// generic kernel.
 template <typename T, class Src, class Epi>
-static tt_status launch_update(cudaStream_t s, int num_sms, const Src& src, LivePattern lp, long nrows,
-                               const double* W, int kcap, const Epi& epi, double* partials, long* grid_out) {
+static tt_status launch_update(const tt_context* ctx, cudaStream_t s, int num_sms, const Src& src, LivePattern lp,
+                               long nrows, const double* W, int kcap, const Epi& epi, double* partials,
+                               long* grid_out, int cat = kUpdate) {
   constexpr int TM = UpdTM<T>::value;
+  if constexpr (sizeof(T) == 4 && std::is_same<Src, SrcStencil<float>>::value) {
+    if (ctx->tensor_cores && update_tc_fits(src, lp, kcap, ctx->smem_optin))
+      return launch_update_tc(s, num_sms, src, lp, nrows, W, kcap, epi, partials, grid_out, cat);
+  }
   if constexpr (sizeof(T) == 4 && StencilOf<Src>::value) {
-    const tt_status bst = launch_update_blk(s, num_sms, src, lp, nrows, W, kcap, epi, partials, grid_out);
+    const tt_status bst = launch_update_blk(s, num_sms, src, lp, nrows, W, kcap, epi, partials, grid_out, cat);
     if (bst != TT_ERR_UNSUPPORTED) return bst;
   }
   // Staging the stencil rows takes shared memory: keep it when it costs no resident CTA or
@@ -238,7 +248,7 @@ static tt_status launch_update(cudaStream_t s, int num_sms, const Src& src, Live
   const long grid = update_grid<T, TM, Src, Epi>(num_sms, lp.ncap(), kcap, nrows, stage);
   if (grid < 1) return TT_ERR_CUDA;
   if (grid_out) *grid_out = grid;
-  TimerScope scope(kUpdate, s);
+  TimerScope scope(cat, s);
   k_update<T, TM, Src, Epi><<<(unsigned)grid, 256, smem, s>>>(src2, lp, nrows, W, kcap, epi, partials); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
@@ -340,7 +350,7 @@ static tt_status randomized_factor(tt_context* ctx, cudaStream_t s, const Src& s
   *RZ_out = RZ;
   if (ws.dry) return TT_OK;
   small_gemm<double, double>(s, R, l, nang, B0, nang, 1, ctx->sketch, ctx->sketch_ell, 1, Op, l, nullptr, nullptr);
-  tt_status st = launch_update<T>(s, ctx->num_sms, src, lp, N, Op, l, EpiPlain<S>{Y, l, &ctx->ctrl->status}, nullptr, nullptr);
+  tt_status st = launch_update<T>(ctx, s, ctx->num_sms, src, lp, N, Op, l, EpiPlain<S>{Y, l, &ctx->ctrl->status}, nullptr, nullptr);
   if (st != TT_OK) return st;
   double* RY = nullptr;
   st = run_tsqr_cfg<T>(ycfg, s, ctx->num_sms, SrcRows<S>{Y, l}, LivePattern{nullptr, l, 1, 0}, N, ta, tb, &RY,
@@ -420,7 +430,7 @@ tt_status round_impl(tt_context* ctx, tt_tensor* x, double tol, int rmax, Bump& 
   job.RZ = RZ;
   tt_status st = small_round(s, ctx->num_sms, job, ws);
   if (st != TT_OK || ws.dry) return st;
-  st = launch_update<T>(s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
+  st = launch_update<T>(ctx, s, ctx->num_sms, SrcRows<S>{(const S*)x->core[0], K1}, lp, N, b.W, K1,
                         EpiPlain<S>{(S*)x->core[0], K1, &ctx->ctrl->status}, nullptr, nullptr);
   if (st != TT_OK) return st;
   const long tot = (long)K1 * n1 * K2 + (long)K2 * n2;
@@ -536,7 +546,7 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
     st = coupled_t_dagger(s, const_cast<tt_plan*>(p), jstar);  // the plan holds the material state
     if (st != TT_OK) return st;
   }
-  st = launch_update<T>(s, ctx->num_sms, src1, lp1, N, b1.W, K1,
+  st = launch_update<T>(ctx, s, ctx->num_sms, src1, lp1, N, b1.W, K1,
                         EpiSource<S>{Zsrc, K1 + 1, b1.vJ, p->acoef, p->scoef, p->eps, &ctx->ctrl->status}, part1,
                         &ngrid1);
   if (st != TT_OK) return st;
@@ -568,8 +578,9 @@ tt_status step_impl(tt_context* ctx, const tt_plan* p, tt_tensor* I, double tol,
   j2.vJ = b2.vJ;
   st = small_round(s, ctx->num_sms, j2, ws);
   if (st != TT_OK) return st;
-  st = launch_update<T>(s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
-                        EpiFinal<S>{(S*)I->core[0], K1, b2.vJ, jnew, &ctx->ctrl->status}, part2, &ngrid2);
+  st = launch_update<T>(ctx, s, ctx->num_sms, SrcRows<S>{Zsrc, K1 + 1}, lp2, N, b2.W, K1,
+                        EpiFinal<S>{(S*)I->core[0], K1, b2.vJ, jnew, &ctx->ctrl->status}, part2, &ngrid2,
+                        kUpdateSrc);
   if (st != TT_OK) return st;
   if (p->coupled) {
     st = coupled_t_update(s, const_cast<tt_plan*>(p), jstar, jnew);

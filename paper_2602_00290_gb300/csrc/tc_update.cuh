@@ -1,0 +1,246 @@
+// Update pass over the stencil sum on the tensor cores (mixed path, FP32 storage of the merged
+// core): the GEMM of k_update_blk, Z_new = C W_0 + sum_a (D_L,a WL_a + D_H,a WH_a), as tcgen05
+// kind::tf32 MMAs in split precision (3xTF32) with the FP32 accumulator in tensor memory.
+//
+// A tile is 128 rows.  The centre rows C and their lower and upper neighbours along every axis are
+// staged by cp.async straight into the K-major core-matrix layout of the A operand (K = the
+// stencil sum's width, (1 + 2 d_X) rcap), the neighbours are turned into the differences
+// D_L = C - L and D_H = H - C in place, and every value is split into its TF32 part and the FP32
+// remainder.  The combined weights (formed once per CTA in FP64, as in k_update_blk) are the B
+// operand, split the same way.  One thread issues three MMAs per K step of 8 (hi hi, hi lo, lo hi);
+// the 128 x N accumulator is read back by the four warps (a row per thread), the inflow columns
+// are added per row, and the update epilogue (energy dot, source or final scaling, non-finite
+// check) runs on the tile as for the other update kernels.
+#pragma once
+#include "tc.cuh"
+#include "update_blk.cuh"
+
+namespace ttk {
+
+constexpr int kTcRows = 128;  // rows per tile: the M of one MMA, one TMEM lane per row
+
+// Output columns of the tensor-core update: kcap rounded up to a multiple of 16 (the MMA's N).
+__host__ __device__ inline int update_tc_n(int kcap) { return (kcap + 15) & ~15; }
+
+// Shared memory: A hi and lo [128][K] and B hi and lo [N][K] (FP32, K-major core matrices),
+// inflow weights [nbc][N], row scalars [3][128] (FP64), vJ [N], row flags [128].  The output tile
+// [128][N + 1] reuses A lo once the MMAs of a tile are done, the energy partials reuse A hi.
+__host__ __device__ inline size_t update_tc_smem_bytes(int K, int N, int nbc) {
+  size_t b = sizeof(float) * (2 * (size_t)kTcRows * K + 2 * (size_t)N * K + (size_t)nbc * N);
+  b = (b + 7) & ~(size_t)7;
+  return b + sizeof(double) * 3 * kTcRows + sizeof(float) * (size_t)N + sizeof(unsigned) * kTcRows;
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, LivePattern lp, long nrows,
+                                                      const double* __restrict__ W, int kcap, Epi epi,
+                                                      double* __restrict__ partials) {
+  extern __shared__ __align__(1024) unsigned char tcu_smem[];
+  const int rcap = src.rcap, nb = 1 + 2 * src.nax, nbc = lp.nextra;
+  const int K = nb * rcap, N = update_tc_n(kcap), ldo = N + 1;
+  const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
+  const int rq = r < rcap ? r : rcap;  // live columns of each Z block
+  float* Ahi = reinterpret_cast<float*>(tcu_smem);
+  float* Alo = Ahi + (size_t)kTcRows * K;
+  float* Bhi = Alo + (size_t)kTcRows * K;
+  float* Blo = Bhi + (size_t)N * K;
+  float* Wbc = Blo + (size_t)N * K;  // [nbc][N]
+  size_t off = sizeof(float) * (2 * (size_t)kTcRows * K + 2 * (size_t)N * K + (size_t)nbc * N);
+  off = (off + 7) & ~(size_t)7;
+  double* rowv = reinterpret_cast<double*>(tcu_smem + off);  // [3][128]
+  float* vJs = reinterpret_cast<float*>(rowv + 3 * kTcRows);  // [N]
+  unsigned* fl = reinterpret_cast<unsigned*>(vJs + N);        // [128]
+  float* Os = Alo;                                            // [128][N + 1] after a tile's MMAs
+  double* red = reinterpret_cast<double*>(Ahi);               // energy partials after the last tile
+  __shared__ uint64_t bar;
+  __shared__ uint32_t tbase;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double* vJ = epi_vj(epi);
+  const uint32_t ncols = tc::tmem_cols(N);
+  if (warp == 0) {
+    tc::tmem_alloc(&tbase, ncols);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) tc::mbar_init(&bar, 1);
+
+  // combined weights B[n][k] for k = b rcap + q (FP64 sums as in k_update_blk), split in TF32 parts
+  for (int i = tid; i < N * K; i += blockDim.x) {
+    const int n = i / K, kk = i - (i / K) * K;
+    const int b = kk / rcap, q = kk - (kk / rcap) * rcap;
+    double sum = 0.0;
+    if (n < kcap && q < rq) {
+      if (b == 0) {
+        sum = W[(size_t)q * kcap + n];
+      } else {
+        for (int t = 1; t <= src.nterm; ++t) {
+          const int ax = src.axis[t - 1];
+          if (b != 1 + 2 * ax && b != 2 + 2 * ax) continue;
+          double cL, cH;
+          blk_coefs(src, t, cL, cH);
+          const double cf = (b == 1 + 2 * ax) ? cL : cH;
+          if (cf != 0.0) sum += cf * W[(size_t)(t * rcap + q) * kcap + n];
+        }
+      }
+    }
+    const float f = (float)sum, h = tc::tf32_hi(f);
+    const uint32_t o = tc::kmajor_off(n, kk, K) >> 2;
+    Bhi[o] = h;
+    Blo[o] = f - h;
+  }
+  for (int i = tid; i < nbc * N; i += blockDim.x) {
+    const int e = i / N, n = i - (i / N) * N;
+    const int c = (src.nterm + 1) * rcap + e;
+    Wbc[i] = (n < kcap && lp.live(c, r)) ? (float)W[(size_t)c * kcap + n] : 0.0f;
+  }
+  for (int n = tid; n < N; n += blockDim.x) vJs[n] = (vJ && n < kcap) ? (float)vJ[n] : 0.0f;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tbase;
+  const uint32_t idesc = tc::idesc_tf32(kTcRows, N);
+  const uint32_t lbo = 128, sbo = (uint32_t)(K / 4) * 128u;
+  const int gpr = rcap / 4;  // 16-byte granules of a row block
+  const long ntiles = (nrows + kTcRows - 1) / kTcRows;
+  uint32_t phase = 0;
+  bool ok = true;
+  double e0t = 0.0, e1t = 0.0;
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long row0 = tile * kTcRows;
+    __syncthreads();  // the previous tile's epilogue is done with the output tile and row scalars
+    fl[tid] = (row0 + tid < nrows) ? src.row_flags(row0 + tid) : 0u;
+    __syncthreads();
+    // every granule of the tile's row blocks in flight at once, into the A layout; rows outside
+    // the core and neighbours the row does not have are zero-filled.  Eight consecutive threads
+    // take one granule of eight consecutive rows (one 128-byte core matrix: no bank conflict), a
+    // warp four granules of them (whole 32-byte sectors of every row it reads)
+    const int per_block = kTcRows * gpr;
+    for (int i = tid; i < nb * per_block; i += blockDim.x) {
+      const int b = i / per_block, rem = i - b * per_block;
+      const int r8 = rem >> 3, g = r8 % gpr, m = (r8 / gpr) * 8 + (rem & 7);
+      long k = row0 + m;
+      bool okr = k < nrows;
+      if (b > 0) {
+        const int ax = (b - 1) >> 1;
+        const bool upper = ((b - 1) & 1) != 0;
+        okr = okr && ((fl[m] >> (2 * ax + (upper ? 1 : 0))) & 1u);
+        k += upper ? src.stride[ax] : -src.stride[ax];
+      }
+      float* dst = Ahi + (tc::kmajor_off(m, b * rcap + 4 * g, K) >> 2);
+      const float* from = okr ? src.Z + k * src.ldz + (size_t)4 * g : src.Z;
+      cp_async16(dst, from, okr ? 16 : 0);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // neighbours to differences with the centre rows (L -> C - L, H -> H - C), then every value
+    // to its TF32 part (A hi) and remainder (A lo); a thread takes 4 consecutive K values of a
+    // row (16-byte vectors; a warp's 32 rows fall on distinct banks)
+    for (int i = tid; i < kTcRows * gpr; i += blockDim.x) {
+      const int g = i / kTcRows, m = i - g * kTcRows;
+      const uint32_t oc = tc::kmajor_off(m, 4 * g, K) >> 2;
+      const float4 c = *reinterpret_cast<const float4*>(Ahi + oc);
+      for (int b = 1; b < nb; ++b) {
+        const uint32_t o = tc::kmajor_off(m, b * rcap + 4 * g, K) >> 2;
+        float4 v = *reinterpret_cast<const float4*>(Ahi + o);
+        if (b & 1) {
+          v = make_float4(c.x - v.x, c.y - v.y, c.z - v.z, c.w - v.w);
+        } else {
+          v = make_float4(v.x - c.x, v.y - c.y, v.z - c.z, v.w - c.w);
+        }
+        const float4 h = make_float4(tc::tf32_hi(v.x), tc::tf32_hi(v.y), tc::tf32_hi(v.z), tc::tf32_hi(v.w));
+        *reinterpret_cast<float4*>(Ahi + o) = h;
+        *reinterpret_cast<float4*>(Alo + o) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+      }
+      const float4 h = make_float4(tc::tf32_hi(c.x), tc::tf32_hi(c.y), tc::tf32_hi(c.z), tc::tf32_hi(c.w));
+      *reinterpret_cast<float4*>(Ahi + oc) = h;
+      *reinterpret_cast<float4*>(Alo + oc) = make_float4(c.x - h.x, c.y - h.y, c.z - h.z, c.w - h.w);
+    }
+    tc::fence_smem_to_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+      for (int s = 0; s < K / 8; ++s) {
+        const uint32_t so = 256u * (uint32_t)s;
+        const uint64_t dah = tc::smem_desc(ah + so, lbo, sbo), dal = tc::smem_desc(al + so, lbo, sbo);
+        const uint64_t dbh = tc::smem_desc(bh + so, lbo, sbo), dbl = tc::smem_desc(bl + so, lbo, sbo);
+        tc::mma_tf32(tmem, dal, dbh, idesc, s > 0 ? 1u : 0u);  // small terms first
+        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
+        tc::mma_tf32(tmem, dah, dbh, idesc, 1u);
+      }
+      tc::mma_commit(&bar);
+    }
+    ok = __syncthreads_and(tc::mbar_wait(&bar, phase)) != 0;
+    if (!ok) break;
+    phase ^= 1u;
+    tc::fence_after_sync();
+    // accumulator rows to the output tile (A lo is free now), plus the inflow columns
+    {
+      const int m = 32 * warp + lane;
+      const unsigned f = fl[m];
+      for (int c0 = 0; c0 < N; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        tc::tmem_wait_ld();
+        for (int e = 0; e < nbc; ++e) {
+          const int tt = src.bc_term[e], ax = src.axis[tt];
+          const bool lower_face = src.w[tt] > 0;
+          const bool at_face = lower_face ? !((f >> (2 * ax)) & 1u) : !((f >> (2 * ax + 1)) & 1u);
+          const float val = (at_face && row0 + m < nrows) ? (float)src.bcval[e * src.G + (int)(f >> 8)] : 0.0f;
+          if (val != 0.0f) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (c0 + j < N) v[j] += val * Wbc[e * N + c0 + j];
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+          if (c0 + j < N) Os[(size_t)m * ldo + c0 + j] = v[j];
+      }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    update_epilogue<float, kTcRows>(epi, Os, ldo, kcap, vJs, vJ != nullptr, rowv, row0, nrows, e0t, e1t);
+  }
+  if (!ok) {
+    // the MMAs of the tile may still be running: wait for them again (bounded) before the
+    // accumulator is released, and report the timeout
+    if (tid == 0) latch(epi.status, TT_ERR_TIMEOUT);
+    (void)__syncthreads_and(tc::mbar_wait(&bar, phase));
+  }
+  if (partials) update_partials(red, e0t, e1t, partials);
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, ncols);
+  }
+}
+
+// Whether the tensor-core update takes a pass: FP32 storage with rows of whole MMA K steps
+// (rcap a multiple of 8, 16-byte aligned rows), at most 256 output columns, and its shared memory.
+inline bool update_tc_fits(const SrcStencil<float>& src, const LivePattern& lp, int kcap, int smem_optin) {
+  if (src.rcap % 8 != 0 || src.ldz != src.rcap || ((size_t)src.Z % 16) != 0 || src.rcap != lp.rcap || src.nax < 1)
+    return false;
+  if (kcap < 1 || update_tc_n(kcap) > 256) return false;
+  const int K = (1 + 2 * src.nax) * src.rcap;
+  return update_tc_smem_bytes(K, update_tc_n(kcap), lp.nextra) <= (size_t)smem_optin;
+}
+
+template <class Epi>
+tt_status launch_update_tc(cudaStream_t s, int num_sms, const SrcStencil<float>& src, LivePattern lp, long nrows,
+                           const double* W, int kcap, const Epi& epi, double* partials, long* grid_out,
+                           int cat = kUpdate) {
+  const int K = (1 + 2 * src.nax) * src.rcap, N = update_tc_n(kcap);
+  const size_t smem = update_tc_smem_bytes(K, N, lp.nextra);
+  if (const tt_status a = smem_optin(k_update_tc<Epi>, smem); a != TT_OK) return a;
+  const long ntiles = (nrows + kTcRows - 1) / kTcRows;
+  long grid = num_sms;  // one CTA per SM: its shared memory and accumulator stay resident
+  if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
+  if (grid_out) *grid_out = grid;
+  TimerScope scope(cat, s);
+  k_update_tc<Epi><<<(unsigned)grid, 128, smem, s>>>(src, lp, nrows, W, kcap, epi, partials);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+}  // namespace ttk

@@ -7,7 +7,7 @@
 
 namespace {
 
-int esize_of(tt_precision prec) { return prec == TT_PREC_MIXED ? 4 : 8; }
+int esize_of(tt_precision prec) { return prec == TT_PREC_FP64 ? 8 : 4; }
 
 // Default leaf wave of the passes over the merged core (the cap tsqr_cfg clamps to).
 int default_wave(const tt_context* ctx, int esize) { return (esize == 8 ? 2 : 3) * ctx->num_sms; }
@@ -47,7 +47,7 @@ struct Scratch {
 extern "C" {
 
 tt_status tt_context_set_tsqr(tt_context* ctx, tt_precision prec, int32_t ncap, int32_t variant, int32_t leaves) {
-  if (!ctx || (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED)) return TT_ERR_ARG;
+  if (!ctx || (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED && prec != TT_PREC_MIXED_3XTF32)) return TT_ERR_ARG;
   ttk::TsqrTune* tab = ttk::tune_of(ctx);
   if (ncap <= 0) {
     tab->m.clear();
@@ -62,7 +62,7 @@ tt_status tt_context_set_tsqr(tt_context* ctx, tt_precision prec, int32_t ncap, 
 
 tt_status tt_context_get_tsqr(const tt_context* ctx, tt_precision prec, int32_t ncap, int32_t* variant,
                               int32_t* leaves) {
-  if (!ctx || ncap <= 0 || (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED)) return TT_ERR_ARG;
+  if (!ctx || ncap <= 0 || (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED && prec != TT_PREC_MIXED_3XTF32)) return TT_ERR_ARG;
   const int es = esize_of(prec);
   const ttk::TsqrCfg cfg = ttk::resolve_tsqr(ctx, es, ncap, default_wave(ctx, es));
   if (variant) *variant = cfg.variant;
@@ -73,7 +73,7 @@ tt_status tt_context_get_tsqr(const tt_context* ctx, tt_precision prec, int32_t 
 tt_status tt_autotune(tt_context* ctx, const tt_plan* plan, const tt_tensor* I, double tol, int32_t rmax,
                       tt_precision prec, int32_t steps, int32_t* chosen, float* ms) {
   if (!ctx || !plan || !I || !I->rank || steps < 1 || steps > 64) return TT_ERR_ARG;
-  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED) return TT_ERR_ARG;
+  if (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED && prec != TT_PREC_MIXED_3XTF32) return TT_ERR_ARG;
   if (ctx->rounding != TT_ROUND_TSQR) return TT_ERR_UNSUPPORTED;
   if (I->d != plan->d || I->n[0] != plan->nrow || I->rcap[1] <= 0) return TT_ERR_SHAPE;
   if (cudaSetDevice(ctx->device) != cudaSuccess) return TT_ERR_CUDA;

@@ -22,7 +22,8 @@ from paper_2602_00290_gb300.workloads import plane_config1, random_tt  # noqa: E
 
 TIE = 1e-9
 PINNED = {"fp64": {"transport": ("column", 304), "source": ("rowsplit", 304)},
-          "mixed": {"transport": ("column_dense", 608), "source": ("rowsplit", 456)}}
+          "mixed": {"transport": ("column_dense", 608), "source": ("rowsplit", 456)},
+          "mixed_3xtf32": {"transport": ("column_dense", 608), "source": ("rowsplit", 456)}}
 
 
 @pytest.fixture(scope="module")
@@ -55,7 +56,7 @@ def sampled_rows(cores, rows):
     return z @ right.reshape(right.shape[0], -1)
 
 
-@pytest.mark.parametrize("prec,dtype", [("fp64", "f64"), ("mixed", "f32"), ("mixed", "f64")])
+@pytest.mark.parametrize("prec,dtype", [("fp64", "f64"), ("mixed", "f32"), ("mixed", "f64"), ("mixed_3xtf32", "f32")])
 def test_full_size_step_matches_oracle(tt, case, prec, dtype):
     wl, coef, a, ref, info, rows = case
     ctx = tt.Context(0)
