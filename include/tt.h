@@ -192,7 +192,10 @@ tt_status tt_context_set_sketch(tt_context *ctx, const double *omega_dev, int32_
  *   variant 0: one thread per column (the default; at most 256 threads, i.e. ncap <= 256);
  *   variant 1: four lanes per column, each holding a quarter of the rows of a block (4 ncap <= 1024);
  *   variant 2: FP32 only, one thread per column over 32-row blocks with registers held so that
- *              four CTAs share an SM (ncap <= 160).
+ *              four CTAs share an SM (ncap <= 160);
+ *   variant 3: FP32 only, blocked: 256-row blocks (a row per thread) held in tensor memory,
+ *              32-column panels factored with block-wide reductions and their compact-WY block
+ *              reflector applied to the trailing columns at once; one CTA per SM (ncap <= 224).
  * A variant that cannot take the shape runs variant 0.  The variant picks the leaf kernel; the
  * merge tree over the leaves' R factors runs four lanes per column in every variant when
  * 4 ncap <= 1024.  leaves = cap on the TSQR leaves: <= 0 gives the default wave (2 CTAs per SM for

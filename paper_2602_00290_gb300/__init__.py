@@ -38,7 +38,7 @@ EXPORTS = ("tt_status_string", "tt_context_create", "tt_context_destroy", "tt_sy
            "tt_internal_ranks", "tt_context_set_sketch", "tt_context_set_tsqr", "tt_context_get_tsqr",
            "tt_autotune", "tt_context_set_graphs", "tt_tsqr_geometry", "tt_context_set_limits",
            "tt_tc_gemm", "tt_peak_probe")
-TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2}
+TSQR_VARIANTS = {"column": 0, "rowsplit": 1, "column_dense": 2, "blocked": 3}
 TIMER_NAMES = ("tsqr_leaf", "tsqr_merge", "small", "update", "other", "tsqr_leaf_source", "update_source")
 
 

@@ -2,6 +2,7 @@
 // functions the launchers use (tsqr_split, tsqr_max_leaves, the shared-memory layouts), so that
 // it can be checked without a GPU against the buffers a step sizes.
 #include "bigpass.cuh"
+#include "tsqr_blk.cuh"
 #include "tsqr_rs.cuh"
 #include "tune.cuh"
 
@@ -14,10 +15,17 @@ tt_status geometry(int variant, int ncap, long nrows, int num_sms, int per_sm, i
   const int rs_threads = ttk::tsqr_rs_threads<4>(ncap);
   if (variant == ttk::kTsqrColumnDense && (sizeof(T) != 4 || col_threads > 160)) variant = ttk::kTsqrColumn;
   if (variant == ttk::kTsqrRowSplit && rs_threads > 1024) variant = ttk::kTsqrColumn;
+  if (variant == ttk::kTsqrBlocked && (sizeof(T) != 4 || ncap > 224)) variant = ttk::kTsqrColumn;
   int br, threads;
   size_t smem;
   long cap2 = 0;
-  if (variant == ttk::kTsqrRowSplit) {
+  if (variant == ttk::kTsqrBlocked) {
+    // one CTA per SM (the block takes an SM's tensor memory), shared memory of the stencil source
+    br = ttk::kBlkRows;
+    threads = ttk::kBlkRows;
+    smem = ttk::tsqr_blk_smem_bytes<ttk::SrcStencil<float>>(ncap);
+    per_sm = 1;
+  } else if (variant == ttk::kTsqrRowSplit) {
     br = kBR;
     threads = rs_threads;
     smem = ttk::tsqr_rs_smem_bytes<T, kBR, 4>(ncap);

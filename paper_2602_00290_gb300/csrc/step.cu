@@ -11,6 +11,7 @@
 #include "small.cuh"
 #include "step.cuh"
 #include "tc_update.cuh"
+#include "tsqr_blk.cuh"
 #include "tsqr_rs.cuh"
 #include "tune.cuh"
 
@@ -283,6 +284,8 @@ inline tt_status run_tsqr_cfg(const TsqrCfg& cfg, cudaStream_t s, int num_sms, c
   if constexpr (sizeof(T) == 4) {
     if (cfg.variant == kTsqrColumnDense)
       return run_tsqr<T, 32, 160, 4>(s, num_sms, src, lp, nrows, cfg.leaves, ws_a, ws_b, Rfinal, leaf_cat);
+    if (cfg.variant == kTsqrBlocked)
+      return run_tsqr_blk(s, num_sms, src, lp, nrows, cfg.leaves, ws_a, ws_b, Rfinal, leaf_cat);
   }
   return run_tsqr<T, BR>(s, num_sms, src, lp, nrows, cfg.leaves, ws_a, ws_b, Rfinal, leaf_cat);
 }

@@ -10,10 +10,11 @@
 // One kind::tf32 MMA consumes K = 8, i.e. two core matrices along K, so step s of K starts 256 s
 // bytes further.
 //
-// Split-precision products (3xTF32): x = hi + lo with hi = x rounded to TF32 (round to nearest,
-// ties away) and lo = x - hi (exact in FP32); a b ~ hi_a hi_b + hi_a lo_b + lo_a hi_b, each product
-// exact in the FP32 accumulator's 24 bits, the dropped lo_a lo_b and the TF32 truncation of lo
-// below 2^-22 |a b|: FP32-level products on the tensor pipe.
+// Split-precision products (3xTF32): x ~ hi + lo with hi = x rounded to TF32 (round to nearest,
+// ties away) and lo = x - hi rounded to TF32 as well (the tensor core truncates its operands to
+// TF32, which would otherwise bias every remainder toward zero); a b ~ hi_a hi_b + hi_a lo_b +
+// lo_a hi_b, each product exact in the FP32 accumulator's 24 bits, the dropped lo_a lo_b and the
+// rounding of lo below about 2^-23 |a b|: FP32-level products on the tensor pipe.
 #pragma once
 #include <stdint.h>
 
@@ -123,6 +124,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// Warp-wide: store 32 consecutive FP32 columns of each lane of this warp's quarter of TMEM.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};\n" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])),
+      "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])),
+      "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+      "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+      "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+      "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+      "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+      "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
 
 // x rounded to TF32 (round to nearest, ties away from zero), as an FP32 bit pattern.
 __device__ __forceinline__ float tf32_hi(float x) {

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(long M, int N, int K, const flo
       const float h = tc::tf32_hi(a);
       const uint32_t o = tc::kmajor_off(r, k, KT) >> 2;
       Ahi[o] = h;
-      Alo[o] = a - h;
+      Alo[o] = tc::tf32_hi(a - h);
     }
     for (int i = tid; i < N * KT; i += 128) {
       const int r = i / KT, k = i - (i / KT) * KT;
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm(long M, int N, int K, const flo
       const float h = tc::tf32_hi(b);
       const uint32_t o = tc::kmajor_off(r, k, KT) >> 2;
       Bhi[o] = h;
-      Blo[o] = b - h;
+      Blo[o] = tc::tf32_hi(b - h);
     }
     tc::fence_smem_to_async();
     __syncthreads();

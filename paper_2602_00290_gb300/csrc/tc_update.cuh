@@ -6,11 +6,14 @@
 // staged by cp.async straight into the K-major core-matrix layout of the A operand (K = the
 // stencil sum's width, (1 + 2 d_X) rcap), the neighbours are turned into the differences
 // D_L = C - L and D_H = H - C in place, and every value is split into its TF32 part and the FP32
-// remainder.  The combined weights (formed once per CTA in FP64, as in k_update_blk) are the B
-// operand, split the same way.  One thread issues three MMAs per K step of 8 (hi hi, hi lo, lo hi);
-// the 128 x N accumulator is read back by the four warps (a row per thread), the inflow columns
-// are added per row, and the update epilogue (energy dot, source or final scaling, non-finite
-// check) runs on the tile as for the other update kernels.
+// remainder (itself rounded to TF32, so that the tensor core's truncation of its operands adds no
+// bias).  The combined weights (formed once per CTA in FP64, as in k_update_blk) are the B operand,
+// split the same way.  One thread issues three MMAs per K step of 8 (lo hi, hi lo, hi hi).  The K
+// steps are spread over several accumulators in tensor memory, a few steps each, because the
+// tensor core's FP32 accumulation is not rounded to nearest: its error grows with the number of
+// MMAs summed into one accumulator.  The four warps read the accumulators back (a row per thread)
+// and add them in FP32, the inflow columns are added per row, and the update epilogue (energy dot,
+// source or final scaling, non-finite check) runs on the tile as for the other update kernels.
 #pragma once
 #include "tc.cuh"
 #include "update_blk.cuh"
@@ -21,6 +24,13 @@ constexpr int kTcRows = 128;  // rows per tile: the M of one MMA, one TMEM lane 
 
 // Output columns of the tensor-core update: kcap rounded up to a multiple of 16 (the MMA's N).
 __host__ __device__ inline int update_tc_n(int kcap) { return (kcap + 15) & ~15; }
+// K steps (of 8) summed into one accumulator: as few as the 256 tensor-memory columns allow for
+// the ceil(K / 8 / steps) accumulators of N columns each.
+__host__ __device__ inline int update_tc_steps_per_acc(int K, int N) {
+  const int ksteps = K / 8;
+  const int s = (ksteps * N + 255) / 256;
+  return s < 1 ? 1 : s;
+}
 
 // Shared memory: A hi and lo [128][K] and B hi and lo [N][K] (FP32, K-major core matrices),
 // inflow weights [nbc][N], row scalars [3][128] (FP64), vJ [N], row flags [128].  The output tile
@@ -38,6 +48,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
   extern __shared__ __align__(1024) unsigned char tcu_smem[];
   const int rcap = src.rcap, nb = 1 + 2 * src.nax, nbc = lp.nextra;
   const int K = nb * rcap, N = update_tc_n(kcap), ldo = N + 1;
+  const int spa = update_tc_steps_per_acc(K, N), nacc = (K / 8 + spa - 1) / spa;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
   const int rq = r < rcap ? r : rcap;  // live columns of each Z block
   float* Ahi = reinterpret_cast<float*>(tcu_smem);
@@ -56,7 +67,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
   __shared__ uint32_t tbase;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double* vJ = epi_vj(epi);
-  const uint32_t ncols = tc::tmem_cols(N);
+  const uint32_t ncols = tc::tmem_cols(nacc * N);
   if (warp == 0) {
     tc::tmem_alloc(&tbase, ncols);
     tc::tmem_relinquish();
@@ -85,7 +96,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
     const float f = (float)sum, h = tc::tf32_hi(f);
     const uint32_t o = tc::kmajor_off(n, kk, K) >> 2;
     Bhi[o] = h;
-    Blo[o] = f - h;
+    Blo[o] = tc::tf32_hi(f - h);
   }
   for (int i = tid; i < nbc * N; i += blockDim.x) {
     const int e = i / N, n = i - (i / N) * N;
@@ -148,11 +159,13 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
         }
         const float4 h = make_float4(tc::tf32_hi(v.x), tc::tf32_hi(v.y), tc::tf32_hi(v.z), tc::tf32_hi(v.w));
         *reinterpret_cast<float4*>(Ahi + o) = h;
-        *reinterpret_cast<float4*>(Alo + o) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        *reinterpret_cast<float4*>(Alo + o) = make_float4(tc::tf32_hi(v.x - h.x), tc::tf32_hi(v.y - h.y),
+                                                          tc::tf32_hi(v.z - h.z), tc::tf32_hi(v.w - h.w));
       }
       const float4 h = make_float4(tc::tf32_hi(c.x), tc::tf32_hi(c.y), tc::tf32_hi(c.z), tc::tf32_hi(c.w));
       *reinterpret_cast<float4*>(Ahi + oc) = h;
-      *reinterpret_cast<float4*>(Alo + oc) = make_float4(c.x - h.x, c.y - h.y, c.z - h.z, c.w - h.w);
+      *reinterpret_cast<float4*>(Alo + oc) = make_float4(tc::tf32_hi(c.x - h.x), tc::tf32_hi(c.y - h.y),
+                                                         tc::tf32_hi(c.z - h.z), tc::tf32_hi(c.w - h.w));
     }
     tc::fence_smem_to_async();
     __syncthreads();
@@ -163,9 +176,10 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
         const uint32_t so = 256u * (uint32_t)s;
         const uint64_t dah = tc::smem_desc(ah + so, lbo, sbo), dal = tc::smem_desc(al + so, lbo, sbo);
         const uint64_t dbh = tc::smem_desc(bh + so, lbo, sbo), dbl = tc::smem_desc(bl + so, lbo, sbo);
-        tc::mma_tf32(tmem, dal, dbh, idesc, s > 0 ? 1u : 0u);  // small terms first
-        tc::mma_tf32(tmem, dah, dbl, idesc, 1u);
-        tc::mma_tf32(tmem, dah, dbh, idesc, 1u);
+        const uint32_t d = tmem + (uint32_t)((s / spa) * N);  // accumulator of this K step
+        tc::mma_tf32(d, dal, dbh, idesc, (s % spa) ? 1u : 0u);  // small terms first
+        tc::mma_tf32(d, dah, dbl, idesc, 1u);
+        tc::mma_tf32(d, dah, dbh, idesc, 1u);
       }
       tc::mma_commit(&bar);
     }
@@ -173,14 +187,22 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
     if (!ok) break;
     phase ^= 1u;
     tc::fence_after_sync();
-    // accumulator rows to the output tile (A lo is free now), plus the inflow columns
+    // accumulator rows, summed over the accumulators (FP32 adds rounded to nearest: a few ulp over
+    // the handful of partial sums), plus the inflow columns, to the output tile (A lo is free now)
     {
       const int m = 32 * warp + lane;
       const unsigned f = fl[m];
       for (int c0 = 0; c0 < N; c0 += 32) {
-        float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-        tc::tmem_wait_ld();
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = 0.0f;
+        for (int a = 0; a < nacc; ++a) {
+          float v[32];
+          tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(a * N + c0), v);
+          tc::tmem_wait_ld();
+#pragma unroll
+          for (int j = 0; j < 32; ++j) acc[j] += v[j];
+        }
         for (int e = 0; e < nbc; ++e) {
           const int tt = src.bc_term[e], ax = src.axis[tt];
           const bool lower_face = src.w[tt] > 0;
@@ -189,12 +211,12 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
           if (val != 0.0f) {
 #pragma unroll
             for (int j = 0; j < 32; ++j)
-              if (c0 + j < N) v[j] += val * Wbc[e * N + c0 + j];
+              if (c0 + j < N) acc[j] = fmaf(val, Wbc[e * N + c0 + j], acc[j]);
           }
         }
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-          if (c0 + j < N) Os[(size_t)m * ldo + c0 + j] = v[j];
+          if (c0 + j < N) Os[(size_t)m * ldo + c0 + j] = acc[j];
       }
     }
     tc::fence_before_sync();
@@ -223,7 +245,8 @@ inline bool update_tc_fits(const SrcStencil<float>& src, const LivePattern& lp, 
     return false;
   if (kcap < 1 || update_tc_n(kcap) > 256) return false;
   const int K = (1 + 2 * src.nax) * src.rcap;
-  return update_tc_smem_bytes(K, update_tc_n(kcap), lp.nextra) <= (size_t)smem_optin;
+  const size_t need = update_tc_smem_bytes(K, update_tc_n(kcap), lp.nextra);
+  return (need > 117 * 1024 ? need : 117 * 1024) <= (size_t)smem_optin;
 }
 
 template <class Epi>
@@ -231,7 +254,10 @@ tt_status launch_update_tc(cudaStream_t s, int num_sms, const SrcStencil<float>&
                            const double* W, int kcap, const Epi& epi, double* partials, long* grid_out,
                            int cat = kUpdate) {
   const int K = (1 + 2 * src.nax) * src.rcap, N = update_tc_n(kcap);
-  const size_t smem = update_tc_smem_bytes(K, N, lp.nextra);
+  // at least half an SM's shared memory, so that one CTA is resident per SM and its tensor-memory
+  // accumulators never wait for another CTA's
+  size_t smem = update_tc_smem_bytes(K, N, lp.nextra);
+  if (smem < 117 * 1024) smem = 117 * 1024;
   if (const tt_status a = smem_optin(k_update_tc<Epi>, smem); a != TT_OK) return a;
   const long ntiles = (nrows + kTcRows - 1) / kTcRows;
   long grid = num_sms;  // one CTA per SM: its shared memory and accumulator stay resident

@@ -103,7 +103,9 @@ tt_status tt_autotune(tt_context* ctx, const tt_plan* plan, const tt_tensor* I, 
   auto trial = [&](float* out) -> tt_status {
     sc.load(I, s);
     if (temp0) cudaMemcpyAsync(plan->temp, temp0, sizeof(double) * ncell, cudaMemcpyDeviceToDevice, s);
+    // two untimed steps: with step graphs on, the first steps eagerly and the second captures
     tt_status t = tt_step(ctx, plan, &sc.x, tol, rmax, prec, nullptr);
+    if (t == TT_OK) t = tt_step(ctx, plan, &sc.x, tol, rmax, prec, nullptr);
     if (t != TT_OK) return t;
     cudaEventRecord(e0, s);
     for (int i = 0; i < steps && t == TT_OK; ++i) t = tt_step(ctx, plan, &sc.x, tol, rmax, prec, nullptr);
@@ -126,7 +128,7 @@ tt_status tt_autotune(tt_context* ctx, const tt_plan* plan, const tt_tensor* I, 
     std::vector<int> o;
     for (int m : {1, 2, 3, 4, 6, 8}) {
       const int l = m * ctx->num_sms / 2;
-      const int hi = (v == ttk::kTsqrColumnDense) ? most : wave;
+      const int hi = (v == ttk::kTsqrColumnDense) ? most : (v == ttk::kTsqrBlocked) ? ctx->num_sms : wave;
       const int lo = (v == ttk::kTsqrColumnDense) ? ctx->num_sms : 8;
       if (l >= lo && l <= hi) o.push_back(l);
     }

@@ -11,8 +11,11 @@ namespace ttk {
 // kTsqrColumn: one thread per column over 64-row (FP32) / 32-row (FP64) blocks, default
 // residency; kTsqrRowSplit: four lanes per column; kTsqrColumnDense: FP32 only, one thread per
 // column over 32-row blocks with registers held to four resident CTAs per SM (passes of at most
-// 160 columns; otherwise the column kernels run).
-enum TsqrVariant : int { kTsqrColumn = 0, kTsqrRowSplit = 1, kTsqrColumnDense = 2, kTsqrVariants = 3 };
+// 160 columns; otherwise the column kernels run); kTsqrBlocked: FP32 only, 256-row blocks held in
+// tensor memory, 32-column panels and compact-WY trailing updates, one CTA per SM (passes of at
+// most 224 columns).
+enum TsqrVariant : int { kTsqrColumn = 0, kTsqrRowSplit = 1, kTsqrColumnDense = 2, kTsqrBlocked = 3,
+                         kTsqrVariants = 4 };
 
 // Most leaves a tuned entry may ask for, per SM (workspace is sized for the entry in effect).
 constexpr int kTsqrMaxLeavesPerSm = 4;
@@ -51,6 +54,7 @@ inline TsqrCfg resolve_tsqr(const tt_context* ctx, int esize, int ncap, int wave
   const int col_threads = ((ncap + 31) / 32) * 32;
   const int rs_threads = ((4 * ncap + 31) / 32) * 32;
   if (cfg.variant == kTsqrColumnDense && (esize != 4 || col_threads > 160)) cfg.variant = kTsqrColumn;
+  if (cfg.variant == kTsqrBlocked && (esize != 4 || ncap > 224)) cfg.variant = kTsqrColumn;
   if (cfg.variant == kTsqrRowSplit && rs_threads > 1024) cfg.variant = kTsqrColumn;
   return cfg;
 }

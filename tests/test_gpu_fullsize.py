@@ -23,7 +23,8 @@ from paper_2602_00290_gb300.workloads import plane_config1, random_tt  # noqa: E
 TIE = 1e-9
 PINNED = {"fp64": {"transport": ("column", 304), "source": ("rowsplit", 304)},
           "mixed": {"transport": ("column_dense", 608), "source": ("rowsplit", 456)},
-          "mixed_3xtf32": {"transport": ("column_dense", 608), "source": ("rowsplit", 456)}}
+          "mixed_3xtf32": {"transport": ("column_dense", 608), "source": ("rowsplit", 456)},
+          "mixed_blocked": {"transport": ("blocked", 152), "source": ("blocked", 152)}}
 
 
 @pytest.fixture(scope="module")
@@ -56,13 +57,17 @@ def sampled_rows(cores, rows):
     return z @ right.reshape(right.shape[0], -1)
 
 
-@pytest.mark.parametrize("prec,dtype", [("fp64", "f64"), ("mixed", "f32"), ("mixed", "f64"), ("mixed_3xtf32", "f32")])
+@pytest.mark.parametrize("prec,dtype", [("fp64", "f64"), ("mixed", "f32"), ("mixed", "f64"), ("mixed_3xtf32", "f32"),
+                                        ("mixed_blocked", "f32")])
 def test_full_size_step_matches_oracle(tt, case, prec, dtype):
     wl, coef, a, ref, info, rows = case
     ctx = tt.Context(0)
     K1 = wl.rmax
+    pins = PINNED[prec]
+    if prec == "mixed_blocked":  # the mixed step with the blocked TSQR leaf over both sums
+        prec = "mixed"
     for role, ncap in (("transport", 5 * K1), ("source", K1 + 1)):
-        variant, leaves = PINNED[prec][role]
+        variant, leaves = pins[role]
         ctx.set_tsqr(prec, ncap, variant, leaves)
     plan = tt.Plan(ctx, wl)
     x = tt.TT.from_cores(a, rcap=[K1, K1], dtype=dtype)

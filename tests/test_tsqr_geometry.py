@@ -32,11 +32,36 @@ def tri_elems(n):
     return (n * (n + 1) // 2 + 3) // 4 * 4
 
 
+# Column descriptor of the stencil source (int kind, q, ax, w, b; double lam; float lamf; long s):
+# 20 bytes of ints, padded to 24, the double to 32, the float to 36, padded to 40, the long to 48.
+STENCIL_COL_BYTES = 48
+
+
+def blocked_touch(ncap):
+    """(end byte, vector accesses) of the blocked leaf: column descriptors, packed R, U and C-chunk
+    tiles [256][36], W/Y [32][ncap], T [32][33], norm [8] + dot [8][32] + per-warp [8][32] partials,
+    row flags [256]; 16-byte vectors on the U and C-chunk rows."""
+    off = (STENCIL_COL_BYTES * ncap + 15) // 16 * 16
+    R = off
+    off += 4 * tri_elems(ncap)
+    U = off
+    off += 4 * 256 * 36
+    C = off
+    off += 4 * 256 * 36
+    off += 4 * 32 * ncap + 4 * 32 * 33 + 4 * (8 + 8 * 32 + 8 * 32) + 4 * 256
+    vec = [(U + 4 * (t * 36 + c), 16) for t in range(256) for c in range(0, 32, 4)]
+    vec += [(C + 4 * (t * 36 + c), 16) for t in range(256) for c in range(0, 32, 4)]
+    assert R % 16 == 0
+    return off, vec
+
+
 def leaf_touch(prec, variant, ncap, br):
     """(end byte, list of (offset, width) vector accesses) of the leaf kernel's shared memory."""
     sz = 8 if prec == "fp64" else 4
     R4 = tri_elems(ncap)
     vec = []
+    if variant == 3:
+        return blocked_touch(ncap)
     if variant == 1:  # row-split: QS = 4 lanes per column, lane q holds RPT rows at stride SS
         QS, RPT = 4, br // 4
         SS = RPT + 4
@@ -94,8 +119,12 @@ def check(g, prec, variant, ncap, nrows):
     # threads: a column per thread (column owner) or per four lanes (row-split), whole warps
     t = g["leaf_threads"]
     assert t % 32 == 0
-    want = 4 * ncap if g["variant"] == 1 else ncap
-    assert want <= t < want + 32
+    if g["variant"] == 3:  # blocked: a row per thread, one CTA per SM (the block's tensor memory)
+        assert t == 256 and br == 256 and prec == "mixed" and ncap <= 224
+        assert L <= g["leaves_cap_sms"]
+    else:
+        want = 4 * ncap if g["variant"] == 1 else ncap
+        assert want <= t < want + 32
     if g["variant"] == 2:
         assert t <= 160 and prec == "mixed"
     # shared memory: every restated access inside the launch's dynamic shared memory, vectors aligned
@@ -127,7 +156,7 @@ SHAPES = [
 
 
 @pytest.mark.parametrize("prec,ncap,nrows", SHAPES)
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("num_sms,max_leaves", [(152, 0), (152, 608), (152, 456), (152, 8), (7, 0), (3, 5)])
 def test_tsqr_geometry_stays_inside_its_buffers(tt, prec, ncap, nrows, variant, num_sms, max_leaves):
     g0 = tt.tsqr_geometry(prec, variant, ncap, nrows, num_sms, 1, max_leaves)
@@ -135,6 +164,7 @@ def test_tsqr_geometry_stays_inside_its_buffers(tt, prec, ncap, nrows, variant, 
     assert most >= 1
     for per_sm in range(1, min(most, 32) + 1):
         g = tt.tsqr_geometry(prec, variant, ncap, nrows, num_sms, per_sm, max_leaves)
+        g["leaves_cap_sms"] = num_sms
         check(g, prec, variant, ncap, nrows)
         if max_leaves > 0:
             assert g["leaves"] <= max_leaves
@@ -151,6 +181,9 @@ def test_tsqr_geometry_refuses_what_no_kernel_takes(tt):
     assert tt.tsqr_geometry("fp64", 2, 160, 1000, 152, 1)["variant"] == 0  # dense leaf is FP32 only
     assert tt.tsqr_geometry("mixed", 2, 192, 1000, 152, 1)["variant"] == 0  # more than 160 threads
     assert tt.tsqr_geometry("mixed", 1, 256, 1000, 152, 1)["variant"] == 1  # 1024 lanes: still row-split
+    assert tt.tsqr_geometry("mixed", 3, 224, 1000, 152, 1)["variant"] == 3  # blocked: up to 224 columns
+    assert tt.tsqr_geometry("mixed", 3, 232, 1000, 152, 1)["variant"] == 0
+    assert tt.tsqr_geometry("fp64", 3, 160, 1000, 152, 1)["variant"] == 0  # blocked leaf is FP32 only
     with pytest.raises(tt.TTError) as e:
         tt.tsqr_geometry("fp64", 0, 256, 1000, 152, 1)  # 256 FP64 columns: R beyond 227 KB
     assert e.value.status == tt.TT_ERR_UNSUPPORTED
