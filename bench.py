@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--batch-scale", type=int, default=1)
     ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--batch-in-line", type=int, default=4,
+                    help="scale of the batched block of the default line (256 problems, cells and groups "
+                         "divided by it; 0 leaves the block out)")
     return ap.parse_args()
 
 
@@ -492,6 +495,13 @@ def run_ours(args):
             "seconds": time.time() - t0}
     except Exception as e:  # the analysis is a report, not part of the timed step
         line["internal_ranks"] = {"error": str(e)}
+    # the batched workload (independent problems of uneven shape, one CUDA graph per batch step),
+    # at a stated reduced scale so that the default run stays within minutes
+    if args.batch_in_line > 0 and rank == 0:
+        try:
+            line["batched"] = batched_block(tt, torch, ctx, args, 256, args.batch_in_line, "mixed")
+        except Exception as e:  # a second measurement, never a reason to lose the line
+            line["batched"] = {"error": str(e)}
     # storage factor k_s (App. A, 'Compression'): peak device storage of a step (the state at its
     # rank capacities plus the step's workspace) over the bytes of the rounded TT it leaves
     try:
@@ -594,6 +604,42 @@ def run_ours(args):
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def batched_block(tt, torch, ctx, args, nprob, scale, prec):
+    """Problem steps/s of the batched workload (batch_config3, seed 3) through tt_batch_step."""
+    from paper_2602_00290_gb300.workloads import batch_config3
+    wls = batch_config3(nprob, seed=3, scale=scale)
+    plans = [tt.Plan(ctx, wl) for wl in wls]
+    dtype = "f64" if prec == "fp64" else "f32"
+    states = [tt.initial_state(p, [w.rmax, w.rmax], dtype) for p, w in zip(plans, wls)]
+    b = tt.Batch(ctx, plans, states, [w.tol for w in wls], [w.rmax for w in wls], prec, args.streams)
+    b.step(3)  # eager step, capture, replay
+    b.sync()
+    steps = max(3, args.steps // 2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(ctx.stream)
+    b.step(steps)
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    st = b.sync()
+    ms = e0.elapsed_time(e1)
+    info = b.info()
+    out = {"problems": len(wls), "scale": scale, "precision": prec, "steps": steps,
+           "rows": sum(w.nrow for w in wls), "full_grid_unknowns": sum(w.nrow * w.ntheta * w.nphi for w in wls),
+           "batch_steps_per_s": steps / (ms / 1e3), "problem_steps_per_s": len(wls) * steps / (ms / 1e3),
+           "ms_per_batch_step": ms / steps, "gpu_launches_per_batch_step": info["launches_per_step"],
+           "workspace_gb": info["workspace_bytes"] / 1e9, "all_statuses_ok": all(v == 0 for v in st),
+           "workload": ("batch_config3(seed 3): Nx = Ny in {32..192}, G in {16..96}, 8x16..16x32 ordinates, "
+                        "r_max 8..48, x- inflow; cells, groups divided by `scale`, ordinates halved")}
+    b.close()
+    for p in plans:
+        p.close()
+    del states
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args):

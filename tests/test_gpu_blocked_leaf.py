@@ -87,7 +87,7 @@ def test_blocked_leaf_round_matches_oracle(tt, n, r, leaves):
     assert_tie_free(info, tie=0.01)
     ctx = tt.Context(0)
     _force(ctx, leaves)
-    x = tt.TT.from_cores(a, rcap=[40, 40], dtype="f32")
+    x = tt.TT.from_cores(a, rcap=[max(40, 3 * r[0]), max(40, 3 * r[1])], dtype="f32")
     tt.tt_round(ctx, x, 1e-5, 40, "mixed")
     ctx.sync()
     assert x.ranks() == nt.ranks(want)

@@ -150,7 +150,14 @@ def test_get_tsqr_defaults_and_clear(tt, ctx):
     assert ctx.get_tsqr("mixed", 160) == ("column_dense", 4 * nsm)
     ctx.set_tsqr("mixed", 0)
     assert ctx.get_tsqr("mixed", 41) == ("column", 3 * nsm)
-    assert tt.lib().tt_context_set_tsqr(ctx.handle, tt.TT_PREC_MIXED, 41, 3, 0) == tt.TT_ERR_ARG
+    ctx.set_tsqr("mixed", 224, "blocked", 0)  # the blocked leaf takes up to 224 columns in FP32
+    assert ctx.get_tsqr("mixed", 224)[0] == "blocked"
+    ctx.set_tsqr("mixed", 232, "blocked", 0)
+    assert ctx.get_tsqr("mixed", 232)[0] == "column"
+    ctx.set_tsqr("fp64", 64, "blocked", 0)
+    assert ctx.get_tsqr("fp64", 64)[0] == "column"
+    ctx.set_tsqr("mixed", 0)
+    assert tt.lib().tt_context_set_tsqr(ctx.handle, tt.TT_PREC_MIXED, 41, 4, 0) == tt.TT_ERR_ARG
     assert tt.lib().tt_context_set_tsqr(ctx.handle, 9, 41, 0, 0) == tt.TT_ERR_ARG
 
 
@@ -178,7 +185,7 @@ def test_autotune_keeps_state_and_parity(tt, ctx, prec, dtype):
     ncaps = {"transport": 5 * K1, "source": K1 + 1}
     for role, ncap in ncaps.items():
         v, l = res[role]
-        assert v in ("column", "rowsplit", "column_dense") and l > 0
+        assert v in ("column", "rowsplit", "column_dense", "blocked") and l > 0
         assert ctx.get_tsqr(prec, ncap) == (v, l)
     assert 0 < res["ms_tuned"] <= res["ms_default"]
     for s in range(3):
