@@ -29,6 +29,34 @@ METRIC = "TT transport steps/s and core-contraction TFLOP/s at fixed tol, FP64 v
 NOMINAL_TFLOPS = {"fp64": 152 * 2 * 2 * 2.070e9 / 1e12, "fp32": 152 * 128 * 2 * 2.070e9 / 1e12,
                   "tf32_tensor": 1100.0}
 MIXED_LEGS = ("mixed", "mixed_3xtf32")
+# DRAM traffic of one launch of the transport-sum TSQR leaf (the dominant kernel), per (precision,
+# leaf variant): (bytes read, bytes written, leaves) on the 96 x 96 workload (589,824 rows), from
+#   python bench.py --size medium --precision P --start graded --steps 1 --warmup 0 --breakdown-steps 1
+#       --tsqr transport=V:L,source=rowsplit:456 --no-gram --no-cpu-baseline --e2e-steps 0 --batch-in-line 0
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+#       -k regex:"^k_tsqr_leaf$" -c 1 --csv <the same command>
+# (first leaf launch = the transport sum of the first step, at full rank).  Reads scale with the rows
+# and writes (the leaves' R factors) with the leaves.  Valid only while the leaf kernels' source
+# (csrc/bigpass.cuh) is the one captured: its SHA-256 prefix is LEAF_DRAM_SOURCE.
+LEAF_DRAM_SOURCE = None
+LEAF_DRAM_96 = {}
+
+
+def leaf_source_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2602_00290_gb300", "csrc", "bigpass.cuh")
+    with open(path, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def leaf_traffic(precision, variant, leaves, nrows):
+    """DRAM bytes of one transport-sum leaf launch at nrows rows and `leaves` leaves, scaled from the
+    96 x 96 capture of the same kernel; None when there is none or the kernel source changed since."""
+    t = LEAF_DRAM_96.get(("fp64" if precision == "fp64" else "mixed", variant))
+    if t is None or LEAF_DRAM_SOURCE is None or leaf_source_sha() != LEAF_DRAM_SOURCE:
+        return None
+    rd, wr, lm = t
+    return rd * nrows / 589824 + wr * leaves / lm
 PREC_TEXT = {"fp64": "fp64",
              "mixed": "mixed: f32 passes over the merged core (FP32 FMA), f64 small cores",
              "mixed_3xtf32": "mixed_3xtf32: f32 passes over the merged core, the update GEMM on the tensor cores "
@@ -61,6 +89,9 @@ def parse():
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--batch-scale", type=int, default=1)
     ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--start", default="planck", choices=["planck", "graded"],
+                    help="initial state: I0 = epsilon(T) (rank 1), or the seeded graded state of rank r_max "
+                         "(workloads.graded_state; every pass at full width from the first step, e.g. to profile)")
     ap.add_argument("--batch-in-line", type=int, default=4,
                     help="scale of the batched block of the default line (256 problems, cells and groups "
                          "divided by it; 0 leaves the block out)")
@@ -260,7 +291,11 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     ctx.set_rounding(rounding)
     dtype = "f64" if precision == "fp64" else "f32"
     rcap = [wl.rmax, wl.rmax]
-    x = tt.initial_state(plan, rcap, dtype)
+    if args.start == "graded":
+        from paper_2602_00290_gb300.workloads import graded_state
+        x = tt.TT.from_cores(graded_state(wl), rcap=rcap, dtype=dtype)
+    else:
+        x = tt.initial_state(plan, rcap, dtype)
     stream = ctx.stream
     energy = torch.zeros(4, dtype=torch.float64, device="cuda")
     pinned = None
@@ -357,8 +392,10 @@ def time_precision(tt, torch, ctx, plan, wl, args, precision, dist, clocks_index
     out["roofline"] = {"kernel": kname + " over the transport sum (one launch per step, R1 = 5r columns)",
                        "bound": "alu", "achieved": leaf_tf, "peak": peak, "unit": "TFLOP/s",
                        "frac": (leaf_tf / peak) if leaf_tf else None,
-                       "traffic": None,
-                       "traffic_note": "no DRAM capture of the kernel as it now stands is recorded in this run",
+                       "traffic": leaf_traffic(precision, variant, int(tune["transport"][1]) if tune else 0, wl.nrow),
+                       "traffic_note": ("ncu DRAM bytes (read + written) of this leaf kernel on the 96 x 96 workload, "
+                                        "reads scaled by rows and writes by leaves; null when no capture of the kernel "
+                                        "source as it stands is recorded"),
                        "flops_per_launch": "2 N_Z R1^2 (R1 = 5 r, r the rank entering the step)",
                        "peak_source": ("FP64" if precision == "fp64" else "FP32") + " FMA pipe, " + pk["source"] +
                                       " in this run (tt_peak_probe)",
@@ -483,7 +520,9 @@ def run_ours(args):
     # tolerance and the compression ratios of Eqs. (compression), (rel_compression_nu/_x)
     try:
         t0 = time.time()
-        r1, r1x, _, _ = tt.tt_internal_ranks(ctx, plan, x, wl.tol)
+        r1, r1x, _, _, ir_st = tt.tt_internal_ranks(ctx, plan, x, wl.tol, with_status=True)
+        ir_status = ("ok" if ir_st == tt.TT_OK else
+                     "a Jacobi solve reached its sweep cap (TT_ERR_TIMEOUT): ranks of its last sweep")
         r2, r3 = x.ranks()[1], x.ranks()[2]
         nX, nnu, nth, nph = wl.nx * wl.ny * wl.nz, wl.ngroup, wl.ntheta, wl.nphi
         ntt = nX * nnu * r2 + nth * r2 * r3 + nph * r3
@@ -492,7 +531,7 @@ def run_ours(args):
             "compression": nX * nnu * nth * nph / ntt,
             "compression_rel_nu": ntt / (nnu * r1 + nX * r1 * r2 + nth * r2 * r3 + nph * r3),
             "compression_rel_x": ntt / (nX * r1x + nnu * r1x * r2 + nth * r2 * r3 + nph * r3),
-            "seconds": time.time() - t0}
+            "seconds": time.time() - t0, "status": ir_status}
     except Exception as e:  # the analysis is a report, not part of the timed step
         line["internal_ranks"] = {"error": str(e)}
     # the batched workload (independent problems of uneven shape, one CUDA graph per batch step),
@@ -552,9 +591,14 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_ms = e0.elapsed_time(e1)
+        try:
+            ctx.sync()
+            e2e_status = "ok"
+        except tt.TTError as e:
+            e2e_status = str(e)
         line["e2e"] = {"value": ws * e2e_steps / (e2e_ms / 1e3), "unit": "steps/s",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-                       "steps": e2e_steps, "precision": head}
+                       "steps": e2e_steps, "precision": head, "status": e2e_status}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         start = states["fp64"] if "fp64" in states else x
         cores = start.to_cores()

@@ -328,7 +328,9 @@ tt_status tt_step(tt_context *ctx, const tt_plan *plan, tt_tensor *I, double tol
  * ranks[2] (host) receives r1, r1x; sigma_nu / sigma_x (host, nullable) receive up to nsigma_*
  * singular values, decreasing.  The singular values come from FP64 Gram matrices (N_nu x N_nu and
  * N_nu rcap x N_nu rcap, at most 4096) and Jacobi eigen-solves, so values below about 1e-8 of the
- * largest are not resolved.  TT_ERR_UNSUPPORTED beyond 4096. */
+ * largest are not resolved.  TT_ERR_UNSUPPORTED beyond 4096.  The status latched on the device
+ * during the call is returned (and cleared): TT_ERR_TIMEOUT when a Jacobi solve reached its sweep
+ * cap, with the ranks of its last sweep still written. */
 tt_status tt_internal_ranks(tt_context *ctx, const tt_plan *plan, const tt_tensor *x, double delta_rel,
                             int32_t *ranks, double *sigma_nu, int64_t nsigma_nu, double *sigma_x, int64_t nsigma_x);
 

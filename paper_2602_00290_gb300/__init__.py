@@ -520,8 +520,10 @@ class Batch:
             pass
 
 
-def tt_internal_ranks(ctx: Context, plan: "Plan", x: TT, delta_rel: float):
-    """(r1, r1x, sigma_nu, sigma_x): internal delta-ranks of the merged core (tt_internal_ranks)."""
+def tt_internal_ranks(ctx: Context, plan: "Plan", x: TT, delta_rel: float, with_status: bool = False):
+    """(r1, r1x, sigma_nu, sigma_x): internal delta-ranks of the merged core (tt_internal_ranks).
+    with_status: a TT_ERR_TIMEOUT (a Jacobi sweep cap reached; the ranks of the last sweep) is
+    returned as a fifth element instead of raised."""
     G = plan.wl.ngroup
     ncx = G * x.rcap[1]
     nX = x.n[0] // G
@@ -529,9 +531,12 @@ def tt_internal_ranks(ctx: Context, plan: "Plan", x: TT, delta_rel: float):
     snu = (ctypes.c_double * G)()
     nsx = min(nX, ncx)
     sx = (ctypes.c_double * nsx)()
-    _check(lib().tt_internal_ranks(ctx.handle, plan.handle, ctypes.byref(x._struct()), float(delta_rel), r, snu, G,
-                                   sx, nsx), "tt_internal_ranks")
-    return int(r[0]), int(r[1]), np.array(snu[:]), np.array(sx[:])
+    st = lib().tt_internal_ranks(ctx.handle, plan.handle, ctypes.byref(x._struct()), float(delta_rel), r, snu, G,
+                                 sx, nsx)
+    if not (with_status and st == TT_ERR_TIMEOUT):
+        _check(st, "tt_internal_ranks")
+    out = (int(r[0]), int(r[1]), np.array(snu[:]), np.array(sx[:]))
+    return out + (st,) if with_status else out
 
 
 def tt_round(ctx: Context, x: TT, tol: float, rmax: int, prec="fp64"):

@@ -571,7 +571,13 @@ tt_status tt_internal_ranks(tt_context* ctx, const tt_plan* plan, const tt_tenso
   });
   ranks[0] = r[0];
   ranks[1] = r[1];
-  return st;
+  if (st != TT_OK) return st;
+  // synchronous: report (and clear) what the analysis latched on the device, e.g. a Jacobi sweep
+  // cap reached on a Gram matrix with many eigenvalues at round-off level (ranks still written)
+  int dst = 0;
+  if (cudaMemcpy(&dst, &ctx->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TT_ERR_CUDA;
+  if (dst != 0 && cudaMemset(&ctx->ctrl->status, 0, sizeof(int)) != cudaSuccess) return TT_ERR_CUDA;
+  return static_cast<tt_status>(dst);
 }
 
 tt_status tt_energy_density(tt_context* ctx, const tt_plan* plan, const tt_tensor* x, double* out_dev) {

@@ -293,6 +293,16 @@ def sketch_matrix(nang: int, ell: int, seed: int = 11) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal((nang, ell))
 
 
+def graded_state(wl: Workload, seed: int = 21):
+    """A seeded state of full rank r_max with geometrically graded cores (factors 0.55^j on the
+    merged core's columns, 0.7^j on the polar core's), so that every rank decision of a step is far
+    from a tie: iid N(0,1) cores, shapes of the workload's TT (d = 3)."""
+    a = random_tt([wl.nrow, wl.ntheta, wl.nphi], [wl.rmax, wl.rmax], seed=seed)
+    a[0] = a[0] * (0.55 ** np.arange(wl.rmax))[None, None, :]
+    a[1] = a[1] * (0.7 ** np.arange(wl.rmax))[None, None, :]
+    return a
+
+
 def random_tt(n: Sequence[int], ranks: Sequence[int], seed: int, scale: float = 1.0):
     """Cores with iid N(0,1) entries, core k of shape (r_{k-1}, n_k, r_k)."""
     rng = np.random.default_rng(seed)

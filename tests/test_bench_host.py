@@ -44,3 +44,13 @@ def test_dense_oracle_rate_is_measured():
     rate, unknowns, threads, seconds = bench.dense_dof_rate(wl, n=4, reps=2)
     assert unknowns == 4 * 4 * 4 * 4 * 8
     assert rate > 0 and threads >= 1 and seconds > 0
+
+
+def test_leaf_traffic_is_null_without_a_capture_of_this_source(monkeypatch):
+    monkeypatch.setattr(bench, "LEAF_DRAM_96", {("mixed", "column"): (100.0, 50.0, 10)})
+    monkeypatch.setattr(bench, "LEAF_DRAM_SOURCE", "0" * 16)  # not the source as it stands
+    assert bench.leaf_traffic("mixed", "column", 10, 589824) is None
+    monkeypatch.setattr(bench, "LEAF_DRAM_SOURCE", bench.leaf_source_sha())
+    assert bench.leaf_traffic("mixed", "column", 10, 589824) == 150.0
+    assert bench.leaf_traffic("mixed", "column", 20, 2 * 589824) == 300.0  # rows and leaves scale
+    assert bench.leaf_traffic("mixed", "rowsplit", 10, 589824) is None  # no capture of that kernel
