@@ -38,8 +38,10 @@ MIXED_LEGS = ("mixed", "mixed_3xtf32")
 # (first leaf launch = the transport sum of the first step, at full rank).  Reads scale with the rows
 # and writes (the leaves' R factors) with the leaves.  Valid only while the leaf kernels' source
 # (csrc/bigpass.cuh) is the one captured: its SHA-256 prefix is LEAF_DRAM_SOURCE.
-LEAF_DRAM_SOURCE = None
-LEAF_DRAM_96 = {}
+LEAF_DRAM_SOURCE = "23f5325e1b623755"
+LEAF_DRAM_96 = {("mixed", "column"): (77494016, 28185856, 439),
+                ("mixed", "column_dense"): (77257472, 59731200, 595),
+                ("fp64", "column"): (202129920, 5283072, 303)}
 
 
 def leaf_source_sha():
