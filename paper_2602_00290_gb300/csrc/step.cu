@@ -223,7 +223,7 @@ static tt_status launch_update(const tt_context* ctx, cudaStream_t s, int num_sm
                                long* grid_out, int cat = kUpdate) {
   constexpr int TM = UpdTM<T>::value;
   if constexpr (sizeof(T) == 4 && std::is_same<Src, SrcStencil<float>>::value) {
-    if (ctx->tensor_cores && update_tc_fits(src, lp, kcap, ctx->smem_optin))
+    if (ctx->tensor_cores && update_tc_fits(src, lp, nrows, kcap, ctx->smem_optin))
       return launch_update_tc(s, num_sms, src, lp, nrows, W, kcap, epi, partials, grid_out, cat);
   }
   if constexpr (sizeof(T) == 4 && StencilOf<Src>::value) {

@@ -41,16 +41,34 @@ __host__ __device__ inline size_t update_tc_smem_bytes(int K, int N, int nbc) {
   return b + sizeof(double) * 3 * kTcRows + sizeof(float) * (size_t)N + sizeof(unsigned) * kTcRows;
 }
 
-template <class Epi>
-__global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, LivePattern lp, long nrows,
+// Row flags of k_update_blk (neighbour bits 2a and 2a + 1, the group in bits 8 and up) in 32-bit
+// arithmetic: the host takes this kernel only for merged cores of fewer than 2^31 rows.
+template <typename S>
+__device__ __forceinline__ unsigned tc_row_flags(const SrcStencil<S>& src, unsigned k) {
+  unsigned f = 0u;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const unsigned idx = (k / (unsigned)src.stride[a]) % (unsigned)src.ext[a];
+    f |= (idx > 0u ? 1u : 0u) << (2 * a);
+    f |= (idx + 1u < (unsigned)src.ext[a] ? 1u : 0u) << (2 * a + 1);
+  }
+  return f | ((k % (unsigned)src.G) << 8);
+}
+
+// NB row blocks (1 + 2 d_X) of RCAP columns each: K = NB RCAP, compile-time.  256 threads: all of
+// them stage, split and run the epilogue; warps 0-3 read the accumulators (TMEM lanes = rows).
+template <class Epi, int NB, int RCAP>
+__global__ void __launch_bounds__(256, 1) k_update_tc(SrcStencil<float> src, LivePattern lp, long nrows,
                                                       const double* __restrict__ W, int kcap, Epi epi,
                                                       double* __restrict__ partials) {
   extern __shared__ __align__(1024) unsigned char tcu_smem[];
-  const int rcap = src.rcap, nb = 1 + 2 * src.nax, nbc = lp.nextra;
-  const int K = nb * rcap, N = update_tc_n(kcap), ldo = N + 1;
+  constexpr int K = NB * RCAP, GPR = RCAP / 4;
+  static_assert(RCAP % 8 == 0, "whole MMA K steps per row block");
+  const int nbc = lp.nextra;
+  const int N = update_tc_n(kcap), ldo = N + 1;
   const int spa = update_tc_steps_per_acc(K, N), nacc = (K / 8 + spa - 1) / spa;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
-  const int rq = r < rcap ? r : rcap;  // live columns of each Z block
+  const int rq = r < RCAP ? r : RCAP;  // live columns of each Z block
   float* Ahi = reinterpret_cast<float*>(tcu_smem);
   float* Alo = Ahi + (size_t)kTcRows * K;
   float* Bhi = Alo + (size_t)kTcRows * K;
@@ -74,10 +92,10 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
   }
   if (tid == 0) tc::mbar_init(&bar, 1);
 
-  // combined weights B[n][k] for k = b rcap + q (FP64 sums as in k_update_blk), split in TF32 parts
+  // combined weights B[n][k] for k = b RCAP + q (FP64 sums as in k_update_blk), split in TF32 parts
   for (int i = tid; i < N * K; i += blockDim.x) {
     const int n = i / K, kk = i - (i / K) * K;
-    const int b = kk / rcap, q = kk - (kk / rcap) * rcap;
+    const int b = kk / RCAP, q = kk - (kk / RCAP) * RCAP;
     double sum = 0.0;
     if (n < kcap && q < rq) {
       if (b == 0) {
@@ -89,7 +107,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
           double cL, cH;
           blk_coefs(src, t, cL, cH);
           const double cf = (b == 1 + 2 * ax) ? cL : cH;
-          if (cf != 0.0) sum += cf * W[(size_t)(t * rcap + q) * kcap + n];
+          if (cf != 0.0) sum += cf * W[(size_t)(t * RCAP + q) * kcap + n];
         }
       }
     }
@@ -100,7 +118,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
   }
   for (int i = tid; i < nbc * N; i += blockDim.x) {
     const int e = i / N, n = i - (i / N) * N;
-    const int c = (src.nterm + 1) * rcap + e;
+    const int c = (src.nterm + 1) * RCAP + e;
     Wbc[i] = (n < kcap && lp.live(c, r)) ? (float)W[(size_t)c * kcap + n] : 0.0f;
   }
   for (int n = tid; n < N; n += blockDim.x) vJs[n] = (vJ && n < kcap) ? (float)vJ[n] : 0.0f;
@@ -109,8 +127,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
   tc::fence_after_sync();
   const uint32_t tmem = tbase;
   const uint32_t idesc = tc::idesc_tf32(kTcRows, N);
-  const uint32_t lbo = 128, sbo = (uint32_t)(K / 4) * 128u;
-  const int gpr = rcap / 4;  // 16-byte granules of a row block
+  constexpr uint32_t lbo = 128, sbo = (uint32_t)(K / 4) * 128u;
   const long ntiles = (nrows + kTcRows - 1) / kTcRows;
   uint32_t phase = 0;
   bool ok = true;
@@ -118,16 +135,17 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
   for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long row0 = tile * kTcRows;
     __syncthreads();  // the previous tile's epilogue is done with the output tile and row scalars
-    fl[tid] = (row0 + tid < nrows) ? src.row_flags(row0 + tid) : 0u;
+    if (tid < kTcRows) fl[tid] = (row0 + tid < nrows) ? tc_row_flags(src, (unsigned)(row0 + tid)) : 0u;
     __syncthreads();
     // every granule of the tile's row blocks in flight at once, into the A layout; rows outside
     // the core and neighbours the row does not have are zero-filled.  Eight consecutive threads
     // take one granule of eight consecutive rows (one 128-byte core matrix: no bank conflict), a
     // warp four granules of them (whole 32-byte sectors of every row it reads)
-    const int per_block = kTcRows * gpr;
-    for (int i = tid; i < nb * per_block; i += blockDim.x) {
+    constexpr int per_block = kTcRows * GPR;
+#pragma unroll 4
+    for (int i = tid; i < NB * per_block; i += 256) {
       const int b = i / per_block, rem = i - b * per_block;
-      const int r8 = rem >> 3, g = r8 % gpr, m = (r8 / gpr) * 8 + (rem & 7);
+      const int r8 = rem >> 3, g = r8 % GPR, m = (r8 / GPR) * 8 + (rem & 7);
       long k = row0 + m;
       bool okr = k < nrows;
       if (b > 0) {
@@ -136,21 +154,22 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
         okr = okr && ((fl[m] >> (2 * ax + (upper ? 1 : 0))) & 1u);
         k += upper ? src.stride[ax] : -src.stride[ax];
       }
-      float* dst = Ahi + (tc::kmajor_off(m, b * rcap + 4 * g, K) >> 2);
-      const float* from = okr ? src.Z + k * src.ldz + (size_t)4 * g : src.Z;
+      float* dst = Ahi + (tc::kmajor_off(m, b * RCAP + 4 * g, K) >> 2);
+      const float* from = okr ? src.Z + k * RCAP + (size_t)4 * g : src.Z;
       cp_async16(dst, from, okr ? 16 : 0);
     }
     cp_async_wait_all();
     __syncthreads();
     // neighbours to differences with the centre rows (L -> C - L, H -> H - C), then every value
-    // to its TF32 part (A hi) and remainder (A lo); a thread takes 4 consecutive K values of a
-    // row (16-byte vectors; a warp's 32 rows fall on distinct banks)
-    for (int i = tid; i < kTcRows * gpr; i += blockDim.x) {
+    // to its TF32 part (A hi) and rounded remainder (A lo); a thread takes 4 consecutive K values
+    // of a row (16-byte vectors; a warp's 32 rows fall on distinct banks)
+    for (int i = tid; i < kTcRows * GPR; i += 256) {
       const int g = i / kTcRows, m = i - g * kTcRows;
       const uint32_t oc = tc::kmajor_off(m, 4 * g, K) >> 2;
       const float4 c = *reinterpret_cast<const float4*>(Ahi + oc);
-      for (int b = 1; b < nb; ++b) {
-        const uint32_t o = tc::kmajor_off(m, b * rcap + 4 * g, K) >> 2;
+#pragma unroll
+      for (int b = 1; b < NB; ++b) {
+        const uint32_t o = tc::kmajor_off(m, b * RCAP + 4 * g, K) >> 2;
         float4 v = *reinterpret_cast<const float4*>(Ahi + o);
         if (b & 1) {
           v = make_float4(c.x - v.x, c.y - v.y, c.z - v.z, c.w - v.w);
@@ -172,6 +191,7 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
     if (tid == 0) {
       tc::fence_after_sync();
       const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo), bh = tc::smem_u32(Bhi), bl = tc::smem_u32(Blo);
+#pragma unroll 4
       for (int s = 0; s < K / 8; ++s) {
         const uint32_t so = 256u * (uint32_t)s;
         const uint64_t dah = tc::smem_desc(ah + so, lbo, sbo), dal = tc::smem_desc(al + so, lbo, sbo);
@@ -187,9 +207,10 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
     if (!ok) break;
     phase ^= 1u;
     tc::fence_after_sync();
-    // accumulator rows, summed over the accumulators (FP32 adds rounded to nearest: a few ulp over
-    // the handful of partial sums), plus the inflow columns, to the output tile (A lo is free now)
-    {
+    // accumulator rows (warps 0-3), summed over the accumulators (FP32 adds rounded to nearest: a
+    // few ulp over the handful of partial sums), plus the inflow columns, to the output tile (A lo
+    // is free now)
+    if (warp < 4) {
       const int m = 32 * warp + lane;
       const unsigned f = fl[m];
       for (int c0 = 0; c0 < N; c0 += 32) {
@@ -238,10 +259,13 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(SrcStencil<float> src, Liv
   }
 }
 
-// Whether the tensor-core update takes a pass: FP32 storage with rows of whole MMA K steps
-// (rcap a multiple of 8, 16-byte aligned rows), at most 256 output columns, and its shared memory.
-inline bool update_tc_fits(const SrcStencil<float>& src, const LivePattern& lp, int kcap, int smem_optin) {
-  if (src.rcap % 8 != 0 || src.ldz != src.rcap || ((size_t)src.Z % 16) != 0 || src.rcap != lp.rcap || src.nax < 1)
+// Whether the tensor-core update takes a pass: FP32 storage, rank capacity 8, 16 or 32 (the
+// kernel's instantiations; 16-byte aligned rows of whole MMA K steps), 1 to 3 axes, at most 256
+// output columns, fewer than 2^31 rows, and its shared memory.
+inline bool update_tc_fits(const SrcStencil<float>& src, const LivePattern& lp, long nrows, int kcap,
+                           int smem_optin) {
+  if ((src.rcap != 8 && src.rcap != 16 && src.rcap != 32) || src.ldz != src.rcap || ((size_t)src.Z % 16) != 0 ||
+      src.rcap != lp.rcap || src.nax < 1 || src.nax > 3 || nrows >= (1L << 31))
     return false;
   if (kcap < 1 || update_tc_n(kcap) > 256) return false;
   const int K = (1 + 2 * src.nax) * src.rcap;
@@ -249,24 +273,39 @@ inline bool update_tc_fits(const SrcStencil<float>& src, const LivePattern& lp, 
   return (need > 117 * 1024 ? need : 117 * 1024) <= (size_t)smem_optin;
 }
 
-template <class Epi>
-tt_status launch_update_tc(cudaStream_t s, int num_sms, const SrcStencil<float>& src, LivePattern lp, long nrows,
-                           const double* W, int kcap, const Epi& epi, double* partials, long* grid_out,
-                           int cat = kUpdate) {
-  const int K = (1 + 2 * src.nax) * src.rcap, N = update_tc_n(kcap);
+template <class Epi, int NB, int RCAP>
+tt_status launch_update_tc_k(cudaStream_t s, int num_sms, const SrcStencil<float>& src, LivePattern lp, long nrows,
+                             const double* W, int kcap, const Epi& epi, double* partials, long* grid_out, int cat) {
+  const int K = NB * RCAP, N = update_tc_n(kcap);
   // at least half an SM's shared memory, so that one CTA is resident per SM and its tensor-memory
   // accumulators never wait for another CTA's
   size_t smem = update_tc_smem_bytes(K, N, lp.nextra);
   if (smem < 117 * 1024) smem = 117 * 1024;
-  if (const tt_status a = smem_optin(k_update_tc<Epi>, smem); a != TT_OK) return a;
+  auto kern = k_update_tc<Epi, NB, RCAP>;
+  if (const tt_status a = smem_optin(kern, smem); a != TT_OK) return a;
   const long ntiles = (nrows + kTcRows - 1) / kTcRows;
-  long grid = num_sms;  // one CTA per SM: its shared memory and accumulator stay resident
+  long grid = num_sms;  // one CTA per SM: its shared memory and accumulators stay resident
   if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
   if (grid_out) *grid_out = grid;
   TimerScope scope(cat, s);
-  k_update_tc<Epi><<<(unsigned)grid, 128, smem, s>>>(src, lp, nrows, W, kcap, epi, partials);
+  kern<<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
+}
+
+// Dispatch on (1 + 2 d_X, rcap); update_tc_fits has checked that an instantiation exists.
+template <class Epi>
+tt_status launch_update_tc(cudaStream_t s, int num_sms, const SrcStencil<float>& src, LivePattern lp, long nrows,
+                           const double* W, int kcap, const Epi& epi, double* partials, long* grid_out,
+                           int cat = kUpdate) {
+#define TT_UPDATE_TC_CASE(NB_, RC_)                                                                          \
+  if (1 + 2 * src.nax == NB_ && src.rcap == RC_)                                                            \
+    return launch_update_tc_k<Epi, NB_, RC_>(s, num_sms, src, lp, nrows, W, kcap, epi, partials, grid_out, cat);
+  TT_UPDATE_TC_CASE(3, 8) TT_UPDATE_TC_CASE(3, 16) TT_UPDATE_TC_CASE(3, 32)
+  TT_UPDATE_TC_CASE(5, 8) TT_UPDATE_TC_CASE(5, 16) TT_UPDATE_TC_CASE(5, 32)
+  TT_UPDATE_TC_CASE(7, 8) TT_UPDATE_TC_CASE(7, 16) TT_UPDATE_TC_CASE(7, 32)
+#undef TT_UPDATE_TC_CASE
+  return TT_ERR_UNSUPPORTED;
 }
 
 }  // namespace ttk

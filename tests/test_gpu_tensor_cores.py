@@ -72,7 +72,7 @@ def test_peak_probes_report_work(tt, kind, iters):
 # ------------------------------------------------------------- the mixed step on the tensor cores
 
 from oracle import naive_tt as nt, problem  # noqa: E402
-from paper_2602_00290_gb300.workloads import cube_config, plane_config1  # noqa: E402
+from paper_2602_00290_gb300.workloads import cube_config, plane_config1, slab_config0  # noqa: E402
 
 
 def fro_rel(a, b):
@@ -93,6 +93,7 @@ TC_CASES = {
     "rusanov_r16": _plane(rmax=16).with_(flux="rusanov"),
     "central_r8": _plane().with_(flux="central"),
     "cube_r8_inflow": cube_config().with_(inflow_temperature=(0.9, None, None, None, 0.6, None)),
+    "slab_r8_rusanov": slab_config0().with_(flux="rusanov", tol=1e-6),
 }
 
 
@@ -106,11 +107,12 @@ def test_mixed_3xtf32_step_matches_oracle(tt, name):
     ctx = tt.Context(0)
     coef = problem.build(wl)
     plan = tt.Plan(ctx, wl)
-    x = tt.initial_state(plan, [wl.rmax, wl.rmax], "f32")
+    rc = [wl.rmax] if wl.ndim == 1 else [wl.rmax, wl.rmax]
+    x = tt.initial_state(plan, rc, "f32")
     ref = nt.initial_tt(problem.initial_rows(wl, coef), coef)
     errs = []
     for _ in range(5):
-        y = tt.TT.from_cores(x.to_cores(), rcap=[wl.rmax, wl.rmax], dtype="f32")
+        y = tt.TT.from_cores(x.to_cores(), rcap=rc, dtype="f32")
         tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, "mixed_3xtf32")
         tt.tt_step(ctx, plan, y, wl.tol, wl.rmax, "mixed")
         ref = nt.step(ref, coef, wl.tol, wl.rmax)
