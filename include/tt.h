@@ -212,11 +212,12 @@ tt_status tt_context_get_tsqr(const tt_context *ctx, tt_precision prec, int32_t 
  * the one that runs), max_leaves the leaf cap in force (<= 0: none), on a device with num_sms
  * SMs where per_sm leaf CTAs are resident at once (what the occupancy query reports for the leaf
  * kernel).  A host computation by the functions the launches use: it needs no GPU and touches
- * no device.  out[0..nout) (nout <= 11): [0] leaves, [1] rows per leaf (the last leaf takes the
+ * no device.  out[0..nout) (nout <= 12): [0] leaves, [1] rows per leaf (the last leaf takes the
  * ragged rest), [2] rows per block, [3] leaf threads per CTA, [4] leaf dynamic shared-memory
  * bytes, [5] merge threads per CTA, [6] merge dynamic shared-memory bytes, [7] merge levels,
  * [8] and [9] doubles of the two R-factor buffers the step's workspace holds (leaf output and
- * merge levels alternate between them), [10] the variant that runs.  TT_ERR_UNSUPPORTED for a
+ * merge levels alternate between them), [10] the variant that runs, [11] rows of the second
+ * factor a merge absorbs at a time.  TT_ERR_UNSUPPORTED for a
  * shape no kernel takes (too many columns, or per_sm < 1 for the row-split leaf).  The paper has
  * no counterpart: these are launch-shape choices. */
 tt_status tt_tsqr_geometry(tt_precision prec, int32_t variant, int32_t ncap, int64_t nrows, int32_t num_sms,

@@ -134,7 +134,7 @@ def lib():
 
 
 GEOMETRY_KEYS = ("leaves", "rows_per_leaf", "block_rows", "leaf_threads", "leaf_smem", "merge_threads",
-                 "merge_smem", "merge_levels", "ws_a_doubles", "ws_b_doubles", "variant")
+                 "merge_smem", "merge_levels", "ws_a_doubles", "ws_b_doubles", "variant", "merge_rows")
 
 
 def tsqr_geometry(precision, variant, ncap, nrows, num_sms, per_sm, max_leaves=0):

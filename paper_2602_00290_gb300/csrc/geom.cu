@@ -46,10 +46,13 @@ tt_status geometry(int variant, int ncap, long nrows, int num_sms, int per_sm, i
   // merge tree: the row-split merge where 4 ncap lanes fit a CTA, else the column-owner merge
   size_t msmem;
   int mthreads;
-  if (rs_threads <= 1024 && ttk::tsqr_rs_smem_bytes<T, 64, 4>(ncap) <= 227 * 1024) {
-    msmem = ttk::tsqr_rs_smem_bytes<T, 64, 4>(ncap);
+  int mrows;
+  if (rs_threads <= 1024 && ttk::merge_rs_smem_bytes<T>(ncap) <= 227 * 1024) {
+    msmem = ttk::merge_rs_smem_bytes<T>(ncap);
     mthreads = rs_threads;
+    mrows = ttk::merge_rs_rows<T>(ncap);
   } else {
+    mrows = sizeof(T) == 4 ? 64 : 32;
     msmem = ttk::tsqr_smem_bytes<T, sizeof(T) == 4 ? 64 : 32>(ncap);
     mthreads = col_threads;
     if (msmem > 227 * 1024 || mthreads > 256) return TT_ERR_UNSUPPORTED;
@@ -69,6 +72,7 @@ tt_status geometry(int variant, int ncap, long nrows, int num_sms, int per_sm, i
   g[8] = bound * nn;
   g[9] = ((bound + 1) / 2) * nn;
   g[10] = variant;
+  g[11] = mrows;
   return TT_OK;
 }
 
@@ -77,10 +81,10 @@ tt_status geometry(int variant, int ncap, long nrows, int num_sms, int per_sm, i
 extern "C" tt_status tt_tsqr_geometry(tt_precision prec, int32_t variant, int32_t ncap, int64_t nrows,
                                       int32_t num_sms, int32_t per_sm, int32_t max_leaves, int64_t* out,
                                       int32_t nout) {
-  if (!out || nout < 1 || nout > 11 || ncap < 1 || nrows < 1 || num_sms < 1 || variant < 0 ||
+  if (!out || nout < 1 || nout > 12 || ncap < 1 || nrows < 1 || num_sms < 1 || variant < 0 ||
       variant >= ttk::kTsqrVariants || (prec != TT_PREC_FP64 && prec != TT_PREC_MIXED && prec != TT_PREC_MIXED_3XTF32))
     return TT_ERR_ARG;
-  int64_t g[11] = {};
+  int64_t g[12] = {};
   const tt_status st = (prec == TT_PREC_FP64)
                            ? geometry<double>(variant, ncap, nrows, num_sms, per_sm, max_leaves, g)
                            : geometry<float>(variant, ncap, nrows, num_sms, per_sm, max_leaves, g);

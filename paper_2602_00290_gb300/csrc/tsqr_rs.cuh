@@ -189,7 +189,11 @@ __device__ __forceinline__ void hh_absorb_rs_f64(double* Rs, int ncap, double (&
   }
 }
 
-template <typename T, int BR, int QS, bool VREG = true>
+// TRI (merges): the block holds rows jbeg.. of an upper-triangular factor, so column c has no
+// entries below block row c - jbeg, every reflector j keeps that shape, and its vector vanishes
+// below block row j - jbeg; lanes whose whole segment lies below it skip the dot and the update
+// (they still take part in the group's butterfly).
+template <typename T, int BR, int QS, bool VREG = true, bool TRI = false>
 __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T* vbuf, T* taub, int& buf,
                                              int jbeg, const LivePattern& lp, int r, bool mycol, int c, int q,
                                              unsigned gm) {
@@ -228,47 +232,57 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
     }
     __syncthreads();
     const T tau = taub[buf];
+    // this lane's rows meet the reflector (always, unless TRI)
+    const bool meets = !TRI || q * RPT <= j - jbeg;
     if (tau != T(0) && c > j && mycol && VREG) {
       T v[RPT];
       const T* seg = vb + q * SS;
-#pragma unroll
-      for (int i = 0; i < RPT; i += 4) {
-        T t4[4];
-        ld4(seg + i, t4);
-        v[i] = t4[0];
-        v[i + 1] = t4[1];
-        v[i + 2] = t4[2];
-        v[i + 3] = t4[3];
-      }
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
-      T wv = group_sum<T, QS>(dot4<T, RPT>(v, B, q == 0 ? *rjc : T(0)), gm);
+      T part = q == 0 ? *rjc : T(0);
+      if (meets) {
+#pragma unroll
+        for (int i = 0; i < RPT; i += 4) {
+          T t4[4];
+          ld4(seg + i, t4);
+          v[i] = t4[0];
+          v[i + 1] = t4[1];
+          v[i + 2] = t4[2];
+          v[i + 3] = t4[3];
+        }
+        part = dot4<T, RPT>(v, B, part);
+      }
+      T wv = group_sum<T, QS>(part, gm);
       wv *= tau;
       if (q == 0) *rjc -= wv;
-      axpy_neg<T, RPT>(wv, v, B);
+      if (meets) axpy_neg<T, RPT>(wv, v, B);
     } else if (tau != T(0) && c > j && mycol) {
       const T* seg = vb + q * SS;
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
       T wp[4] = {q == 0 ? *rjc : T(0), T(0), T(0), T(0)};
+      if (meets) {
 #pragma unroll
-      for (int i = 0; i < RPT; i += 4) {
-        T t4[4];
-        ld4(seg + i, t4);
-        wp[0] += t4[0] * B[i];
-        wp[1] += t4[1] * B[i + 1];
-        wp[2] += t4[2] * B[i + 2];
-        wp[3] += t4[3] * B[i + 3];
+        for (int i = 0; i < RPT; i += 4) {
+          T t4[4];
+          ld4(seg + i, t4);
+          wp[0] += t4[0] * B[i];
+          wp[1] += t4[1] * B[i + 1];
+          wp[2] += t4[2] * B[i + 2];
+          wp[3] += t4[3] * B[i + 3];
+        }
       }
       T wv = group_sum<T, QS>((wp[0] + wp[1]) + (wp[2] + wp[3]), gm);
       wv *= tau;
       if (q == 0) *rjc -= wv;
+      if (meets) {
 #pragma unroll
-      for (int i = 0; i < RPT; i += 4) {
-        T t4[4];
-        ld4(seg + i, t4);
-        B[i] -= wv * t4[0];
-        B[i + 1] -= wv * t4[1];
-        B[i + 2] -= wv * t4[2];
-        B[i + 3] -= wv * t4[3];
+        for (int i = 0; i < RPT; i += 4) {
+          T t4[4];
+          ld4(seg + i, t4);
+          B[i] -= wv * t4[0];
+          B[i + 1] -= wv * t4[1];
+          B[i + 2] -= wv * t4[2];
+          B[i + 3] -= wv * t4[3];
+        }
       }
     }
     buf ^= 1;
@@ -312,7 +326,8 @@ __global__ void __launch_bounds__(1024) k_tsqr_leaf_rs(Src src, LivePattern lp, 
 
 // One level of the binary merge tree, row-split: output m = QR([R_{2m}; R_{2m+1}]).R
 template <typename T, int BR, int QS, bool VREG = true>
-__global__ void __launch_bounds__(1024) k_tsqr_merge_rs(LivePattern lp, int nin, const double* __restrict__ Rin,
+__global__ void __launch_bounds__(BR == 160 ? 640 : 1024) k_tsqr_merge_rs(LivePattern lp, int nin,
+                                                                         const double* __restrict__ Rin,
                                                         double* __restrict__ Rout) {
   extern __shared__ __align__(16) unsigned char tsqr_smem[];
   constexpr int RPT = RsGeom<T, BR, QS>::RPT, SS = RsGeom<T, BR, QS>::SS;
@@ -347,7 +362,7 @@ __global__ void __launch_bounds__(1024) k_tsqr_merge_rs(LivePattern lp, int nin,
       B[i] = (mycol && row < ncap) ? (T)Rb[(size_t)row * ncap + c] : T(0);
     }
     // rows i0.. of an upper-triangular factor vanish in columns < i0
-    hh_absorb_rs<T, BR, QS, VREG>(Rs, ncap, B, vbuf, taub, buf, i0, lp, r, mycol, c, q, gm);
+    hh_absorb_rs<T, BR, QS, VREG, true>(Rs, ncap, B, vbuf, taub, buf, i0, lp, r, mycol, c, q, gm);
   }
   __syncthreads();
   write_R<T, BR>(Rs, ncap, Ro);
@@ -380,28 +395,44 @@ tt_status run_tsqr_rs(cudaStream_t s, int num_sms, const Src& src, LivePattern l
   return merge_tree<T>(s, lp, (int)L, ws_a, ws_b, Rfinal);
 }
 
+// Rows of the second factor the row-split merge absorbs at a time.  FP64: 64 (a 160-column
+// level: 288 reflector steps instead of 480), its lanes reading the reflector from shared memory
+// so that the longer row segments stay within 64 registers (measured 15.4 -> 14.4 ms of merges
+// per step).  FP32: 64 rows with the reflector in registers up to 64 columns; wider factors are
+// up to 160 columns are absorbed 160 rows at a time (one block: 160 reflector steps instead of
+// 288 at 160 columns), the reflector read from shared memory, lanes below the reflector idle;
+// that kernel is launched with at most 640 threads, which leaves it 96 registers a thread.
+template <typename T>
+__host__ __device__ inline int merge_rs_rows(int ncap) {
+  return (sizeof(T) == 4 && ncap > 64 && ncap <= 160) ? 160 : 64;
+}
+template <typename T>
+__host__ __device__ inline size_t merge_rs_smem_bytes(int ncap) {
+  return merge_rs_rows<T>(ncap) == 160 ? tsqr_rs_smem_bytes<T, 160, 4>(ncap) : tsqr_rs_smem_bytes<T, 64, 4>(ncap);
+}
+
 // Merge tree of the TSQR: levels of pairwise QRs of stacked R factors, the last one in ws_a or
 // ws_b.  Every leaf kernel merges with the row-split merge (measured faster than the
 // column-owner merge for every pass shape tried) where 4 ncap <= 1024 lanes, else with the
 // column-owner merge.
 template <typename T>
 tt_status merge_tree(cudaStream_t s, LivePattern lp, int nleaves, double* ws_a, double* ws_b, double** Rfinal) {
-  constexpr int MBR = sizeof(T) == 4 ? 64 : 32;  // rows of the second factor absorbed at a time
-  // FP64: the row-split merge absorbs 64 rows at a time (a 160-column level: 288 reflector steps
-  // instead of 480), its lanes reading the reflector from shared memory so that the longer row
-  // segments stay within 64 registers (measured 15.4 -> 14.4 ms of merges per step).  FP32 keeps
-  // 64 rows with the reflector in registers (96 rows with reloads measured slower).
-  constexpr int RBR = 64;
+  constexpr int MBR = sizeof(T) == 4 ? 64 : 32;  // rows of the column-owner merge's blocks
   constexpr bool RVREG = sizeof(T) == 4;
   const int ncap = lp.ncap();
   const int rs_threads = tsqr_rs_threads<4>(ncap);
-  const bool rs = rs_threads <= 1024 && tsqr_rs_smem_bytes<T, RBR, 4>(ncap) <= 227 * 1024;
+  const bool rs = rs_threads <= 1024 && merge_rs_smem_bytes<T>(ncap) <= 227 * 1024;
+  const bool wide = merge_rs_rows<T>(ncap) == 160;
+  auto merge64 = k_tsqr_merge_rs<T, 64, 4, RVREG>;
+  // FP32 only (the FP64 merge never takes 160-row blocks)
+  auto merge160 = k_tsqr_merge_rs<float, 160, 4, false>;
   size_t smem;
   int threads;
   if (rs) {
-    smem = tsqr_rs_smem_bytes<T, RBR, 4>(ncap);
+    smem = merge_rs_smem_bytes<T>(ncap);
     threads = rs_threads;
-    if (const tt_status a = smem_optin(k_tsqr_merge_rs<T, RBR, 4, RVREG>, smem); a != TT_OK) return a;
+    const tt_status a = wide ? smem_optin(merge160, smem) : smem_optin(merge64, smem);
+    if (a != TT_OK) return a;
   } else {
     smem = tsqr_smem_bytes<T, MBR>(ncap);
     threads = ((ncap + 31) / 32) * 32;
@@ -414,8 +445,10 @@ tt_status merge_tree(cudaStream_t s, LivePattern lp, int nleaves, double* ws_a, 
   int n = nleaves;
   while (n > 1) {
     const int m = (n + 1) / 2;
-    if (rs)
-      k_tsqr_merge_rs<T, RBR, 4, RVREG><<<m, threads, smem, s>>>(lp, n, in, out);
+    if (rs && wide)
+      merge160<<<m, threads, smem, s>>>(lp, n, in, out);
+    else if (rs)
+      merge64<<<m, threads, smem, s>>>(lp, n, in, out);
     else
       k_tsqr_merge<T, MBR><<<m, threads, smem, s>>>(lp, n, in, out);
     count_launch();

@@ -84,11 +84,13 @@ def leaf_touch(prec, variant, ncap, br):
     return end, vec
 
 
-def merge_touch(prec, ncap, threads):
+def merge_touch(prec, ncap, threads, rows):
     sz = 8 if prec == "fp64" else 4
     R4 = tri_elems(ncap)
-    if threads >= 4 * ncap:  # row-split merge, 64 rows of the second factor at a time
-        QS, RPT = 4, 16
+    if threads >= 4 * ncap:  # row-split merge: 64 rows of the second factor at a time, FP32 160
+        # from 65 to 160 columns (one block at 160 columns)
+        assert rows == (160 if sz == 4 and 64 < ncap <= 160 else 64)
+        QS, RPT = 4, rows // 4
         SS = RPT + 4
         vec = [(sz * (R4 + buf * QS * SS + q * SS + i), 16) for buf in (0, 1) for q in range(QS)
                for i in range(0, RPT, 4)]
@@ -132,7 +134,7 @@ def check(g, prec, variant, ncap, nrows):
     assert end <= g["leaf_smem"] <= 227 * 1024
     for off, width in vec:
         assert off % width == 0 and off + width <= g["leaf_smem"]
-    mend, mvec = merge_touch(prec, ncap, g["merge_threads"])
+    mend, mvec = merge_touch(prec, ncap, g["merge_threads"], g["merge_rows"])
     assert mend <= g["merge_smem"] <= 227 * 1024
     for off, width in mvec:
         assert off % width == 0 and off + width <= g["merge_smem"]
