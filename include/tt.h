@@ -296,9 +296,9 @@ tt_status tt_axpy(tt_context *ctx, double alpha, const tt_tensor *x, tt_tensor *
  * full contraction of two TTs among the basic TT operations the solver relies on (Sec. 3.1:
  * addition, integration, rounding), which gives the Frobenius norms behind the relative errors
  * of Sec. 5.4 (||x - y||^2 = <x,x> - 2<x,y> + <y,y>).  First core: W1 = Z_x^T Z_y (a reduction
- * over the merged rows), then the small cores.  x and y: equal d and mode sizes (else
- * TT_ERR_SHAPE), any dtype each.  out_dev is a device double owned by the caller, written
- * asynchronously on the context's stream. */
+ * over the merged rows), then the small cores.  x and y: equal d, mode sizes and dtype (else
+ * TT_ERR_SHAPE).  out_dev is a device double owned by the caller, written asynchronously on the
+ * context's stream. */
 tt_status tt_dot(tt_context *ctx, const tt_tensor *x, const tt_tensor *y, double *out_dev);
 
 /* In-place SVD-based rounding (Sec. 3.1 footnote; Oseledets 2011): left-to-right QR
