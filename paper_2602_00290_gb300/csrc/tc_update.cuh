@@ -20,7 +20,8 @@
 
 namespace ttk {
 
-constexpr int kTcRows = 128;  // rows per tile: the M of one MMA, one TMEM lane per row
+constexpr int kTcRows = 128;     // rows per tile: the M of one MMA, one TMEM lane per row
+constexpr int kTcThreads = 512;  // 16 warps: the tile phases are latency-bound at 8
 
 // Output columns of the tensor-core update: kcap rounded up to a multiple of 16 (the MMA's N).
 __host__ __device__ inline int update_tc_n(int kcap) { return (kcap + 15) & ~15; }
@@ -55,10 +56,11 @@ __device__ __forceinline__ unsigned tc_row_flags(const SrcStencil<S>& src, unsig
   return f | ((k % (unsigned)src.G) << 8);
 }
 
-// NB row blocks (1 + 2 d_X) of RCAP columns each: K = NB RCAP, compile-time.  256 threads: all of
-// them stage, split and run the epilogue; warps 0-3 read the accumulators (TMEM lanes = rows).
+// NB row blocks (1 + 2 d_X) of RCAP columns each: K = NB RCAP, compile-time.  kTcThreads threads:
+// all of them stage, split and run the epilogue; warps 0-3 read the accumulators (TMEM lanes =
+// rows).
 template <class Epi, int NB, int RCAP>
-__global__ void __launch_bounds__(256, 1) k_update_tc(SrcStencil<float> src, LivePattern lp, long nrows,
+__global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> src, LivePattern lp, long nrows,
                                                       const double* __restrict__ W, int kcap, Epi epi,
                                                       double* __restrict__ partials) {
   extern __shared__ __align__(1024) unsigned char tcu_smem[];
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(256, 1) k_update_tc(SrcStencil<float> src, Liv
     // warp four granules of them (whole 32-byte sectors of every row it reads)
     constexpr int per_block = kTcRows * GPR;
 #pragma unroll 4
-    for (int i = tid; i < NB * per_block; i += 256) {
+    for (int i = tid; i < NB * per_block; i += kTcThreads) {
       const int b = i / per_block, rem = i - b * per_block;
       const int r8 = rem >> 3, g = r8 % GPR, m = (r8 / GPR) * 8 + (rem & 7);
       long k = row0 + m;
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(256, 1) k_update_tc(SrcStencil<float> src, Liv
     // neighbours to differences with the centre rows (L -> C - L, H -> H - C), then every value
     // to its TF32 part (A hi) and rounded remainder (A lo); a thread takes 4 consecutive K values
     // of a row (16-byte vectors; a warp's 32 rows fall on distinct banks)
-    for (int i = tid; i < kTcRows * GPR; i += 256) {
+    for (int i = tid; i < kTcRows * GPR; i += kTcThreads) {
       const int g = i / kTcRows, m = i - g * kTcRows;
       const uint32_t oc = tc::kmajor_off(m, 4 * g, K) >> 2;
       const float4 c = *reinterpret_cast<const float4*>(Ahi + oc);
@@ -288,7 +290,7 @@ tt_status launch_update_tc_k(cudaStream_t s, int num_sms, const SrcStencil<float
   if (grid > ntiles) grid = ntiles > 0 ? ntiles : 1;
   if (grid_out) *grid_out = grid;
   TimerScope scope(cat, s);
-  kern<<<(unsigned)grid, 256, smem, s>>>(src, lp, nrows, W, kcap, epi, partials);
+  kern<<<(unsigned)grid, kTcThreads, smem, s>>>(src, lp, nrows, W, kcap, epi, partials);
   count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
