@@ -918,6 +918,220 @@ __global__ void __launch_bounds__(1024) k_jacobi_rt(int n, const double* __restr
   }
 }
 
+
+// The same sweep with each pair's columns in registers, for n up to 160 columns: lane tl of a team
+// of ts lanes holds the contiguous elements [tl vv, tl vv + vv) of both columns of its pair, vv a
+// multiple of 4 with vv / 4 odd, so that the 16-byte loads and stores of the 8 lanes served
+// together fall on distinct banks; columns are padded with zeros to ts vv = ld elements.  The
+// dot products and the rotation run on the packed two-lane FP32 FMA.  The sweep is bound by the
+// dependent chain of a round (loads, dots, team sums, rotation, stores, barrier), so:
+//   * R is scaled by 1 / ||R||_F as it is loaded (every column norm <= 1), the test for a pair
+//     becomes g^2 > tol^2 a b without square roots, and the raw values are scaled back at the end;
+//   * the rotation takes the fast reciprocal and reciprocal square root (a few ulp: cs^2 + sn^2 = 1
+//     to FP32 accuracy, and the FP64 refinement that follows the FP32 sweep absorbs the rest);
+//   * rows of R below 2^-30 ||R||_F (the zero rows of capacity columns beyond the live ranks, and
+//     round-off rows) stay out of the sweep, as in k_jacobi_rt's statement of the error: they
+//     change R by less than sqrt(n) 2^-30 ||R||_F; their columns of U and raw values are zero.
+// The team geometry (ts, vv, ld) is that of all n columns; the rounds run over the nk kept ones.
+struct JrtRegGeom {
+  int ts, vv, ld;
+};
+constexpr int kJrtThreadsReg = 640;  // 80 pairs x 8 lanes at 160 columns
+constexpr int kJrtMaxV = 20;
+constexpr float kJrtDropRel = 9.31322574615478515625e-10f;  // 2^-30
+__host__ __device__ inline JrtRegGeom jrt_reg_geom(int n) {
+  JrtRegGeom g;
+  const int np = n + (n & 1);
+  int ts = 32;
+  while (ts > 1 && (np / 2) * ts > kJrtThreadsReg) ts >>= 1;
+  int v = (n + ts - 1) / ts;
+  v = (v + 3) & ~3;
+  if (((v / 4) & 1) == 0) v += 4;
+  g.ts = ts;
+  g.vv = v;
+  g.ld = ts * v;
+  return g;
+}
+__host__ __device__ inline bool jrt_reg_fits(int n) {
+  return n >= 2 && n <= kJrtThreadsReg / 4 && jrt_reg_geom(n).vv <= kJrtMaxV;
+}
+// the column copy, then the kept-row list
+__host__ __device__ inline size_t jrt_reg_smem_bytes(int n) {
+  return sizeof(float) * (size_t)n * jrt_reg_geom(n).ld + sizeof(int) * (size_t)n;
+}
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+// Rotation of the pair (a = |x|^2, b = |y|^2, g = x.y) of columns scaled to norms <= 1, or false
+// when the pair is orthogonal to the working accuracy (or below the round-off level).
+__device__ __forceinline__ bool jrt_rotation_scaled(float a, float b, float g, float tol2, float floor_abs,
+                                                    float& cs, float& sn) {
+  if (!(fabsf(g) > floor_abs && g * g > tol2 * a * b)) return false;
+  const float zeta = __fdividef(b - a, 2.f * g);  // |2g| > 2e-14: inside the fast quotient's range
+  const float az = fabsf(zeta);
+  float t;
+  if (az > 1e18f) {
+    t = __fdividef(0.5f, zeta);
+  } else {
+    const float s = fmaf(zeta, zeta, 1.f);
+    t = copysignf(__fdividef(1.f, az + s * rsqrtf(s)), zeta);
+  }
+  cs = rsqrtf(fmaf(t, t, 1.f));
+  sn = cs * t;
+  return true;
+}
+
+__global__ void __launch_bounds__(kJrtThreadsReg) k_jacobi_rt_reg(int n, const double* __restrict__ R,
+                                                                  double* __restrict__ U, double* __restrict__ raw,
+                                                                  int maxsweep, DevCtrl* ctrl) {
+  extern __shared__ __align__(16) unsigned char jrr_smem[];
+  const JrtRegGeom geo = jrt_reg_geom(n);
+  const int ts = geo.ts, vv = geo.vv, ld = geo.ld;
+  float* At = reinterpret_cast<float*>(jrr_smem);
+  int* kept = reinterpret_cast<int*>(At + (size_t)n * ld);
+  __shared__ int rot_flag, nk_s;
+  __shared__ double red[33];
+  __shared__ float rnorm[kJrtThreadsReg / 8 * 2];  // row norms^2 (n <= 160), FP32
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // FP64 Frobenius norm and FP32 row norms of R
+  double fl = 0.0;
+  for (int c = warp; c < n; c += nwarps) {
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) s2 += R[(size_t)c * n + i] * R[(size_t)c * n + i];
+    s2 = warp_sum(s2);
+    if (lane == 0) rnorm[c] = (float)s2;
+    fl += s2;
+  }
+  if (lane == 0) red[warp] = fl;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0;
+    for (int w = 0; w < nwarps; ++w) f += red[w];
+    red[32] = f;
+    const float thr = (float)(f * (double)kJrtDropRel * (double)kJrtDropRel);
+    int m = 0;
+    for (int c = 0; c < n; ++c)
+      if (rnorm[c] > thr) kept[m++] = c;
+    nk_s = m;
+  }
+  __syncthreads();
+  const int nk = nk_s;
+  const double fro = sqrt(red[32]);
+  const float scale = fro > 0.0 ? (float)(1.0 / fro) : 0.f;
+  for (int idx = threadIdx.x; idx < nk * ld; idx += blockDim.x) {
+    const int s = idx / ld, i = idx - (idx / ld) * ld;
+    At[idx] = (i < n) ? (float)R[(size_t)kept[s] * n + i] * scale : 0.f;
+  }
+  __syncthreads();
+  const float rel_tol = 4.f * sqrtf((float)n) * 1.1920929e-7f;
+  const float tol2 = rel_tol * rel_tol;
+  const float floor_abs = 1e-14f;  // of the scaled ||R||_F^2 = 1
+  const int np = nk + (nk & 1);
+  const int team = threadIdx.x / ts, tl = threadIdx.x & (ts - 1), nteams = blockDim.x / ts;
+  const unsigned tmask = (ts == 32) ? 0xffffffffu : (((1u << ts) - 1u) << (lane & ~(ts - 1)));
+  const int nv4 = vv / 4;
+  int sweeps = 0;
+  for (int sweep = 0; sweep < maxsweep && np > 1; ++sweep) {
+    if (threadIdx.x == 0) rot_flag = 0;
+    __syncthreads();
+    for (int round = 0; round < np - 1; ++round) {
+      for (int pr = team; pr < np / 2; pr += nteams) {
+        int p, q;
+        if (pr == 0) {
+          p = round;
+          q = np - 1;
+        } else {
+          p = round + pr;
+          if (p >= np - 1) p -= np - 1;
+          q = round - pr;
+          if (q < 0) q += np - 1;
+        }
+        if (p >= nk || q >= nk) continue;
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        float4* ap = reinterpret_cast<float4*>(At + (size_t)p * ld + tl * vv);
+        float4* aq = reinterpret_cast<float4*>(At + (size_t)q * ld + tl * vv);
+        float4 x[kJrtMaxV / 4], y[kJrtMaxV / 4];
+        float2 sa0 = f2(0.f, 0.f), sa1 = sa0, sb0 = sa0, sb1 = sa0, sg0 = sa0, sg1 = sa0;
+#pragma unroll
+        for (int k = 0; k < kJrtMaxV / 4; ++k) {
+          if (k < nv4) {
+            x[k] = ap[k];
+            y[k] = aq[k];
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kJrtMaxV / 4; ++k) {
+          if (k < nv4) {
+            const float2 xl = f2(x[k].x, x[k].y), xh = f2(x[k].z, x[k].w);
+            const float2 yl = f2(y[k].x, y[k].y), yh = f2(y[k].z, y[k].w);
+            sa0 = __ffma2_rn(xl, xl, sa0);
+            sa1 = __ffma2_rn(xh, xh, sa1);
+            sb0 = __ffma2_rn(yl, yl, sb0);
+            sb1 = __ffma2_rn(yh, yh, sb1);
+            sg0 = __ffma2_rn(xl, yl, sg0);
+            sg1 = __ffma2_rn(xh, yh, sg1);
+          }
+        }
+        float a = (sa0.x + sa0.y) + (sa1.x + sa1.y);
+        float b = (sb0.x + sb0.y) + (sb1.x + sb1.y);
+        float g = (sg0.x + sg0.y) + (sg1.x + sg1.y);
+        for (int o = 1; o < ts; o <<= 1) {
+          a += __shfl_xor_sync(tmask, a, o);
+          b += __shfl_xor_sync(tmask, b, o);
+          g += __shfl_xor_sync(tmask, g, o);
+        }
+        float cs, sn;
+        if (jrt_rotation_scaled(a, b, g, tol2, floor_abs, cs, sn)) {
+          const float2 c2 = f2(cs, cs), s2 = f2(sn, sn), ns2 = f2(-sn, -sn);
+#pragma unroll
+          for (int k = 0; k < kJrtMaxV / 4; ++k) {
+            if (k < nv4) {
+              const float2 xl = f2(x[k].x, x[k].y), xh = f2(x[k].z, x[k].w);
+              const float2 yl = f2(y[k].x, y[k].y), yh = f2(y[k].z, y[k].w);
+              const float2 pl = __ffma2_rn(c2, xl, __fmul2_rn(ns2, yl));
+              const float2 ph = __ffma2_rn(c2, xh, __fmul2_rn(ns2, yh));
+              const float2 ql = __ffma2_rn(s2, xl, __fmul2_rn(c2, yl));
+              const float2 qh = __ffma2_rn(s2, xh, __fmul2_rn(c2, yh));
+              ap[k] = make_float4(pl.x, pl.y, ph.x, ph.y);
+              aq[k] = make_float4(ql.x, ql.y, qh.x, qh.y);
+            }
+          }
+          if (tl == 0) rot_flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int f = rot_flag;
+    __syncthreads();
+    sweeps = sweep + 1;
+    if (!f) break;
+  }
+  if (ctrl && threadIdx.x == 0) {
+    atomicMax(&ctrl->jac_sweeps_max, sweeps);
+    atomicAdd(&ctrl->jac_calls, 1);
+    atomicAdd(&ctrl->jac_sweeps_sum, sweeps);
+  }
+  // normalised columns -> U[i][s] (s < nk), zero columns and raw values beyond; raw in R's scale
+  for (int c = warp; c < n; c += nwarps) {
+    if (c >= nk) {
+      for (int i = lane; i < n; i += 32) U[(size_t)i * n + c] = 0.0;
+      if (lane == 0) raw[c] = 0.0;
+      continue;
+    }
+    const float* ac = At + (size_t)c * ld;
+    double s2 = 0.0;
+    for (int i = lane; i < n; i += 32) s2 += (double)ac[i] * (double)ac[i];
+    s2 = warp_sum(s2);
+    const double inv = (s2 > 0.0) ? 1.0 / sqrt(s2) : 0.0;
+    for (int i = lane; i < n; i += 32) U[(size_t)i * n + c] = (double)ac[i] * inv;
+    if (lane == 0) raw[c] = sqrt(s2) * fro;
+  }
+}
+
 // The same FP32 one-sided Jacobi on R^T for n <= 32 in one warp: lane c holds column c of R^T
 // (row c of R) in registers, a round exchanges columns between the two lanes of each pair by
 // shuffles, and both lanes compute the rotation from the pair in the same order (x = the lower
@@ -1211,6 +1425,7 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   double* U = ws.take<double>((size_t)cols * cols);
   double* P = ws.take<double>((size_t)rows * cols);
   double* tmp = ws.take<double>(cols);
+  const bool reg = cols > 32 && jrt_reg_fits(cols) && jrt_reg_smem_bytes(cols) <= 200 * 1024;
   const size_t at_bytes = sizeof(float) * (size_t)cols * jrt_ld(cols);
   const bool in_smem = at_bytes <= 200 * 1024;
   float* gwork = in_smem ? nullptr : ws.take<float>((size_t)cols * jrt_ld(cols));
@@ -1220,12 +1435,15 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   double* R = nullptr;
   tt_status st = run_tsqr<float, 64>(s, num_sms, src, lp, rows, 8, a, b, &R);
   if (st != TT_OK) return st;
-  const size_t smem = in_smem ? at_bytes : 0;
   if (cols <= 32) {
     k_jacobi_warp<<<1, 32, 0, s>>>(cols, R, U, raw, 40, ctrl); count_launch();
+  } else if (reg) {
+    const size_t smem = jrt_reg_smem_bytes(cols);
+    if (const tt_status a = smem_optin(k_jacobi_rt_reg, smem); a != TT_OK) return a;
+    k_jacobi_rt_reg<<<1, kJrtThreadsReg, smem, s>>>(cols, R, U, raw, 40, ctrl); count_launch();
   } else if (in_smem) {
-    if (const tt_status a = smem_optin(k_jacobi_rt<float, true>, smem); a != TT_OK) return a;
-    k_jacobi_rt<float, true><<<1, 1024, smem, s>>>(cols, R, U, raw, 40, nullptr, ctrl); count_launch();
+    if (const tt_status a = smem_optin(k_jacobi_rt<float, true>, at_bytes); a != TT_OK) return a;
+    k_jacobi_rt<float, true><<<1, 1024, at_bytes, s>>>(cols, R, U, raw, 40, nullptr, ctrl); count_launch();
   } else {
     k_jacobi_rt<float, false><<<1, 1024, 0, s>>>(cols, R, U, raw, 40, gwork, ctrl); count_launch();
   }
