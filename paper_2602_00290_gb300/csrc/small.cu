@@ -168,21 +168,11 @@ __global__ void __launch_bounds__(1024) k_orthonormalise(int nv, int ldv, double
   }
 }
 
-// k_orthonormalise for nv <= 32 rows and ldv <= 32 columns in one warp, V staged in shared
-// memory: column dots with one lane per earlier column, the update with one lane per row, warp
-// shuffles for norms; no block-wide barriers.  Same algorithm and outputs.
-__global__ void __launch_bounds__(32) k_orthonormalise_warp(int nv, int ldv, double* __restrict__ Vg,
-                                                            const int* kptr, int rowmod, const int* rowlive_ptr) {
-  __shared__ double V[32 * 33];  // row i at V[i * 33 + c]
-  __shared__ double h[32];
-  const int lane = threadIdx.x;
-  const int k = *kptr;
-  const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
-  for (int idx = lane; idx < nv * ldv; idx += 32) {
-    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
-    V[i * 33 + c] = Vg[idx];
-  }
-  __syncwarp();
+// k_orthonormalise for nv <= 32 rows and k <= 32 columns in one warp, on V staged in shared
+// memory (row i at V[i * 33 + c]): column dots with one lane per earlier column, the update with
+// one lane per row, warp shuffles for norms; no block-wide barriers.  Same algorithm and outputs.
+__device__ void cgs2_warp_staged(int nv, int k, int rowmod, int rowlive, double* V, double* h) {
+  const int lane = threadIdx.x & 31;
   for (int j = 0; j < k; ++j) {
     int cand = -1;
     for (int attempt = 0; attempt <= nv; ++attempt) {
@@ -197,15 +187,31 @@ __global__ void __launch_bounds__(32) k_orthonormalise_warp(int nv, int ldv, dou
       double x = (lane < nv) ? V[lane * 33 + j] : 0.0;
       const double n0 = sqrt(warp_sum(x * x));
       for (int pass = 0; pass < 2; ++pass) {
-        double hc = 0.0;
-        if (lane < j)
-          for (int i = 0; i < nv; ++i) hc += V[i * 33 + lane] * V[i * 33 + j];
-        h[lane] = hc;
+        // both dependent FP64 chains in four partial sums
+        double h0 = 0.0, h1 = 0.0, h2 = 0.0, h3 = 0.0;
+        if (lane < j) {
+          int i = 0;
+          for (; i + 3 < nv; i += 4) {
+            h0 += V[i * 33 + lane] * V[i * 33 + j];
+            h1 += V[(i + 1) * 33 + lane] * V[(i + 1) * 33 + j];
+            h2 += V[(i + 2) * 33 + lane] * V[(i + 2) * 33 + j];
+            h3 += V[(i + 3) * 33 + lane] * V[(i + 3) * 33 + j];
+          }
+          for (; i < nv; ++i) h0 += V[i * 33 + lane] * V[i * 33 + j];
+        }
+        h[lane] = (h0 + h1) + (h2 + h3);
         __syncwarp();
         if (lane < nv) {
-          double v = V[lane * 33 + j];
-          for (int c = 0; c < j; ++c) v -= h[c] * V[lane * 33 + c];
-          V[lane * 33 + j] = v;
+          double v0 = V[lane * 33 + j], v1 = 0.0, v2 = 0.0, v3 = 0.0;
+          int c = 0;
+          for (; c + 3 < j; c += 4) {
+            v0 -= h[c] * V[lane * 33 + c];
+            v1 -= h[c + 1] * V[lane * 33 + c + 1];
+            v2 -= h[c + 2] * V[lane * 33 + c + 2];
+            v3 -= h[c + 3] * V[lane * 33 + c + 3];
+          }
+          for (; c < j; ++c) v0 -= h[c] * V[lane * 33 + c];
+          V[lane * 33 + j] = (v0 + v1) + (v2 + v3);
         }
         __syncwarp();
       }
@@ -219,7 +225,130 @@ __global__ void __launch_bounds__(32) k_orthonormalise_warp(int nv, int ldv, dou
     }
   }
   __syncwarp();
+}
+
+__global__ void __launch_bounds__(32) k_orthonormalise_warp(int nv, int ldv, double* __restrict__ Vg,
+                                                            const int* kptr, int rowmod, const int* rowlive_ptr) {
+  __shared__ double V[32 * 33];  // row i at V[i * 33 + c]
+  __shared__ double h[32];
+  const int lane = threadIdx.x;
+  const int k = *kptr;
+  const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
   for (int idx = lane; idx < nv * ldv; idx += 32) {
+    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+    V[i * 33 + c] = Vg[idx];
+  }
+  __syncwarp();
+  cgs2_warp_staged(nv, k, rowmod, rowlive, V, h);
+  for (int idx = lane; idx < nv * ldv; idx += 32) {
+    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+    Vg[idx] = V[i * 33 + c];
+  }
+}
+
+// The first k columns of V (nv <= 32 rows, k <= ldv <= 32) made orthonormal by Newton-Schulz steps
+// towards the polar factor, V <- V (3 I - V^T V) / 2, when they are already close to
+// orthonormal (the right singular vectors of a Jacobi sweep, normalised in FP64): with
+// e = max |V^T V - I| <= 1e-4 each step takes e to about 1.5 e^2, so one step suffices for e <=
+// 1e-8 (FP64 Jacobi) and two for FP32-accurate columns.  The span of the columns is unchanged and
+// the columns move by O(e).  Other inputs (a vanishing or far from orthogonal column) take the
+// column-by-column Gram-Schmidt of k_orthonormalise_warp, which also replaces dependent columns.
+// Four warps compute V^T V and the update as small matrix products in shared memory: no
+// dependent chain longer than nv, against the column-by-column chains of Gram-Schmidt.
+__global__ void __launch_bounds__(128) k_orthonormalise_polar(int nv, int ldv, double* __restrict__ Vg,
+                                                              const int* kptr, int rowmod, const int* rowlive_ptr) {
+  __shared__ double V[32 * 33];
+  __shared__ double G[32 * 33];
+  __shared__ double h[32];
+  __shared__ double emax[4];
+  __shared__ int nsteps;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int k = *kptr;
+  const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
+  for (int idx = tid; idx < nv * ldv; idx += blockDim.x) {
+    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+    V[i * 33 + c] = Vg[idx];
+  }
+  __syncthreads();
+  // G = V^T V over the first k columns; returns max |G - I| over this thread's entries
+  auto gram = [&]() -> double {
+    double e = 0.0;
+    for (int idx = tid; idx < k * k; idx += blockDim.x) {
+      const int a = idx / k, b = idx - (idx / k) * k;
+      double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+      int i = 0;
+      for (; i + 3 < nv; i += 4) {
+        g0 += V[i * 33 + a] * V[i * 33 + b];
+        g1 += V[(i + 1) * 33 + a] * V[(i + 1) * 33 + b];
+        g2 += V[(i + 2) * 33 + a] * V[(i + 2) * 33 + b];
+        g3 += V[(i + 3) * 33 + a] * V[(i + 3) * 33 + b];
+      }
+      for (; i < nv; ++i) g0 += V[i * 33 + a] * V[i * 33 + b];
+      const double g = (g0 + g1) + (g2 + g3);
+      G[a * 33 + b] = g;
+      const double d = fabs(g - (a == b ? 1.0 : 0.0));
+      e = (d > e || d != d) ? d : e;  // a NaN counts as far from orthonormal
+    }
+    return e;
+  };
+  double e = gram();
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, e, o);
+    e = (t > e || t != t) ? t : e;
+  }
+  if (lane == 0) emax[warp] = e;
+  __syncthreads();
+  if (tid == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = (emax[w] > m || emax[w] != emax[w]) ? emax[w] : m;
+    // no step below the FP64 round-off of a k-term sum; one from e <= 1e-8; two from e <= 1e-4;
+    // otherwise Gram-Schmidt (-1)
+    const double floor64 = 8.0 * 2.220446049250313e-16 * (k > 1 ? k : 1);
+    nsteps = (m <= floor64) ? 0 : (m <= 1e-8) ? 1 : (m <= 1e-4) ? 2 : -1;
+  }
+  __syncthreads();
+  const int ns = nsteps;
+  if (ns < 0) {
+    if (warp == 0) cgs2_warp_staged(nv, k, rowmod, rowlive, V, h);
+    __syncthreads();
+  }
+  for (int step = 0; step < ns; ++step) {
+    if (step > 0) {
+      (void)gram();
+      __syncthreads();
+    }
+    // V[i][b] <- 1.5 V[i][b] - 0.5 sum_a V[i][a] G[a][b] (b < k): nv k <= 1024 entries, 8 a thread
+    double w[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = tid + r * (int)blockDim.x;
+      w[r] = 0.0;
+      if (idx < nv * k) {
+        const int i = idx / k, b = idx - (idx / k) * k;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int a = 0;
+        for (; a + 3 < k; a += 4) {
+          s0 += V[i * 33 + a] * G[a * 33 + b];
+          s1 += V[i * 33 + a + 1] * G[(a + 1) * 33 + b];
+          s2 += V[i * 33 + a + 2] * G[(a + 2) * 33 + b];
+          s3 += V[i * 33 + a + 3] * G[(a + 3) * 33 + b];
+        }
+        for (; a < k; ++a) s0 += V[i * 33 + a] * G[a * 33 + b];
+        w[r] = 1.5 * V[i * 33 + b] - 0.5 * ((s0 + s1) + (s2 + s3));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = tid + r * (int)blockDim.x;
+      if (idx < nv * k) {
+        const int i = idx / k, b = idx - (idx / k) * k;
+        V[i * 33 + b] = w[r];
+      }
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nv * ldv; idx += blockDim.x) {
     const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
     Vg[idx] = V[i * 33 + c];
   }
@@ -262,17 +391,17 @@ __global__ void __launch_bounds__(1024) k_cgs2_sigma(int nv, int ldv, double* __
   }
 }
 
-// ---- CholeskyQR2 of the first K columns of V (FP64) ----------------------------------------
-// The same factorisation V[:, :K] = Q T as Gram-Schmidt in column order, computed as two passes
-// of: Gram matrix G = V^T V (row chunks spread over many CTAs), upper Cholesky factor
-// G = T^T T (one CTA), V <- V T^{-1} (explicit triangular inverse in one CTA, then a row-parallel
-// product over many CTAs).  Column j of T depends on columns 0..j of V only, so leading columns
-// are unaffected by what follows them.  The columns here are
-// P = A U for nearly orthogonal U, i.e. graded: V = W D with D the column norms and W of
-// condition near 1 on the columns that matter; Cholesky and triangular solves are invariant
-// under that scaling, so two passes give FP64-orthonormal Q and |T_jj| to FP64 relative
-// accuracy.  A column whose Cholesky pivot is at the round-off level of its own diagonal has
-// nothing left beyond the earlier columns: its row of T and its column of Q are set to zero.
+// ---- CholeskyQR of the first K columns of V (FP64) -----------------------------------------
+// The same factorisation V[:, :K] = Q T as Gram-Schmidt in column order, computed as: Gram
+// matrix G = V^T V (row chunks spread over many CTAs), upper Cholesky factor G = T^T T (one
+// CTA), V <- V T^{-1} (explicit triangular inverse in one CTA, then a row-parallel product over
+// many CTAs).  Column j of T depends on columns 0..j of V only, so leading columns are
+// unaffected by what follows them.  The columns here are P = A U for nearly orthogonal U, i.e.
+// graded: V = W D with D the column norms and W of condition near 1 on the columns that matter;
+// Cholesky and triangular solves are invariant under that scaling, so one pass gives Q
+// orthonormal to about kappa(W)^2 eps_64 and |T_jj| to FP64 relative accuracy.  A column whose
+// Cholesky pivot is at the round-off level of its own diagonal has nothing left beyond the
+// earlier columns: its row of T and its column of Q are set to zero.
 
 constexpr int kGramTileRows = 32;   // rows staged in shared memory per step
 constexpr int kGramChunkRows = 64;  // rows per CTA (one partial Gram matrix each)
@@ -355,24 +484,40 @@ __global__ void __launch_bounds__(256) k_chol_upper(int K, const double* __restr
 // M = T^{-1} for the upper-triangular T restricted to its live pivots (T_jj > 0), with zero rows
 // and columns at dead pivots, so that v M equals the forward substitution v T^{-1} over the live
 // pivots (dead columns give 0).  One thread per column of M, back substitution up the column.  One CTA.
+// The reciprocals of the pivots are formed once, in parallel, and each step's dot product runs in
+// four partial sums: on this part an FP64 division or a long dependent FP64 chain inside the
+// sequential substitution costs hundreds of cycles per step.
 __global__ void __launch_bounds__(128) k_tri_inv(int K, const double* __restrict__ T, double* __restrict__ M) {
   extern __shared__ double tis[];
-  double* Ts = tis;          // [K][K]
-  double* Ms = tis + K * K;  // [K][K]
+  double* Ts = tis;              // [K][K]
+  double* Ms = tis + K * K;      // [K][K]
+  double* rinv = tis + 2 * K * K;  // [K] 1 / T_ii at live pivots, else 0
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
     Ts[idx] = T[idx];
     Ms[idx] = 0.0;
   }
   __syncthreads();
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const double tii = Ts[i * K + i];
+    rinv[i] = (tii > 0.0) ? 1.0 / tii : 0.0;
+  }
+  __syncthreads();
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    if (!(Ts[j * K + j] > 0.0)) continue;
-    Ms[j * K + j] = 1.0 / Ts[j * K + j];
+    if (!(rinv[j] > 0.0)) continue;
+    Ms[j * K + j] = rinv[j];
     for (int i = j - 1; i >= 0; --i) {
-      const double tii = Ts[i * K + i];
-      if (!(tii > 0.0)) continue;
-      double acc = 0.0;
-      for (int k = i + 1; k <= j; ++k) acc += Ts[i * K + k] * Ms[k * K + j];
-      Ms[i * K + j] = -acc / tii;
+      const double ri = rinv[i];
+      if (!(ri > 0.0)) continue;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int k = i + 1;
+      for (; k + 3 <= j; k += 4) {
+        a0 += Ts[i * K + k] * Ms[k * K + j];
+        a1 += Ts[i * K + k + 1] * Ms[(k + 1) * K + j];
+        a2 += Ts[i * K + k + 2] * Ms[(k + 2) * K + j];
+        a3 += Ts[i * K + k + 3] * Ms[(k + 3) * K + j];
+      }
+      for (; k <= j; ++k) a0 += Ts[i * K + k] * Ms[k * K + j];
+      Ms[i * K + j] = -((a0 + a1) + (a2 + a3)) * ri;
     }
   }
   __syncthreads();
@@ -406,7 +551,7 @@ __global__ void __launch_bounds__(256) k_rows_times_upper(int nv, int ldv, doubl
 __global__ void k_sig_from_chol(int K, const double* __restrict__ T1, const double* __restrict__ T2,
                                 double* __restrict__ sig) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j < K) sig[j] = T1[(size_t)j * K + j] * T2[(size_t)j * K + j];
+  if (j < K) sig[j] = T1[(size_t)j * K + j] * (T2 ? T2[(size_t)j * K + j] : 1.0);
 }
 
 // Sort the first K columns of V (nv x ldv) and sig[0..K) by decreasing sig (ties by index).
@@ -1135,19 +1280,25 @@ __global__ void __launch_bounds__(kJrtThreadsReg) k_jacobi_rt_reg(int n, const d
 // The same FP32 one-sided Jacobi on R^T for n <= 32 in one warp: lane c holds column c of R^T
 // (row c of R) in registers, a round exchanges columns between the two lanes of each pair by
 // shuffles, and both lanes compute the rotation from the pair in the same order (x = the lower
-// column), so they agree bit for bit.  No barriers.  Same outputs as k_jacobi_rt.
+// column), so they agree bit for bit.  No barriers.  As in k_jacobi_rt_reg, R is scaled to unit
+// Frobenius norm (the pair test needs no square roots), the rotation takes the fast reciprocal
+// and reciprocal square root, and the dot products run in four partial sums (the round is one
+// dependent chain).  Same outputs as k_jacobi_rt.
 __global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restrict__ R, double* __restrict__ U,
                                                     double* __restrict__ raw, int maxsweep, DevCtrl* ctrl) {
   const int lane = threadIdx.x;
+  double f = 0.0;
+  if (lane < n)
+    for (int i = 0; i < n; ++i) f += R[(size_t)lane * n + i] * R[(size_t)lane * n + i];
+  f = warp_sum(f);
+  const double fro = sqrt(f);
+  const float scale = fro > 0.0 ? (float)(1.0 / fro) : 0.f;
   float col[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) col[i] = (lane < n && i < n) ? (float)R[(size_t)lane * n + i] : 0.f;
-  float fro = 0.f;
-#pragma unroll
-  for (int i = 0; i < 32; ++i) fro += col[i] * col[i];
-  fro = warp_sum(fro);
+  for (int i = 0; i < 32; ++i) col[i] = (lane < n && i < n) ? (float)R[(size_t)lane * n + i] * scale : 0.f;
   const float rel_tol = 4.f * sqrtf((float)n) * 1.1920929e-7f;
-  const float floor_abs = 1e-14f * fro;
+  const float tol2 = rel_tol * rel_tol;
+  const float floor_abs = 1e-14f;  // of the scaled ||R||_F^2 = 1
   const int np = n + (n & 1);
   int sweeps = 0;
   for (int sweep = 0; sweep < maxsweep; ++sweep) {
@@ -1168,22 +1319,19 @@ __global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restr
       for (int i = 0; i < 32; ++i) other[i] = __shfl_sync(0xffffffffu, col[i], partner);
       const bool pair = lane < n && partner < n && partner != lane;
       const bool low = lane < partner;
-      float a = 0.f, b = 0.f, g = 0.f;
+      float pa[4] = {0.f, 0.f, 0.f, 0.f}, pb[4] = {0.f, 0.f, 0.f, 0.f}, pg[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 0; i < 32; ++i) {
         const float x = low ? col[i] : other[i], y = low ? other[i] : col[i];
-        a += x * x;
-        b += y * y;
-        g += x * y;
+        pa[i & 3] = fmaf(x, x, pa[i & 3]);
+        pb[i & 3] = fmaf(y, y, pb[i & 3]);
+        pg[i & 3] = fmaf(x, y, pg[i & 3]);
       }
-      if (pair && fabsf(g) > floor_abs && fabsf(g) > rel_tol * sqrtf(a) * sqrtf(b)) {
-        const float zeta = (b - a) / (2.f * g);
-        float t;
-        if (fabsf(zeta) > 1e18f)
-          t = 0.5f / zeta;
-        else  // the divisor lies in [1, 2e18]
-          t = __fdividef(zeta >= 0.f ? 1.f : -1.f, fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-        const float cs = rsqrtf(1.f + t * t), sn = cs * t;
+      const float a = (pa[0] + pa[1]) + (pa[2] + pa[3]);
+      const float b = (pb[0] + pb[1]) + (pb[2] + pb[3]);
+      const float g = (pg[0] + pg[1]) + (pg[2] + pg[3]);
+      float cs, sn;
+      if (pair && jrt_rotation_scaled(a, b, g, tol2, floor_abs, cs, sn)) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float x = low ? col[i] : other[i], y = low ? other[i] : col[i];
@@ -1208,7 +1356,7 @@ __global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restr
 #pragma unroll
     for (int i = 0; i < 32; ++i)
       if (i < n) U[(size_t)i * n + lane] = (double)col[i] * inv;
-    raw[lane] = sqrt(s2);
+    raw[lane] = sqrt(s2) * fro;
   }
 }
 
@@ -1375,15 +1523,19 @@ tt_status svd_right(cudaStream_t s, int num_sms, int m, int n, const double* M, 
   return coop_jacobi(s, num_sms, m, n, At, V, sigma, nullptr, 0, 0, Vout, perm, tmp, ctrl, grid_max);
 }
 
-// V[:, :K] (nv x ldv, row-major) <- Q and sig[j] = |T_jj| of V[:, :K] = Q T, by CholeskyQR2
-// in FP64 for K <= 112, by one-CTA Gram-Schmidt beyond.
-static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K, double* sig, Bump& ws) {
+// V[:, :K] (nv x ldv, row-major) <- Q and sig[j] = |T_jj| of V[:, :K] = Q T, by CholeskyQR in
+// FP64 for K <= 112, by one-CTA Gram-Schmidt beyond.  One pass: the columns are P = A U for U
+// from a converged Jacobi sweep, nearly orthogonal once each is normalised, and the error of a
+// Cholesky factor is governed by the condition number of the column-equilibrated Gram matrix,
+// not by that of P (whose column norms are the singular values), so Q is orthonormal to about
+// kappa(P D^-1)^2 eps_64 in one pass; columns that are numerically dependent in that scaled
+// sense meet a dead pivot (k_chol_upper) and give zero columns, as in the two-pass form.
+static tt_status cholqr_sigma(cudaStream_t s, int nv, int ldv, double* V, int K, double* sig, Bump& ws) {
   const int KK = K * K;
   const int nchunks = (nv + kGramChunkRows - 1) / kGramChunkRows;
   double* part = ws.take<double>((size_t)nchunks * KK);
   double* G = ws.take<double>(KK);
   double* T1 = ws.take<double>(KK);
-  double* T2 = ws.take<double>(KK);
   double* Minv = ws.take<double>(KK);
   if (ws.dry) return TT_OK;
   if (K > 112 || nv < 1) {  // the inverse kernel holds 2 K^2 doubles in shared memory
@@ -1391,24 +1543,21 @@ static tt_status cholqr2_sigma(cudaStream_t s, int nv, int ldv, double* V, int K
     return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
   }
   const size_t chol_smem = sizeof(double) * ((size_t)KK + K);
-  const size_t inv_smem = sizeof(double) * 2 * (size_t)KK;
+  const size_t inv_smem = sizeof(double) * (2 * (size_t)KK + K);
   const size_t rtu_smem = sizeof(double) * ((size_t)KK + (size_t)kRowsTile * K);
   for (const auto& [f, b] : {std::make_pair((const void*)k_chol_upper, chol_smem),
                               std::make_pair((const void*)k_tri_inv, inv_smem),
                               std::make_pair((const void*)k_rows_times_upper, rtu_smem)})
     if (const tt_status a = smem_optin_impl(f, b); a != TT_OK) return a;
-  for (int pass = 0; pass < 2; ++pass) {
-    double* T = pass ? T2 : T1;
-    k_gram_chunks<<<dim3((unsigned)nchunks, (unsigned)((KK + kGramEntries - 1) / kGramEntries)), 256, 0, s>>>(
-        nv, ldv, V, K, part); count_launch();
-    k_gram_sum<<<(KK + 255) / 256, 256, 0, s>>>(nchunks, KK, part, G); count_launch();
-    k_chol_upper<<<1, 256, chol_smem, s>>>(K, G, T); count_launch();
-    // V <- V T^{-1} as a product with the explicit inverse: row-parallel without a dependent chain
-    k_tri_inv<<<1, 128, inv_smem, s>>>(K, T, Minv); count_launch();
-    k_rows_times_upper<<<(nv + kRowsTile - 1) / kRowsTile, 256, rtu_smem, s>>>(nv, ldv, V, K, Minv);
-    count_launch();
-  }
-  k_sig_from_chol<<<(K + 127) / 128, 128, 0, s>>>(K, T1, T2, sig); count_launch();
+  k_gram_chunks<<<dim3((unsigned)nchunks, (unsigned)((KK + kGramEntries - 1) / kGramEntries)), 256, 0, s>>>(
+      nv, ldv, V, K, part); count_launch();
+  k_gram_sum<<<(KK + 255) / 256, 256, 0, s>>>(nchunks, KK, part, G); count_launch();
+  k_chol_upper<<<1, 256, chol_smem, s>>>(K, G, T1); count_launch();
+  // V <- V T^{-1} as a product with the explicit inverse: row-parallel without a dependent chain
+  k_tri_inv<<<1, 128, inv_smem, s>>>(K, T1, Minv); count_launch();
+  k_rows_times_upper<<<(nv + kRowsTile - 1) / kRowsTile, 256, rtu_smem, s>>>(nv, ldv, V, K, Minv);
+  count_launch();
+  k_sig_from_chol<<<(K + 127) / 128, 128, 0, s>>>(K, T1, nullptr, sig); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -1494,7 +1643,7 @@ static tt_status svd_right_pre(cudaStream_t s, int num_sms, const Src& src, long
 // d = 3 small-core sweep.  For each bond a TSQR of the small matrix A and a one-sided Jacobi on
 // R^T give right vectors U (mixed path: FP32 TSQR and one-CTA FP32 Jacobi, U nearly orthogonal;
 // F64: FP64 TSQR and the cooperative FP64 Jacobi).  P = A U in FP64, sorted by column norm;
-// CholeskyQR2 of the leading columns gives FP64 singular values |T_jj| and orthonormal left
+// CholeskyQR of the leading columns gives FP64 singular values |T_jj| and orthonormal left
 // vectors; the energy beyond them comes from the FP64 Jacobi singular values (F64) or from
 // Pythagoras (mixed).
 template <bool F64>
@@ -1522,14 +1671,14 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
                      s>>>(R * n1, n2, n2, P2, sigc2, perm2, P2s, n2, 0); count_launch();
     k_write_sorted<<<(n2 * n2 + 255) / 256, 256, 0, s>>>(n2, n2, n2, U2, sigc2, perm2, V2, n2, 0); count_launch();
   }
-  st = cholqr2_sigma(s, R * n1, n2, P2s, n2, sig2, ws);
+  st = cholqr_sigma(s, R * n1, n2, P2s, n2, sig2, ws);
   if (st != TT_OK) return st;
   if (!ws.dry) {
     k_sort_cols<<<1, 1024, 0, s>>>(n2, n2, n2, sig2, V2, tmp2); count_launch();
     k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
                               j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
     if (n2 <= 32)
-      k_orthonormalise_warp<<<1, 32, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
+      k_orthonormalise_polar<<<1, 128, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     else
       k_orthonormalise<<<1, 1024, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     count_launch();
@@ -1555,7 +1704,7 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
     k_write_sorted<<<(unsigned)(((long)nv * R + 255) / 256 < 1024 ? ((long)nv * R + 255) / 256 : 1024), 256, 0,
                      s>>>(nv, R, R, P1, sigc1, perm1, P1s, R, 0); count_launch();
   }
-  st = cholqr2_sigma(s, nv, R, P1s, Kr, sig1, ws);
+  st = cholqr_sigma(s, nv, R, P1s, Kr, sig1, ws);
   if (st != TT_OK || ws.dry) return st;
   // energy beyond the Kr refined values: from the FP64 Jacobi singular values (FP64 path), or
   // ||A1||_F^2 - sum sigma_j^2 (mixed path; accurate to about sqrt(eps_64) ||A1||)
