@@ -245,63 +245,76 @@ struct LiveWalk {
 
 // FP32 form of the reflector loop on the packed two-lane FMA of sm_100+ (__ffma2_rn: each lane
 // rounds as one fmaf): the column owner's norm, the dot of the reflector with a column and the
-// column update each run BR/2 packed FMAs, and the reflector is read from shared memory in
-// 16-byte vectors.  Same arithmetic as the generic loop below up to the order of the partial sums.
+// column update each run BR/2 packed FMAs in four partial sums, and the reflector is read from
+// shared memory in 16-byte vectors.  The pivot thread's work is the critical path of every
+// reflector step (the other columns wait for it at the barrier), so, as in the FP64 form, it
+// stores the reflector unscaled, u = [alpha - beta; B], and the other columns apply
+// sc = 1/(alpha - beta) (H x = x - tau v (v^T x), v = sc u); its own rows are not cleared (no
+// later step of this block reads them: the pivot column takes no further update).  Same
+// arithmetic as the generic loop below up to the order of the partial sums and the place of sc.
 template <int BR>
 __device__ __forceinline__ void hh_absorb_x2(float* Rs, int ncap, float (&B)[BR], float* vbuf, float* taub,
                                              int& buf, int jbeg, const LivePattern& lp, int r, bool mycol) {
-  static_assert(BR % 4 == 0, "block rows in float4 groups");
+  static_assert(BR % 8 == 0, "block rows in pairs of float4 groups");
   const int c = threadIdx.x;
   LiveWalk walk(lp, jbeg);
   for (int j = jbeg; j < ncap; ++j) {
     if (!walk.next(lp, r)) continue;
     float* vb = vbuf + buf * BR;
     if (c == j) {
-      float2 xp0 = make_float2(0.f, 0.f), xp1 = make_float2(0.f, 0.f);
+      float2 xp0 = make_float2(0.f, 0.f), xp1 = xp0, xp2 = xp0, xp3 = xp0;
 #pragma unroll
-      for (int i = 0; i < BR; i += 4) {
+      for (int i = 0; i < BR; i += 8) {
         xp0 = __ffma2_rn(make_float2(B[i], B[i + 1]), make_float2(B[i], B[i + 1]), xp0);
         xp1 = __ffma2_rn(make_float2(B[i + 2], B[i + 3]), make_float2(B[i + 2], B[i + 3]), xp1);
+        xp2 = __ffma2_rn(make_float2(B[i + 4], B[i + 5]), make_float2(B[i + 4], B[i + 5]), xp2);
+        xp3 = __ffma2_rn(make_float2(B[i + 6], B[i + 7]), make_float2(B[i + 6], B[i + 7]), xp3);
       }
-      const float x2 = (xp0.x + xp0.y) + (xp1.x + xp1.y);
-      float tau = 0.f;
+      const float x2 = ((xp0.x + xp0.y) + (xp1.x + xp1.y)) + ((xp2.x + xp2.y) + (xp3.x + xp3.y));
+      float tau = 0.f, sc = 0.f;
       if (x2 > 0.f) {
+#pragma unroll
+        for (int i = 0; i < BR; i += 4)
+          *reinterpret_cast<float4*>(vb + i) = make_float4(B[i], B[i + 1], B[i + 2], B[i + 3]);
         float* rjj = Rs + tri_off(j, ncap);
         const float alpha = *rjj;
         const float nrm = sqrtf(alpha * alpha + x2);
         const float beta = (alpha >= 0.f) ? -nrm : nrm;
-        const float sc = chain_div<float>(1.f, alpha - beta);
-#pragma unroll
-        for (int i = 0; i < BR; i += 4)
-          *reinterpret_cast<float4*>(vb + i) = make_float4(B[i] * sc, B[i + 1] * sc, B[i + 2] * sc, B[i + 3] * sc);
+        sc = chain_div<float>(1.f, alpha - beta);
         tau = chain_div<float>(beta - alpha, beta);
         *rjj = beta;
-#pragma unroll
-        for (int i = 0; i < BR; ++i) B[i] = 0.f;
       }
       taub[buf] = tau;
+      taub[2 + buf] = sc;
     }
     __syncthreads();
     const float tau = taub[buf];
     if (tau != 0.f && c > j && mycol) {
+      const float sc = taub[2 + buf];
       float* rjc = Rs + tri_off(j, ncap) + (c - j);
       // up to 32 block rows the reflector stays in registers between the dot and the update;
       // wider blocks read it again (their B already fills the register budget)
       constexpr bool kKeep = BR <= 32;
-      float2 w0 = make_float2(*rjc, 0.f), w1 = make_float2(0.f, 0.f);
+      float2 w0 = make_float2(0.f, 0.f), w1 = w0, w2 = w0, w3 = w0;
       float v[kKeep ? BR : 1];
 #pragma unroll
-      for (int i = 0; i < BR; i += 4) {
+      for (int i = 0; i < BR; i += 8) {
         const float4 t = *reinterpret_cast<const float4*>(vb + i);
+        const float4 t2 = *reinterpret_cast<const float4*>(vb + i + 4);
         if constexpr (kKeep) {
           v[i] = t.x; v[i + 1] = t.y; v[i + 2] = t.z; v[i + 3] = t.w;
+          v[i + 4] = t2.x; v[i + 5] = t2.y; v[i + 6] = t2.z; v[i + 7] = t2.w;
         }
         w0 = __ffma2_rn(make_float2(t.x, t.y), make_float2(B[i], B[i + 1]), w0);
         w1 = __ffma2_rn(make_float2(t.z, t.w), make_float2(B[i + 2], B[i + 3]), w1);
+        w2 = __ffma2_rn(make_float2(t2.x, t2.y), make_float2(B[i + 4], B[i + 5]), w2);
+        w3 = __ffma2_rn(make_float2(t2.z, t2.w), make_float2(B[i + 6], B[i + 7]), w3);
       }
-      const float wv = ((w0.x + w0.y) + (w1.x + w1.y)) * tau;
+      const float d = ((w0.x + w0.y) + (w1.x + w1.y)) + ((w2.x + w2.y) + (w3.x + w3.y));
+      const float wv = fmaf(sc, d, *rjc) * tau;
       *rjc -= wv;
-      const float2 nw = make_float2(-wv, -wv);
+      const float ws = wv * sc;
+      const float2 nw = make_float2(-ws, -ws);
 #pragma unroll
       for (int i = 0; i < BR; i += 4) {
         float4 t;
