@@ -423,34 +423,36 @@ __device__ __forceinline__ void hh_absorb(T* Rs, int ncap, T (&B)[BR], T* vbuf, 
 #pragma unroll
       for (int i = 0; i < BR; ++i) xp[i & 3] += B[i] * B[i];
       const T x2 = (xp[0] + xp[1]) + (xp[2] + xp[3]);
-      T tau = T(0);
+      // the reflector goes out unscaled, u = [alpha - beta; B], with sc = 1/(alpha - beta) for
+      // the other columns, and the pivot's rows are not cleared (as in hh_absorb_x2)
+      T tau = T(0), sc = T(0);
       if (x2 > T(0)) {
+#pragma unroll
+        for (int i = 0; i < BR; ++i) vb[i] = B[i];
         T* rjj = Rs + tri_off(j, ncap);
         const T alpha = *rjj;
         const T nrm = sqrt(alpha * alpha + x2);
         const T beta = (alpha >= T(0)) ? -nrm : nrm;
-        const T sc = chain_div<T>(T(1), alpha - beta);
-#pragma unroll
-        for (int i = 0; i < BR; ++i) vb[i] = B[i] * sc;
+        sc = chain_div<T>(T(1), alpha - beta);
         tau = chain_div<T>(beta - alpha, beta);
         *rjj = beta;
-#pragma unroll
-        for (int i = 0; i < BR; ++i) B[i] = T(0);
       }
       taub[buf] = tau;
+      taub[2 + buf] = sc;
     }
     __syncthreads();
     const T tau = taub[buf];
     if (tau != T(0) && c > j && mycol) {
+      const T sc = taub[2 + buf];
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
-      T wp[4] = {*rjc, T(0), T(0), T(0)};
+      T wp[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
       for (int i = 0; i < BR; ++i) wp[i & 3] += vb[i] * B[i];
-      T wv = (wp[0] + wp[1]) + (wp[2] + wp[3]);
-      wv *= tau;
+      const T wv = (*rjc + sc * ((wp[0] + wp[1]) + (wp[2] + wp[3]))) * tau;
       *rjc -= wv;
+      const T ws = wv * sc;
 #pragma unroll
-      for (int i = 0; i < BR; ++i) B[i] -= wv * vb[i];
+      for (int i = 0; i < BR; ++i) B[i] -= ws * vb[i];
     }
     buf ^= 1;
   }

@@ -1677,8 +1677,13 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
     k_sort_cols<<<1, 1024, 0, s>>>(n2, n2, n2, sig2, V2, tmp2); count_launch();
     k_decide<<<1, 32, 0, s>>>(sig2, n2, 1, 3, j.tol, j.rmax, K2, 0, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, n1,
                               j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
-    if (n2 <= 32)
+    // FP64 path: the columns come from the FP64 Jacobi, orthonormal to round-off, and take at most
+    // one polar step; the mixed path's FP32-accurate small columns are only ~1e-2 orthogonal
+    // (the FP32 sweep stops at its round-off floor), so they take Gram-Schmidt directly
+    if (n2 <= 32 && F64)
       k_orthonormalise_polar<<<1, 128, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
+    else if (n2 <= 32)
+      k_orthonormalise_warp<<<1, 32, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     else
       k_orthonormalise<<<1, 1024, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     count_launch();

@@ -202,17 +202,23 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
     return;
   }
   constexpr int RPT = RsGeom<T, BR, QS>::RPT, SS = RsGeom<T, BR, QS>::SS;
-  const int lead = (threadIdx.x & 31) & ~(QS - 1);
   LiveWalk walk(lp, jbeg);
   for (int j = jbeg; j < ncap; ++j) {
     if (!walk.next(lp, r)) continue;
     T* vb = vbuf + buf * (QS * SS);
     if (c == j) {
+      // the reflector goes out unscaled, u = [alpha - beta; B], with sc = 1/(alpha - beta) for
+      // the other columns, and the pivot's rows are not cleared (no later step of this block
+      // reads them): the pivot group's part of the step is the critical path
       const T x2 = group_sum<T, QS>(dot4<T, RPT>(B, B, T(0)), gm);
-      T tau = T(0);
       if (x2 > T(0)) {
-        T sc = T(0);
-        if (q == 0) {
+        T* seg = vb + q * SS;
+#pragma unroll
+        for (int i = 0; i < RPT; i += 4) st4<T>(seg + i, B[i], B[i + 1], B[i + 2], B[i + 3]);
+      }
+      if (q == 0) {
+        T tau = T(0), sc = T(0);
+        if (x2 > T(0)) {
           T* rjj = Rs + tri_off(j, ncap);
           const T alpha = *rjj;
           const T nrm = sqrt(alpha * alpha + x2);
@@ -221,14 +227,9 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
           tau = chain_div<T>(beta - alpha, beta);
           *rjj = beta;
         }
-        sc = __shfl_sync(gm, sc, lead);
-        T* seg = vb + q * SS;
-#pragma unroll
-        for (int i = 0; i < RPT; i += 4) st4<T>(seg + i, B[i] * sc, B[i + 1] * sc, B[i + 2] * sc, B[i + 3] * sc);
-#pragma unroll
-        for (int i = 0; i < RPT; ++i) B[i] = T(0);
+        taub[buf] = tau;
+        taub[2 + buf] = sc;
       }
-      if (q == 0) taub[buf] = tau;
     }
     __syncthreads();
     const T tau = taub[buf];
@@ -238,7 +239,8 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
       T v[RPT];
       const T* seg = vb + q * SS;
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
-      T part = q == 0 ? *rjc : T(0);
+      const T sc = taub[2 + buf];
+      T part = T(0);
       if (meets) {
 #pragma unroll
         for (int i = 0; i < RPT; i += 4) {
@@ -251,14 +253,14 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
         }
         part = dot4<T, RPT>(v, B, part);
       }
-      T wv = group_sum<T, QS>(part, gm);
-      wv *= tau;
+      const T wv = (*rjc + sc * group_sum<T, QS>(part, gm)) * tau;
       if (q == 0) *rjc -= wv;
-      if (meets) axpy_neg<T, RPT>(wv, v, B);
+      if (meets) axpy_neg<T, RPT>(wv * sc, v, B);
     } else if (tau != T(0) && c > j && mycol) {
       const T* seg = vb + q * SS;
       T* rjc = Rs + tri_off(j, ncap) + (c - j);
-      T wp[4] = {q == 0 ? *rjc : T(0), T(0), T(0), T(0)};
+      const T sc = taub[2 + buf];
+      T wp[4] = {T(0), T(0), T(0), T(0)};
       if (meets) {
 #pragma unroll
         for (int i = 0; i < RPT; i += 4) {
@@ -270,18 +272,18 @@ __device__ __forceinline__ void hh_absorb_rs(T* Rs, int ncap, T (&B)[BR / QS], T
           wp[3] += t4[3] * B[i + 3];
         }
       }
-      T wv = group_sum<T, QS>((wp[0] + wp[1]) + (wp[2] + wp[3]), gm);
-      wv *= tau;
+      const T wv = (*rjc + sc * group_sum<T, QS>((wp[0] + wp[1]) + (wp[2] + wp[3]), gm)) * tau;
       if (q == 0) *rjc -= wv;
+      const T ws = wv * sc;
       if (meets) {
 #pragma unroll
         for (int i = 0; i < RPT; i += 4) {
           T t4[4];
           ld4(seg + i, t4);
-          B[i] -= wv * t4[0];
-          B[i + 1] -= wv * t4[1];
-          B[i + 2] -= wv * t4[2];
-          B[i + 3] -= wv * t4[3];
+          B[i] -= ws * t4[0];
+          B[i + 1] -= ws * t4[1];
+          B[i + 2] -= ws * t4[2];
+          B[i + 3] -= ws * t4[3];
         }
       }
     }
