@@ -8,10 +8,11 @@
 // D_L = C - L and D_H = H - C in place, and every value is split into its TF32 part and the FP32
 // remainder (itself rounded to TF32, so that the tensor core's truncation of its operands adds no
 // bias).  The combined weights (formed once per CTA in FP64, as in k_update_blk) are the B operand,
-// split the same way.  One thread issues three MMAs per K step of 8 (lo hi, hi lo, hi hi).  The K
-// steps are spread over several accumulators in tensor memory, a few steps each, because the
-// tensor core's FP32 accumulation is not rounded to nearest: its error grows with the number of
-// MMAs summed into one accumulator.  The four warps read the accumulators back (a row per thread)
+// split the same way.  One thread issues three MMAs per K step of 8 (lo hi, hi lo, hi hi).  The
+// hi hi products are spread over several accumulators in tensor memory, at most two K steps each,
+// and the small products of all steps go to one more (update_tc_acc_plan), because the tensor
+// core's FP32 accumulation is not rounded to nearest: its error, biased toward zero, grows with
+// the MMAs summed into one accumulator.  Four warps read the accumulators back (a row per thread)
 // and add them in FP32, the inflow columns are added per row, and the update epilogue (energy dot,
 // source or final scaling, non-finite check) runs on the tile as for the other update kernels.
 #pragma once
@@ -25,12 +26,27 @@ constexpr int kTcThreads = 512;  // 16 warps: the tile phases are latency-bound 
 
 // Output columns of the tensor-core update: kcap rounded up to a multiple of 16 (the MMA's N).
 __host__ __device__ inline int update_tc_n(int kcap) { return (kcap + 15) & ~15; }
-// K steps (of 8) summed into one accumulator: as few as the 256 tensor-memory columns allow for
-// the ceil(K / 8 / steps) accumulators of N columns each.
-__host__ __device__ inline int update_tc_steps_per_acc(int K, int N) {
+// Accumulators in tensor memory (N FP32 columns each, 512 columns in all): the hi x hi products of
+// the K steps (of 8) go to nhh accumulators of at most `sph` steps each, the two small products
+// of every step (lo x hi, hi x lo, about 2^-11 of the result) to one more.  The tensor core's FP32
+// accumulation rounds toward zero, up to an ulp of the partial sum per MMA, so the bias of an
+// accumulator grows with the MMAs summed into it; keeping the large products few per accumulator
+// and the small ones apart holds that bias to about one ulp of the result (the accumulators are
+// added in FP32 rounded to nearest).
+struct TcAccPlan {
+  int sph, nhh, nacc;
+};
+__host__ __device__ inline TcAccPlan update_tc_acc_plan(int K, int N) {
   const int ksteps = K / 8;
-  const int s = (ksteps * N + 255) / 256;
-  return s < 1 ? 1 : s;
+  int amax = 512 / N;  // N <= 256: at least 2
+  if (amax < 2) amax = 2;
+  const int hmax = amax - 1;
+  TcAccPlan p;
+  p.sph = (ksteps + hmax - 1) / hmax;
+  if (p.sph < 1) p.sph = 1;
+  p.nhh = (ksteps + p.sph - 1) / p.sph;
+  p.nacc = p.nhh + 1;
+  return p;
 }
 
 // Shared memory: A hi and lo [128][K] and B hi and lo [N][K] (FP32, K-major core matrices),
@@ -68,7 +84,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> s
   static_assert(RCAP % 8 == 0, "whole MMA K steps per row block");
   const int nbc = lp.nextra;
   const int N = update_tc_n(kcap), ldo = N + 1;
-  const int spa = update_tc_steps_per_acc(K, N), nacc = (K / 8 + spa - 1) / spa;
+  const TcAccPlan ap = update_tc_acc_plan(K, N);
+  const int sph = ap.sph, nhh = ap.nhh, nacc = ap.nacc;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
   const int rq = r < RCAP ? r : RCAP;  // live columns of each Z block
   float* Ahi = reinterpret_cast<float*>(tcu_smem);
@@ -198,10 +215,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> s
         const uint32_t so = 256u * (uint32_t)s;
         const uint64_t dah = tc::smem_desc(ah + so, lbo, sbo), dal = tc::smem_desc(al + so, lbo, sbo);
         const uint64_t dbh = tc::smem_desc(bh + so, lbo, sbo), dbl = tc::smem_desc(bl + so, lbo, sbo);
-        const uint32_t d = tmem + (uint32_t)((s / spa) * N);  // accumulator of this K step
-        tc::mma_tf32(d, dal, dbh, idesc, (s % spa) ? 1u : 0u);  // small terms first
-        tc::mma_tf32(d, dah, dbl, idesc, 1u);
-        tc::mma_tf32(d, dah, dbh, idesc, 1u);
+        const uint32_t dhh = tmem + (uint32_t)((s / sph) * N);  // this step's hi x hi accumulator
+        const uint32_t dlo = tmem + (uint32_t)(nhh * N);        // the small products of every step
+        tc::mma_tf32(dlo, dal, dbh, idesc, s ? 1u : 0u);
+        tc::mma_tf32(dlo, dah, dbl, idesc, 1u);
+        tc::mma_tf32(dhh, dah, dbh, idesc, (s % sph) ? 1u : 0u);
       }
       tc::mma_commit(&bar);
     }
