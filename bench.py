@@ -38,10 +38,10 @@ MIXED_LEGS = ("mixed", "mixed_3xtf32")
 # (first leaf launch = the transport sum of the first step, at full rank).  Reads scale with the rows
 # and writes (the leaves' R factors) with the leaves.  Valid only while the leaf kernels' source
 # (csrc/bigpass.cuh) is the one captured: its SHA-256 prefix is LEAF_DRAM_SOURCE.
-LEAF_DRAM_SOURCE = "23f5325e1b623755"
-LEAF_DRAM_96 = {("mixed", "column"): (77494016, 28185856, 439),
-                ("mixed", "column_dense"): (77257472, 59731200, 595),
-                ("fp64", "column"): (202129920, 5283072, 303)}
+LEAF_DRAM_SOURCE = "2a260ffa11b3c772"
+LEAF_DRAM_96 = {("mixed", "column"): (76399616, 28006400, 439),
+                ("mixed", "column_dense"): (76594688, 59895296, 595),
+                ("fp64", "column"): (201468672, 4627456, 303)}
 
 
 def leaf_source_sha():
