@@ -16,6 +16,8 @@
 // and add them in FP32, the inflow columns are added per row, and the update epilogue (energy dot,
 // source or final scaling, non-finite check) runs on the tile as for the other update kernels.
 #pragma once
+#include <type_traits>
+
 #include "tc.cuh"
 #include "update_blk.cuh"
 
@@ -50,12 +52,12 @@ __host__ __device__ inline TcAccPlan update_tc_acc_plan(int K, int N) {
 }
 
 // Shared memory: A hi and lo [128][K] and B hi and lo [N][K] (FP32, K-major core matrices),
-// inflow weights [nbc][N], row scalars [3][128] (FP64), vJ [N], row flags [128].  The output tile
+// inflow weights [nbc][N], row scalars [3][128] (FP64), vJ [N], row flags [2][128].  The output tile
 // [128][N + 1] reuses A lo once the MMAs of a tile are done, the energy partials reuse A hi.
 __host__ __device__ inline size_t update_tc_smem_bytes(int K, int N, int nbc) {
   size_t b = sizeof(float) * (2 * (size_t)kTcRows * K + 2 * (size_t)N * K + (size_t)nbc * N);
   b = (b + 7) & ~(size_t)7;
-  return b + sizeof(double) * 3 * kTcRows + sizeof(float) * (size_t)N + sizeof(unsigned) * kTcRows;
+  return b + sizeof(double) * 3 * kTcRows + sizeof(float) * (size_t)N + sizeof(unsigned) * 2 * kTcRows;
 }
 
 // Row flags of k_update_blk (neighbour bits 2a and 2a + 1, the group in bits 8 and up) in 32-bit
@@ -97,7 +99,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> s
   off = (off + 7) & ~(size_t)7;
   double* rowv = reinterpret_cast<double*>(tcu_smem + off);  // [3][128]
   float* vJs = reinterpret_cast<float*>(rowv + 3 * kTcRows);  // [N]
-  unsigned* fl = reinterpret_cast<unsigned*>(vJs + N);        // [128]
+  unsigned* fl = reinterpret_cast<unsigned*>(vJs + N);        // [2][128]
   float* Os = Alo;                                            // [128][N + 1] after a tile's MMAs
   double* red = reinterpret_cast<double*>(Ahi);               // energy partials after the last tile
   __shared__ uint64_t bar;
@@ -151,15 +153,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> s
   uint32_t phase = 0;
   bool ok = true;
   double e0t = 0.0, e1t = 0.0;
-  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long row0 = tile * kTcRows;
-    __syncthreads();  // the previous tile's epilogue is done with the output tile and row scalars
-    if (tid < kTcRows) fl[tid] = (row0 + tid < nrows) ? tc_row_flags(src, (unsigned)(row0 + tid)) : 0u;
-    __syncthreads();
-    // every granule of the tile's row blocks in flight at once, into the A layout; rows outside
-    // the core and neighbours the row does not have are zero-filled.  Eight consecutive threads
-    // take one granule of eight consecutive rows (one 128-byte core matrix: no bank conflict), a
-    // warp four granules of them (whole 32-byte sectors of every row it reads)
+  // row flags of a tile into f (threads < 128)
+  auto flags_of = [&](long row0, unsigned* f) {
+    if (tid < kTcRows) f[tid] = (row0 + tid < nrows) ? tc_row_flags(src, (unsigned)(row0 + tid)) : 0u;
+  };
+  // every granule of a tile's row blocks in flight at once, into the A layout; rows outside the
+  // core and neighbours the row does not have are zero-filled.  Eight consecutive threads take
+  // one granule of eight consecutive rows (one 128-byte core matrix: no bank conflict), a warp
+  // four granules of them (whole 32-byte sectors of every row it reads)
+  auto stage = [&](long row0, const unsigned* f) {
     constexpr int per_block = kTcRows * GPR;
 #pragma unroll 4
     for (int i = tid; i < NB * per_block; i += kTcThreads) {
@@ -170,15 +172,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> s
       if (b > 0) {
         const int ax = (b - 1) >> 1;
         const bool upper = ((b - 1) & 1) != 0;
-        okr = okr && ((fl[m] >> (2 * ax + (upper ? 1 : 0))) & 1u);
+        okr = okr && ((f[m] >> (2 * ax + (upper ? 1 : 0))) & 1u);
         k += upper ? src.stride[ax] : -src.stride[ax];
       }
       float* dst = Ahi + (tc::kmajor_off(m, b * RCAP + 4 * g, K) >> 2);
       const float* from = okr ? src.Z + k * RCAP + (size_t)4 * g : src.Z;
       cp_async16(dst, from, okr ? 16 : 0);
     }
-    cp_async_wait_all();
+    // the source step's per-row coefficients of the tile into L2 ahead of its epilogue
+    if constexpr (std::is_same<Epi, EpiSource<float>>::value) {
+      const long last = (row0 + kTcRows < nrows ? row0 + kTcRows : nrows) - 1;
+      if (tid < 24) {
+        const double* arr = tid < 8 ? epi.acoef : tid < 16 ? epi.scoef : epi.eps;
+        const long k = row0 + (long)(tid & 7) * 16;
+        if (k <= last) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(arr + k));
+      }
+    }
+  };
+  // Tile pipeline: a tile's rows are staged as soon as the previous tile's MMAs have read the A
+  // buffer, so the copies overlap that tile's read-back and epilogue; row flags alternate
+  // between two buffers (the read-back of one tile and the staging of the next use both).
+  int fb = 0;
+  if ((long)blockIdx.x < ntiles) {
+    flags_of((long)blockIdx.x * kTcRows, fl);
     __syncthreads();
+    stage((long)blockIdx.x * kTcRows, fl);
+  }
+  for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long row0 = tile * kTcRows;
+    const unsigned* flc = fl + fb * kTcRows;
+    cp_async_wait_all();
+    __syncthreads();  // the tile's rows are in place, and the previous epilogue is done with A lo
     // neighbours to differences with the centre rows (L -> C - L, H -> H - C), then every value
     // to its TF32 part (A hi) and rounded remainder (A lo); a thread takes 4 consecutive K values
     // of a row (16-byte vectors; a warp's 32 rows fall on distinct banks)
@@ -227,12 +251,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> s
     if (!ok) break;
     phase ^= 1u;
     tc::fence_after_sync();
+    // A hi is free: the next tile's rows can land during this tile's read-back and epilogue
+    const long next = tile + gridDim.x;
+    if (next < ntiles) {
+      unsigned* fln = fl + (fb ^ 1) * kTcRows;
+      flags_of(next * kTcRows, fln);
+      __syncthreads();
+      stage(next * kTcRows, fln);
+    }
     // accumulator rows (warps 0-3), summed over the accumulators (FP32 adds rounded to nearest: a
     // few ulp over the handful of partial sums), plus the inflow columns, to the output tile (A lo
     // is free now)
     if (warp < 4) {
       const int m = 32 * warp + lane;
-      const unsigned f = fl[m];
+      const unsigned f = flc[m];
       for (int c0 = 0; c0 < N; c0 += 32) {
         float acc[32];
 #pragma unroll
@@ -263,6 +295,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_update_tc(SrcStencil<float> s
     tc::fence_before_sync();
     __syncthreads();
     update_epilogue<float, kTcRows>(epi, Os, ldo, kcap, vJs, vJ != nullptr, rowv, row0, nrows, e0t, e1t);
+    fb ^= 1;
   }
   if (!ok) {
     // the MMAs of the tile may still be running: wait for them again (bounded) before the
