@@ -90,7 +90,7 @@ def parse():
                          "256-problem batch stepped as one CUDA graph (a separate measurement)")
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--batch-scale", type=int, default=1)
-    ap.add_argument("--streams", type=int, default=16)
+    ap.add_argument("--streams", type=int, default=128)
     ap.add_argument("--start", default="planck", choices=["planck", "graded"],
                     help="initial state: I0 = epsilon(T) (rank 1), or the seeded graded state of rank r_max "
                          "(workloads.graded_state; every pass at full width from the first step, e.g. to profile)")
@@ -704,7 +704,8 @@ def run_batched(args):
     plans = [tt.Plan(ctx, wl) for wl in wls]
     rows = sum(w.nrow for w in wls)
     unknowns = sum(w.nrow * w.ntheta * w.nphi for w in wls)
-    precs = ["fp64", "mixed"] if args.precision == "both" else [args.precision]
+    # "all" (the default of the single-problem line) runs the three precision levels here too
+    precs = ["fp64", "mixed", "mixed_3xtf32"] if args.precision == "all" else [args.precision]
     out = {"metric": "batched TT transport steps/s", "unit": "batch steps/s", "n_gpus": 1,
            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
            "config": {"workload": f"batch of {len(wls)} independent 2-D problems", "seed": 3,

@@ -348,7 +348,7 @@ tt_status tt_internal_ranks(tt_context *ctx, const tt_plan *plan, const tt_tenso
  * tolerance tol[i] and rank cap rmax[i], all at precision prec.  Each problem runs exactly the
  * launch sequence of tt_step on its own device control block and workspace region (sized once
  * here by dry runs and allocated as one buffer); problems are spread over nstreams streams
- * (<= 0: 16), largest first onto the least-loaded stream, so that the latency-bound small-core
+ * (<= 0: 128), largest first onto the least-loaded stream, so that the latency-bound small-core
  * phases of different problems overlap.  The cooperative Jacobi of the FP64 path runs as a
  * single CTA per problem inside a batch (concurrent problems never wait on one another).
  * Same argument checks as tt_step (TT_ERR_ARG, TT_ERR_SHAPE, TT_ERR_CAPACITY). */

@@ -29,7 +29,13 @@ constexpr double kPi = 3.14159265358979323846;
 template <typename TA, typename TB>
 __global__ void k_small_gemm(int M, int N, int K, const TA* __restrict__ A, long sa0, long sa1,
                              const TB* __restrict__ B, long sb0, long sb1, double* __restrict__ C, long ldc,
-                             const int* __restrict__ nlive, const double* __restrict__ inv_colscale) {
+                             const int* __restrict__ nlive, const double* __restrict__ inv_colscale,
+                             const TA* __restrict__ A2, double* __restrict__ C2) {
+  // a second product with the same B, shape and strides (A2 B into C2) in the CTAs of z = 1
+  if (blockIdx.z == 1) {
+    A = A2;
+    C = C2;
+  }
   __shared__ double As[16][17];
   __shared__ double Bs[16][17];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -452,12 +458,11 @@ __global__ void k_gram_sum(int nchunks, int KK, const double* __restrict__ part,
 }
 
 // Upper Cholesky factor T (K x K, row-major, zero below the diagonal) of the symmetric G.
-__global__ void __launch_bounds__(256) k_chol_upper(int K, const double* __restrict__ G, double* __restrict__ T) {
-  extern __shared__ double chs[];
-  double* A = chs;         // [K][K] working copy (upper triangle used)
-  double* d0 = chs + K * K;  // original diagonal
-  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) A[idx] = G[idx];
-  for (int j = threadIdx.x; j < K; j += blockDim.x) d0[j] = G[(size_t)j * K + j];
+// Upper Cholesky factor of the K x K Gram matrix in A (shared memory, overwritten: T in the upper
+// triangle, zero rows at dead pivots), d0 (shared, K) its original diagonal.  A pivot at the
+// round-off level of its own diagonal is dead: its row of T is zero.  Block-wide.
+__device__ void chol_upper_smem(int K, double* A, double* d0) {
+  for (int j = threadIdx.x; j < K; j += blockDim.x) d0[j] = A[(size_t)j * K + j];
   __syncthreads();
   const double thr = 64.0 * K * 2.220446049250313e-16;
   for (int j = 0; j < K; ++j) {
@@ -475,6 +480,15 @@ __global__ void __launch_bounds__(256) k_chol_upper(int K, const double* __restr
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(256) k_chol_upper(int K, const double* __restrict__ G, double* __restrict__ T) {
+  extern __shared__ double chs[];
+  double* A = chs;           // [K][K] working copy (upper triangle used)
+  double* d0 = chs + K * K;  // original diagonal
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) A[idx] = G[idx];
+  __syncthreads();
+  chol_upper_smem(K, A, d0);
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
     const int i = idx / K, c = idx - (idx / K) * K;
     T[idx] = (c >= i) ? A[idx] : 0.0;
@@ -487,16 +501,10 @@ __global__ void __launch_bounds__(256) k_chol_upper(int K, const double* __restr
 // The reciprocals of the pivots are formed once, in parallel, and each step's dot product runs in
 // four partial sums: on this part an FP64 division or a long dependent FP64 chain inside the
 // sequential substitution costs hundreds of cycles per step.
-__global__ void __launch_bounds__(128) k_tri_inv(int K, const double* __restrict__ T, double* __restrict__ M) {
-  extern __shared__ double tis[];
-  double* Ts = tis;              // [K][K]
-  double* Ms = tis + K * K;      // [K][K]
-  double* rinv = tis + 2 * K * K;  // [K] 1 / T_ii at live pivots, else 0
-  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) {
-    Ts[idx] = T[idx];
-    Ms[idx] = 0.0;
-  }
-  __syncthreads();
+// Ms <- T^{-1} over the live pivots of the upper-triangular Ts (both K x K in shared memory,
+// rinv: K doubles of shared scratch), one thread per column.  Block-wide.
+__device__ void tri_inv_smem(int K, const double* Ts, double* Ms, double* rinv) {
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Ms[idx] = 0.0;
   for (int i = threadIdx.x; i < K; i += blockDim.x) {
     const double tii = Ts[i * K + i];
     rinv[i] = (tii > 0.0) ? 1.0 / tii : 0.0;
@@ -521,7 +529,42 @@ __global__ void __launch_bounds__(128) k_tri_inv(int K, const double* __restrict
     }
   }
   __syncthreads();
+}
+
+__global__ void __launch_bounds__(128) k_tri_inv(int K, const double* __restrict__ T, double* __restrict__ M) {
+  extern __shared__ double tis[];
+  double* Ts = tis;                // [K][K]
+  double* Ms = tis + K * K;        // [K][K]
+  double* rinv = tis + 2 * K * K;  // [K] 1 / T_ii at live pivots, else 0
+  for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) Ts[idx] = T[idx];
+  __syncthreads();
+  tri_inv_smem(K, Ts, Ms, rinv);
   for (int idx = threadIdx.x; idx < K * K; idx += blockDim.x) M[idx] = Ms[idx];
+}
+
+// The one-CTA part of a CholeskyQR pass in one launch, for K <= 64: the Gram partials summed
+// (fixed order), the upper Cholesky factor T, its inverse over the live pivots into M, and
+// sig[j] = T_jj.  Shared memory: 2 K^2 + 2 K doubles.
+constexpr int kCholFusedMaxK = 64;
+__global__ void __launch_bounds__(256) k_chol_inv_sig(int K, int nchunks, const double* __restrict__ part,
+                                                      double* __restrict__ M, double* __restrict__ sig) {
+  extern __shared__ double cis[];
+  const int KK = K * K;
+  double* A = cis;         // [K][K]: G, then T in the upper triangle
+  double* Ms = A + KK;     // [K][K]
+  double* d0 = Ms + KK;    // [K]
+  double* rinv = d0 + K;   // [K]
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
+    double t = 0.0;
+    for (int c = 0; c < nchunks; ++c) t += part[(size_t)c * KK + e];
+    A[e] = t;
+  }
+  __syncthreads();
+  chol_upper_smem(K, A, d0);
+  // below the diagonal A still holds Gram entries; the inverse reads the upper triangle only
+  tri_inv_smem(K, A, Ms, rinv);
+  for (int idx = threadIdx.x; idx < KK; idx += blockDim.x) M[idx] = Ms[idx];
+  for (int j = threadIdx.x; j < K; j += blockDim.x) sig[j] = A[(size_t)j * K + j];
 }
 
 // V[row][:K] <- V[row][:K] M for upper-triangular M (K x K): rows staged kRowsTile per CTA in
@@ -584,30 +627,30 @@ __global__ void __launch_bounds__(1024) k_sort_cols(int nv, int ldv, int K, doub
 }
 
 // tail = max(0, fro2 - sum_{j<K} sig_j^2): the energy of A outside its K leading singular pairs
-__global__ void k_tail_from_fro(int K, const double* __restrict__ sig, const double* __restrict__ fro2,
-                                double* __restrict__ tail) {
-  if (threadIdx.x || blockIdx.x) return;
-  double s2 = 0.0;
-  for (int j = K - 1; j >= 0; --j) s2 += sig[j] * sig[j];
-  const double t = *fro2 - s2;
-  *tail = t > 0.0 ? t : 0.0;
+// *tail = max(0, ||A||_F^2 - sum_j sig_j^2) with ||A||_F^2 over `count` entries of A: the energy
+// beyond the K refined singular values (one CTA).
+__global__ void k_tail_from_frob(long count, const double* __restrict__ A, int K, const double* __restrict__ sig,
+                                 double* __restrict__ fro2, double* __restrict__ tail) {
+  __shared__ double red[33];
+  double s = 0.0;
+  for (long i = threadIdx.x; i < count; i += blockDim.x) s += A[i] * A[i];
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) {
+    *fro2 = s;
+    double s2 = 0.0;
+    for (int j = K - 1; j >= 0; --j) s2 += sig[j] * sig[j];
+    const double t = s - s2;
+    *tail = t > 0.0 ? t : 0.0;
+  }
 }
 
 // Energy beyond the first K of n sorted singular values that are accurate to FP64 (the squared
-// tail, like k_tail_from_fro, but without the cancellation of ||A||^2 - sum sigma^2).
+// tail, like k_tail_from_frob, but without the cancellation of ||A||^2 - sum sigma^2).
 __global__ void k_tail_from_sigma(int n, int K, const double* __restrict__ sig, double* __restrict__ tail) {
   if (threadIdx.x || blockIdx.x) return;
   double s2 = 0.0;
   for (int j = n - 1; j >= K; --j) s2 += sig[j] * sig[j];
   *tail = s2;
-}
-
-__global__ void k_copy_cols(int nv, int ncols, const double* __restrict__ A, int lda, double* __restrict__ B, int ldb) {
-  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)nv * ncols;
-       idx += (long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / ncols), j = (int)(idx - (long)i * ncols);
-    B[(size_t)i * ldb + j] = A[(size_t)i * lda + j];
-  }
 }
 
 // Columns j < k of V (nv x ldv, row-major) whose singular value is exactly zero carry no
@@ -617,9 +660,18 @@ __global__ void k_copy_cols(int nv, int ncols, const double* __restrict__ A, int
 // out of the converged Jacobi sweep orthonormal and are left as they are.
 __global__ void __launch_bounds__(1024) k_fix_zero_columns(int nv, int ldv, double* __restrict__ V,
                                                            const double* __restrict__ sigma, const int* kptr,
-                                                           int rowmod, const int* rowlive_ptr) {
+                                                           int rowmod, const int* rowlive_ptr,
+                                                           const double* __restrict__ from, int ldfrom) {
   __shared__ double red[33];
   __shared__ double h[1024];
+  // V[:, :ldv] <- from[:, :ldv] first (the leading columns of a wider matrix), when given
+  if (from) {
+    for (long idx = threadIdx.x; idx < (long)nv * ldv; idx += blockDim.x) {
+      const int i = (int)(idx / ldv), j = (int)(idx - (long)i * ldv);
+      V[(size_t)i * ldv + j] = from[(size_t)i * ldfrom + j];
+    }
+    __syncthreads();
+  }
   const int k = *kptr;
   const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -1128,7 +1180,7 @@ __device__ __forceinline__ bool jrt_rotation_scaled(float a, float b, float g, f
 
 __global__ void __launch_bounds__(kJrtThreadsReg) k_jacobi_rt_reg(int n, const double* __restrict__ R,
                                                                   double* __restrict__ U, double* __restrict__ raw,
-                                                                  int maxsweep, DevCtrl* ctrl) {
+                                                                  int maxsweep, DevCtrl* ctrl, int* __restrict__ perm) {
   extern __shared__ __align__(16) unsigned char jrr_smem[];
   const JrtRegGeom geo = jrt_reg_geom(n);
   const int ts = geo.ts, vv = geo.vv, ld = geo.ld;
@@ -1137,6 +1189,7 @@ __global__ void __launch_bounds__(kJrtThreadsReg) k_jacobi_rt_reg(int n, const d
   __shared__ int rot_flag, nk_s;
   __shared__ double red[33];
   __shared__ float rnorm[kJrtThreadsReg / 8 * 2];  // row norms^2 (n <= 160), FP32
+  __shared__ double rawk[kJrtThreadsReg / 4];      // rank keys of the raw values (n <= 160)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   // FP64 Frobenius norm and FP32 row norms of R
   double fl = 0.0;
@@ -1264,7 +1317,10 @@ __global__ void __launch_bounds__(kJrtThreadsReg) k_jacobi_rt_reg(int n, const d
   for (int c = warp; c < n; c += nwarps) {
     if (c >= nk) {
       for (int i = lane; i < n; i += 32) U[(size_t)i * n + c] = 0.0;
-      if (lane == 0) raw[c] = 0.0;
+      if (lane == 0) {
+        raw[c] = 0.0;
+        rawk[c] = 0.0;
+      }
       continue;
     }
     const float* ac = At + (size_t)c * ld;
@@ -1273,7 +1329,24 @@ __global__ void __launch_bounds__(kJrtThreadsReg) k_jacobi_rt_reg(int n, const d
     s2 = warp_sum(s2);
     const double inv = (s2 > 0.0) ? 1.0 / sqrt(s2) : 0.0;
     for (int i = lane; i < n; i += 32) U[(size_t)i * n + c] = (double)ac[i] * inv;
-    if (lane == 0) raw[c] = sqrt(s2) * fro;
+    if (lane == 0) {
+      const double rv = sqrt(s2) * fro;
+      raw[c] = rv;
+      rawk[c] = rank_key(rv);
+    }
+  }
+  // perm[r] = the column of rank r by decreasing raw value (ties by index), as k_rank_perm
+  if (perm) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const double v = rawk[c];
+      int rk = 0;
+      for (int q = 0; q < n; ++q) {
+        const double w = rawk[q];
+        rk += (w > v) || (w == v && q < c);
+      }
+      perm[rk] = c;
+    }
   }
 }
 
@@ -1285,7 +1358,8 @@ __global__ void __launch_bounds__(kJrtThreadsReg) k_jacobi_rt_reg(int n, const d
 // and reciprocal square root, and the dot products run in four partial sums (the round is one
 // dependent chain).  Same outputs as k_jacobi_rt.
 __global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restrict__ R, double* __restrict__ U,
-                                                    double* __restrict__ raw, int maxsweep, DevCtrl* ctrl) {
+                                                    double* __restrict__ raw, int maxsweep, DevCtrl* ctrl,
+                                                    int* __restrict__ perm) {
   const int lane = threadIdx.x;
   double f = 0.0;
   if (lane < n)
@@ -1348,6 +1422,7 @@ __global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restr
     atomicAdd(&ctrl->jac_calls, 1);
     atomicAdd(&ctrl->jac_sweeps_sum, sweeps);
   }
+  double rawv = 0.0;
   if (lane < n) {
     double s2 = 0.0;
 #pragma unroll
@@ -1356,7 +1431,18 @@ __global__ void __launch_bounds__(32) k_jacobi_warp(int n, const double* __restr
 #pragma unroll
     for (int i = 0; i < 32; ++i)
       if (i < n) U[(size_t)i * n + lane] = (double)col[i] * inv;
-    raw[lane] = sqrt(s2) * fro;
+    rawv = sqrt(s2) * fro;
+    raw[lane] = rawv;
+  }
+  // perm[r] = the column of rank r by decreasing raw value (ties by index), as k_rank_perm
+  if (perm) {
+    const double v = rank_key(rawv);
+    int rk = 0;
+    for (int q = 0; q < n; ++q) {
+      const double w = __shfl_sync(0xffffffffu, v, q);
+      rk += (w > v) || (w == v && q < lane);
+    }
+    if (lane < n) perm[rk] = lane;
   }
 }
 
@@ -1425,7 +1511,17 @@ template <typename TA, typename TB>
 void small_gemm(cudaStream_t s, int M, int N, int K, const TA* A, long sa0, long sa1, const TB* B, long sb0,
                 long sb1, double* C, long ldc, const int* nlive, const double* inv_colscale) {
   dim3 grid((N + 15) / 16, (M + 15) / 16);
-  k_small_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sa0, sa1, B, sb0, sb1, C, ldc, nlive, inv_colscale); count_launch();
+  k_small_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sa0, sa1, B, sb0, sb1, C, ldc, nlive, inv_colscale,
+                                            nullptr, nullptr); count_launch();
+}
+
+// A B -> C and A2 B -> C2 in one launch (same shape, strides and B).
+template <typename TA, typename TB>
+void small_gemm_pair(cudaStream_t s, int M, int N, int K, const TA* A, const TA* A2, long sa0, long sa1, const TB* B,
+                     long sb0, long sb1, double* C, double* C2, long ldc, const int* nlive) {
+  dim3 grid((N + 15) / 16, (M + 15) / 16, 2);
+  k_small_gemm<TA, TB><<<grid, 256, 0, s>>>(M, N, K, A, sa0, sa1, B, sb0, sb1, C, ldc, nlive, nullptr, A2, C2);
+  count_launch();
 }
 
 template void small_gemm<double, double>(cudaStream_t, int, int, int, const double*, long, long, const double*,
@@ -1544,20 +1640,28 @@ static tt_status cholqr_sigma(cudaStream_t s, int nv, int ldv, double* V, int K,
   }
   const size_t chol_smem = sizeof(double) * ((size_t)KK + K);
   const size_t inv_smem = sizeof(double) * (2 * (size_t)KK + K);
+  const size_t fused_smem = sizeof(double) * (2 * (size_t)KK + 2 * K);
   const size_t rtu_smem = sizeof(double) * ((size_t)KK + (size_t)kRowsTile * K);
+  const bool fused = K <= kCholFusedMaxK;
   for (const auto& [f, b] : {std::make_pair((const void*)k_chol_upper, chol_smem),
                               std::make_pair((const void*)k_tri_inv, inv_smem),
+                              std::make_pair((const void*)k_chol_inv_sig, fused ? fused_smem : (size_t)0),
                               std::make_pair((const void*)k_rows_times_upper, rtu_smem)})
     if (const tt_status a = smem_optin_impl(f, b); a != TT_OK) return a;
   k_gram_chunks<<<dim3((unsigned)nchunks, (unsigned)((KK + kGramEntries - 1) / kGramEntries)), 256, 0, s>>>(
       nv, ldv, V, K, part); count_launch();
-  k_gram_sum<<<(KK + 255) / 256, 256, 0, s>>>(nchunks, KK, part, G); count_launch();
-  k_chol_upper<<<1, 256, chol_smem, s>>>(K, G, T1); count_launch();
-  // V <- V T^{-1} as a product with the explicit inverse: row-parallel without a dependent chain
-  k_tri_inv<<<1, 128, inv_smem, s>>>(K, T1, Minv); count_launch();
+  if (fused) {
+    // partial sums, Cholesky, inverse and |T_jj| in one CTA
+    k_chol_inv_sig<<<1, 256, fused_smem, s>>>(K, nchunks, part, Minv, sig); count_launch();
+  } else {
+    k_gram_sum<<<(KK + 255) / 256, 256, 0, s>>>(nchunks, KK, part, G); count_launch();
+    k_chol_upper<<<1, 256, chol_smem, s>>>(K, G, T1); count_launch();
+    // V <- V T^{-1} as a product with the explicit inverse: row-parallel without a dependent chain
+    k_tri_inv<<<1, 128, inv_smem, s>>>(K, T1, Minv); count_launch();
+    k_sig_from_chol<<<(K + 127) / 128, 128, 0, s>>>(K, T1, nullptr, sig); count_launch();
+  }
   k_rows_times_upper<<<(nv + kRowsTile - 1) / kRowsTile, 256, rtu_smem, s>>>(nv, ldv, V, K, Minv);
   count_launch();
-  k_sig_from_chol<<<(K + 127) / 128, 128, 0, s>>>(K, T1, nullptr, sig); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -1585,18 +1689,19 @@ static tt_status svd_right_mixed(cudaStream_t s, int num_sms, const Src& src, lo
   tt_status st = run_tsqr<float, 64>(s, num_sms, src, lp, rows, 8, a, b, &R);
   if (st != TT_OK) return st;
   if (cols <= 32) {
-    k_jacobi_warp<<<1, 32, 0, s>>>(cols, R, U, raw, 40, ctrl); count_launch();
+    k_jacobi_warp<<<1, 32, 0, s>>>(cols, R, U, raw, 40, ctrl, perm); count_launch();
   } else if (reg) {
     const size_t smem = jrt_reg_smem_bytes(cols);
     if (const tt_status a = smem_optin(k_jacobi_rt_reg, smem); a != TT_OK) return a;
-    k_jacobi_rt_reg<<<1, kJrtThreadsReg, smem, s>>>(cols, R, U, raw, 40, ctrl); count_launch();
+    k_jacobi_rt_reg<<<1, kJrtThreadsReg, smem, s>>>(cols, R, U, raw, 40, ctrl, perm); count_launch();
   } else if (in_smem) {
     if (const tt_status a = smem_optin(k_jacobi_rt<float, true>, at_bytes); a != TT_OK) return a;
     k_jacobi_rt<float, true><<<1, 1024, at_bytes, s>>>(cols, R, U, raw, 40, nullptr, ctrl); count_launch();
+    k_rank_perm<<<1, 1024, 0, s>>>(cols, raw, perm); count_launch();
   } else {
     k_jacobi_rt<float, false><<<1, 1024, 0, s>>>(cols, R, U, raw, 40, gwork, ctrl); count_launch();
+    k_rank_perm<<<1, 1024, 0, s>>>(cols, raw, perm); count_launch();
   }
-  k_rank_perm<<<1, 1024, 0, s>>>(cols, raw, perm); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
 }
 
@@ -1687,8 +1792,7 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
     else
       k_orthonormalise<<<1, 1024, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     count_launch();
-    small_gemm<double, double>(s, R * n1, K2, n2, Y, n2, 1, V2, n2, 1, Y2, K2, &j.ctrl->k[1], nullptr);
-    small_gemm<double, double>(s, R * n1, K2, n2, j.B0, n2, 1, V2, n2, 1, B0p, K2, &j.ctrl->k[1], nullptr);
+    small_gemm_pair<double, double>(s, R * n1, K2, n2, Y, j.B0, n2, 1, V2, n2, 1, Y2, B0p, K2, &j.ctrl->k[1]);
   }
   // ---- bond 1: A1 = Y2^T (nv x R); its left vectors are V1
   double* sigc1 = ws.take<double>(R);
@@ -1716,15 +1820,13 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   if (F64) {  // the FP64 Jacobi singular values resolve the whole tail
     k_tail_from_sigma<<<1, 32, 0, s>>>(R, Kr, sigc1, tailK); count_launch();
   } else {
-    k_fro2<<<1, 1024, 0, s>>>((long)R * nv, Y2, fro1); count_launch();
-    k_tail_from_fro<<<1, 32, 0, s>>>(Kr, sig1, fro1, tailK); count_launch();
+    k_tail_from_frob<<<1, 1024, 0, s>>>((long)R * nv, Y2, Kr, sig1, fro1, tailK); count_launch();
   }
   k_sort_cols<<<1, 1024, 0, s>>>(nv, R, Kr, sig1, P1s, tmpK); count_launch();
   k_decide<<<1, 32, 0, s>>>(sig1, Kr, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
                             nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, tailK); count_launch();
-  k_copy_cols<<<(unsigned)(((long)nv * K1 + 255) / 256 < 1024 ? ((long)nv * K1 + 255) / 256 : 1024), 256, 0, s>>>(
-      nv, K1, P1s, R, V1, K1); count_launch();
-  k_fix_zero_columns<<<1, 1024, 0, s>>>(nv, K1, V1, sig1, &j.ctrl->k[0], K2, &j.ctrl->k[1]); count_launch();
+  // V1 <- the leading K1 columns of P1s, with the zero ones replaced by independent unit vectors
+  k_fix_zero_columns<<<1, 1024, 0, s>>>(nv, K1, V1, sig1, &j.ctrl->k[0], K2, &j.ctrl->k[1], P1s, R); count_launch();
   k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2); count_launch();
   small_gemm<double, double>(s, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], nullptr);
   small_gemm<double, double>(s, K1 * n1, n2, K2, j.core1, K2, 1, j.core2, n2, 1, j.Bnew, n2, nullptr, nullptr);
