@@ -80,6 +80,15 @@ typedef enum { TT_QUAD_GAUSS_LEGENDRE_MU = 0, TT_QUAD_LATLONG_MIDPOINT = 1 } tt_
  * TT_ERR_UNSUPPORTED. */
 typedef enum { TT_FLUX_UPWIND = 0, TT_FLUX_RUSANOV = 1, TT_FLUX_CENTRAL = 2 } tt_flux;
 
+/* Tensor-train layout of the state (Sec. 3.1 and the split topologies of Sec. 5).
+ * MERGED: the first core merges all spatial axes with the frequency groups, Z(x nu) (row
+ *   k = g + G (ix + Nx (iy + Ny iz))), followed by the angular cores (Theta, Phi; mu for the slab).
+ *   The only layout built.
+ * MERGED_NUX_Y: [Z(nu x)][y][theta][phi], the y axis in a core of its own (d = 4).
+ * SPLIT_X: [X][nu][theta][phi], the spatial core apart from the groups (d = 4).
+ * tt_plan_create refuses the two d = 4 layouts with TT_ERR_UNSUPPORTED. */
+typedef enum { TT_TOPO_MERGED = 0, TT_TOPO_MERGED_NUX_Y = 1, TT_TOPO_SPLIT_X = 2 } tt_topology;
+
 typedef struct {
   int32_t d;                       /* number of cores, 2 or 3                               */
   int32_t n[TT_MAX_CORES];         /* mode sizes n_0..n_{d-1}                               */
@@ -112,6 +121,7 @@ typedef struct {
                                       the source update and advances T by total energy
                                       conservation with the rounded state's J^{m+1}.  The plan
                                       then carries the material state of ONE problem.      */
+  int32_t topology;                /* tt_topology (TT_TOPO_MERGED)                          */
 } tt_problem;
 
 typedef struct tt_context tt_context;

@@ -63,7 +63,10 @@ class _Problem(ctypes.Structure):
                 ("group_edges", ctypes.c_void_p), ("temperature", ctypes.c_void_p),
                 ("rho_kappa_a", ctypes.c_void_p), ("rho_kappa_s", ctypes.c_void_p),
                 ("inflow_temperature", ctypes.c_double * 6), ("flux", ctypes.c_int32),
-                ("rho_cv", ctypes.c_void_p)]
+                ("rho_cv", ctypes.c_void_p), ("topology", ctypes.c_int32)]
+
+
+TOPOLOGIES = {"merged": 0, "merged_nux_y": 1, "split_x": 2}
 
 
 _lib = None
@@ -376,6 +379,7 @@ class Plan:
             t = wl.inflow_temperature[f] if f < len(wl.inflow_temperature) else None
             p.inflow_temperature[f] = -1.0 if t is None else float(t)
         p.flux = {"upwind": 0, "rusanov": 1, "central": 2}[getattr(wl, "flux", "upwind")]
+        p.topology = TOPOLOGIES[getattr(wl, "topology", "merged")]
         rcv = getattr(wl, "rho_cv", None)
         if rcv is not None:
             self._arrays.append(torch.as_tensor(np.asarray(rcv, dtype=np.float64), device=dev).contiguous())

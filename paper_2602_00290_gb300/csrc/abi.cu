@@ -357,6 +357,9 @@ tt_status tt_plan_create(tt_context* ctx, const tt_problem* prob, tt_plan** out)
   if (prob->ndim_x >= 3 && !(prob->dz > 0)) return TT_ERR_ARG;
   if (prob->flux != TT_FLUX_UPWIND && prob->flux != TT_FLUX_RUSANOV && prob->flux != TT_FLUX_CENTRAL)
     return TT_ERR_ARG;
+  if (prob->topology != TT_TOPO_MERGED && prob->topology != TT_TOPO_MERGED_NUX_Y && prob->topology != TT_TOPO_SPLIT_X)
+    return TT_ERR_ARG;
+  if (prob->topology != TT_TOPO_MERGED) return TT_ERR_UNSUPPORTED;  // the d = 4 layouts are not built
   if (prob->flux != TT_FLUX_UPWIND)
     for (int f = 0; f < 2 * prob->ndim_x; ++f)
       if (prob->inflow_temperature[f] >= 0.0) return TT_ERR_UNSUPPORTED;

@@ -56,6 +56,7 @@ class Workload:
     rho_kappa_s: np.ndarray        # (N_X*G,) per merged row
     rho_cv: Optional[np.ndarray] = None  # per cell: couples the material temperature
     flux: str = "upwind"            # "upwind", "rusanov" or "central" (vacuum boundaries only)
+    topology: str = "merged"        # TT layout of the state: "merged" (built), "merged_nux_y", "split_x"
     inflow_temperature: Tuple[Optional[float], ...] = (None,) * 6
     initial_temperature: Optional[np.ndarray] = None  # radiation temperature per cell for I^0
     tol: float = 1e-6

@@ -113,3 +113,15 @@ def test_rank_cap_one(tt, ctx, prec, dtype):
             Er = nt.energy_density_rows(ref, coef)
             assert np.linalg.norm(E - Er) <= 1e-6 * np.linalg.norm(Er), s
     plan.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("topology", ["merged_nux_y", "split_x"])
+def test_plan_refuses_unbuilt_topologies(tt, ctx, topology):
+    # the d = 4 layouts have a place in the problem description but no CUDA path
+    wl = plane_config1(nx=4, ny=4, G=2, ntheta=2, nphi=4).with_(topology=topology)
+    with pytest.raises(tt.TTError) as e:
+        tt.Plan(ctx, wl)
+    assert "unsupported" in str(e.value).lower() or "TT_ERR_UNSUPPORTED" in str(e.value)
+    ok = tt.Plan(ctx, wl.with_(topology="merged"))
+    assert ok.d == 3
