@@ -347,11 +347,24 @@ __global__ void __launch_bounds__(BR == 160 ? 640 : 1024) k_tsqr_merge_rs(LivePa
   T* vbuf = Rs + tsqr_r_elems(ncap);
   T* taub = vbuf + 2 * QS * SS;
   const int r = lp.r_ptr ? *lp.r_ptr : lp.rcap;
-  for (int idx = threadIdx.x; idx < ncap * ncap; idx += blockDim.x) {
-    const int i = idx / ncap, j = idx - (idx / ncap) * ncap;
-    if (j >= i) Rs[tri_off(i, ncap) + (j - i)] = (T)Ra[idx];
-  }
   const int c = threadIdx.x / QS, q = threadIdx.x % QS;
+  // the first factor's column c, rows q, q + QS, ... up to the diagonal, into packed R with eight
+  // loads in flight per lane (a loop of one load per element waits out the memory latency each time)
+  if (c < ncap) {
+    for (int i0 = q; i0 <= c; i0 += 8 * QS) {
+      T t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int row = i0 + u * QS;
+        t[u] = (row <= c) ? (T)Ra[(size_t)row * ncap + c] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int row = i0 + u * QS;
+        if (row <= c) Rs[tri_off(row, ncap) + (c - row)] = t[u];
+      }
+    }
+  }
   const unsigned gm = ((1u << QS) - 1u) << ((threadIdx.x & 31) & ~(QS - 1));
   const bool mycol = (c < ncap) && lp.live(c, r);
   __syncthreads();
@@ -367,7 +380,12 @@ __global__ void __launch_bounds__(BR == 160 ? 640 : 1024) k_tsqr_merge_rs(LivePa
     hh_absorb_rs<T, BR, QS, VREG, true>(Rs, ncap, B, vbuf, taub, buf, i0, lp, r, mycol, c, q, gm);
   }
   __syncthreads();
-  write_R<T, BR>(Rs, ncap, Ro);
+  // column c of the result, rows q, q + QS, ... (zeros below the diagonal)
+  if (c < ncap) {
+#pragma unroll 4
+    for (int row = q; row < ncap; row += QS)
+      Ro[(size_t)row * ncap + c] = (row <= c) ? (double)Rs[tri_off(row, ncap) + (c - row)] : 0.0;
+  }
 }
 
 // Host driver of the row-split TSQR; same contract as run_tsqr (final R, ncap x ncap row-major
