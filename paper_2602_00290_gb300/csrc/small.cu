@@ -360,6 +360,204 @@ __global__ void __launch_bounds__(128) k_orthonormalise_polar(int nv, int ldv, d
   }
 }
 
+// Mixed-path form of k_orthonormalise_polar, for columns that are FP32-accurate right singular
+// vectors (~1e-2 from orthonormal where the FP32 sweep resolves a small singular value only to its
+// round-off floor).  Newton-Schulz steps V <- V (3 I - V^T V) / 2 converge to the polar factor of
+// V whenever the singular values of V lie in (0, sqrt 3), i.e. ||V^T V - I||_2 < 1; with
+// E = V^T V - I each step takes E to about -(3/4) E^2 - (1/4) E^3.  The steps run in FP32 while
+// ||E||_F is above the FP32 floor (||E||_F <= 1/2 bounds ||E||_2 <= 1/2 on entry), then in FP64
+// from the FP32 result (one step from e = max |E_ij| <= 1.5e-7, two from e <= 1e-4), so the FP64
+// pipe, which holds a sub-partition for ~64 cycles per warp instruction, runs one or two small
+// products instead of the 2 nv k^2 dependent products of Gram-Schmidt.  The columns end
+// orthonormal to FP64 round-off and span a space within the FP32 round-off of span(V), the
+// accuracy V itself has.  Inputs outside the bounds (a vanishing, dependent or far from
+// orthogonal column, a NaN) take the column-by-column Gram-Schmidt of k_orthonormalise_warp on
+// the original columns, which also replaces dependent columns.
+__global__ void __launch_bounds__(128) k_orthonormalise_polar_mixed(int nv, int ldv, double* __restrict__ Vg,
+                                                                    const int* kptr, int rowmod,
+                                                                    const int* rowlive_ptr) {
+  __shared__ double V[32 * 33];
+  __shared__ double G[32 * 33];
+  __shared__ float Vf[32 * 33];
+  __shared__ float Gf[32 * 33];
+  __shared__ double h[32];
+  __shared__ double emax[4];
+  __shared__ double red[33];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int k = *kptr;
+  const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
+  for (int idx = tid; idx < nv * ldv; idx += blockDim.x) {
+    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+    V[i * 33 + c] = Vg[idx];
+    Vf[i * 33 + c] = (float)Vg[idx];
+  }
+  __syncthreads();
+  // block-wide maximum of one value per thread (a NaN wins)
+  auto block_max = [&](double e) -> double {
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, e, o);
+      e = (t > e || t != t) ? t : e;
+    }
+    if (lane == 0) emax[warp] = e;
+    __syncthreads();
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = (emax[w] > m || emax[w] != emax[w]) ? emax[w] : m;
+    __syncthreads();
+    return m;
+  };
+  // ---- FP32 steps: Gf = Vf^T Vf over the first k columns, ||Gf - I||_F and max |Gf - I|
+  const int n_entries = k * k;
+  int mode32 = 0;  // 1: at the FP32 floor, -1: outside the bounds
+  int steps32 = 0;  // FP32 updates made (none: V keeps its FP64 columns)
+  double e_prev = 1e300;
+  for (int step = 0; step < 6; ++step) {
+    double f2 = 0.0, e = 0.0;
+    for (int idx = tid; idx < n_entries; idx += blockDim.x) {
+      const int a = idx / k, b = idx - (idx / k) * k;
+      float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+      int i = 0;
+      for (; i + 3 < nv; i += 4) {
+        g0 = fmaf(Vf[i * 33 + a], Vf[i * 33 + b], g0);
+        g1 = fmaf(Vf[(i + 1) * 33 + a], Vf[(i + 1) * 33 + b], g1);
+        g2 = fmaf(Vf[(i + 2) * 33 + a], Vf[(i + 2) * 33 + b], g2);
+        g3 = fmaf(Vf[(i + 3) * 33 + a], Vf[(i + 3) * 33 + b], g3);
+      }
+      for (; i < nv; ++i) g0 = fmaf(Vf[i * 33 + a], Vf[i * 33 + b], g0);
+      const float g = (g0 + g1) + (g2 + g3);
+      Gf[a * 33 + b] = g;
+      const double d = (double)g - (a == b ? 1.0 : 0.0);
+      f2 += d * d;
+      e = (fabs(d) > e || d != d) ? fabs(d) : e;
+    }
+    const double fro2 = block_sum(f2, red);
+    const double e32 = block_max(e);
+    // ||E||_2 <= ||E||_F <= 1/2 keeps every singular value of V inside the convergence region;
+    // the comparison is false for a NaN
+    if (!(fro2 <= 0.25)) {
+      mode32 = -1;
+      break;
+    }
+    // at the FP32 floor: small, or no longer falling quadratically
+    if (e32 <= 1e-6 || e32 > 0.5 * e_prev) {
+      mode32 = 1;
+      break;
+    }
+    e_prev = e32;
+    float w[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = tid + r * (int)blockDim.x;
+      w[r] = 0.f;
+      if (idx < nv * k) {
+        const int i = idx / k, b = idx - (idx / k) * k;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int a = 0;
+        for (; a + 3 < k; a += 4) {
+          s0 = fmaf(Vf[i * 33 + a], Gf[a * 33 + b], s0);
+          s1 = fmaf(Vf[i * 33 + a + 1], Gf[(a + 1) * 33 + b], s1);
+          s2 = fmaf(Vf[i * 33 + a + 2], Gf[(a + 2) * 33 + b], s2);
+          s3 = fmaf(Vf[i * 33 + a + 3], Gf[(a + 3) * 33 + b], s3);
+        }
+        for (; a < k; ++a) s0 = fmaf(Vf[i * 33 + a], Gf[a * 33 + b], s0);
+        w[r] = 1.5f * Vf[i * 33 + b] - 0.5f * ((s0 + s1) + (s2 + s3));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = tid + r * (int)blockDim.x;
+      if (idx < nv * k) {
+        const int i = idx / k, b = idx - (idx / k) * k;
+        Vf[i * 33 + b] = w[r];
+      }
+    }
+    __syncthreads();
+    ++steps32;
+  }
+  // six steps without reaching the floor: the FP64 check below decides
+  const int ok32 = (mode32 < 0) ? -1 : 1;
+  int ns = -1;
+  if (ok32 == 1) {
+    // ---- FP64 steps from the FP32 result
+    if (steps32 > 0) {
+      for (int idx = tid; idx < nv * k; idx += blockDim.x) {
+        const int i = idx / k, b = idx - (idx / k) * k;
+        V[i * 33 + b] = (double)Vf[i * 33 + b];
+      }
+    }
+    __syncthreads();
+    for (int step = 0; step < 3; ++step) {
+      if (step > 0 && step >= ns) break;
+      double e = 0.0;
+      for (int idx = tid; idx < n_entries; idx += blockDim.x) {
+        const int a = idx / k, b = idx - (idx / k) * k;
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0, g3 = 0.0;
+        int i = 0;
+        for (; i + 3 < nv; i += 4) {
+          g0 += V[i * 33 + a] * V[i * 33 + b];
+          g1 += V[(i + 1) * 33 + a] * V[(i + 1) * 33 + b];
+          g2 += V[(i + 2) * 33 + a] * V[(i + 2) * 33 + b];
+          g3 += V[(i + 3) * 33 + a] * V[(i + 3) * 33 + b];
+        }
+        for (; i < nv; ++i) g0 += V[i * 33 + a] * V[i * 33 + b];
+        const double g = (g0 + g1) + (g2 + g3);
+        G[a * 33 + b] = g;
+        const double d = fabs(g - (a == b ? 1.0 : 0.0));
+        e = (d > e || d != d) ? d : e;
+      }
+      const double m = block_max(e);
+      // no step below the FP64 round-off of a k-term sum; one from e <= 1.5e-7 (1.5 e^2 is then
+      // below that floor); two from e <= 1e-4; otherwise Gram-Schmidt
+      const double floor64 = 8.0 * 2.220446049250313e-16 * (k > 1 ? k : 1);
+      if (step == 0) ns = (m <= floor64) ? 0 : (m <= 1.5e-7) ? 1 : (m <= 1e-4) ? 2 : -1;
+      if (ns < 0 || step >= ns) break;
+      double w[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = tid + r * (int)blockDim.x;
+        w[r] = 0.0;
+        if (idx < nv * k) {
+          const int i = idx / k, b = idx - (idx / k) * k;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int a = 0;
+          for (; a + 3 < k; a += 4) {
+            s0 += V[i * 33 + a] * G[a * 33 + b];
+            s1 += V[i * 33 + a + 1] * G[(a + 1) * 33 + b];
+            s2 += V[i * 33 + a + 2] * G[(a + 2) * 33 + b];
+            s3 += V[i * 33 + a + 3] * G[(a + 3) * 33 + b];
+          }
+          for (; a < k; ++a) s0 += V[i * 33 + a] * G[a * 33 + b];
+          w[r] = 1.5 * V[i * 33 + b] - 0.5 * ((s0 + s1) + (s2 + s3));
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int idx = tid + r * (int)blockDim.x;
+        if (idx < nv * k) {
+          const int i = idx / k, b = idx - (idx / k) * k;
+          V[i * 33 + b] = w[r];
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (ns < 0) {
+    // Gram-Schmidt on the original columns
+    for (int idx = tid; idx < nv * ldv; idx += blockDim.x) {
+      const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+      V[i * 33 + c] = Vg[idx];
+    }
+    __syncthreads();
+    if (warp == 0) cgs2_warp_staged(nv, k, rowmod, rowlive, V, h);
+    __syncthreads();
+  }
+  for (int idx = tid; idx < nv * ldv; idx += blockDim.x) {
+    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
+    Vg[idx] = V[i * 33 + c];
+  }
+}
+
 // Classical Gram-Schmidt applied twice (FP64) to the first K columns of V (nv x ldv), in
 // column order: V[:, :K] becomes Q of V[:, :K] = Q T and sig[j] = |T_jj|.  With the columns in
 // order of decreasing norm and P = A U for nearly orthogonal U, T is upper triangular with
@@ -449,12 +647,27 @@ __global__ void __launch_bounds__(256) k_gram_chunks(int nv, int ldv, const doub
   }
 }
 
+// Entry e of the sum of the nchunks partial Gram matrices, in four independent chains (chunk c
+// goes to chain c mod 4) so that the loads of several chunks are in flight at once instead of one
+// memory round trip per chunk.
+__device__ __forceinline__ double gram_partials_sum(int nchunks, int KK, const double* __restrict__ part, int e) {
+  double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+  int c = 0;
+#pragma unroll 2
+  for (; c + 3 < nchunks; c += 4) {
+    t0 += part[(size_t)c * KK + e];
+    t1 += part[(size_t)(c + 1) * KK + e];
+    t2 += part[(size_t)(c + 2) * KK + e];
+    t3 += part[(size_t)(c + 3) * KK + e];
+  }
+  for (; c < nchunks; ++c) t0 += part[(size_t)c * KK + e];
+  return (t0 + t1) + (t2 + t3);
+}
+
 __global__ void k_gram_sum(int nchunks, int KK, const double* __restrict__ part, double* __restrict__ G) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= KK) return;
-  double t = 0.0;
-  for (int c = 0; c < nchunks; ++c) t += part[(size_t)c * KK + e];
-  G[e] = t;
+  G[e] = gram_partials_sum(nchunks, KK, part, e);
 }
 
 // Upper Cholesky factor T (K x K, row-major, zero below the diagonal) of the symmetric G.
@@ -554,11 +767,7 @@ __global__ void __launch_bounds__(256) k_chol_inv_sig(int K, int nchunks, const 
   double* Ms = A + KK;     // [K][K]
   double* d0 = Ms + KK;    // [K]
   double* rinv = d0 + K;   // [K]
-  for (int e = threadIdx.x; e < KK; e += blockDim.x) {
-    double t = 0.0;
-    for (int c = 0; c < nchunks; ++c) t += part[(size_t)c * KK + e];
-    A[e] = t;
-  }
+  for (int e = threadIdx.x; e < KK; e += blockDim.x) A[e] = gram_partials_sum(nchunks, KK, part, e);
   __syncthreads();
   chol_upper_smem(K, A, d0);
   // below the diagonal A still holds Gram entries; the inverse reads the upper triangle only
@@ -1784,11 +1993,11 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
                               j.r2_ptr, j.r2_nblk, j.r2_nextra, nullptr, 0, n2, j.ctrl, 1, nullptr); count_launch();
     // FP64 path: the columns come from the FP64 Jacobi, orthonormal to round-off, and take at most
     // one polar step; the mixed path's FP32-accurate small columns are only ~1e-2 orthogonal
-    // (the FP32 sweep stops at its round-off floor), so they take Gram-Schmidt directly
+    // (the FP32 sweep stops at its round-off floor): their polar steps start in FP32
     if (n2 <= 32 && F64)
       k_orthonormalise_polar<<<1, 128, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     else if (n2 <= 32)
-      k_orthonormalise_warp<<<1, 32, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
+      k_orthonormalise_polar_mixed<<<1, 128, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     else
       k_orthonormalise<<<1, 1024, 0, s>>>(n2, n2, V2, &j.ctrl->k[1], n2, nullptr);
     count_launch();

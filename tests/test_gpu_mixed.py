@@ -83,3 +83,25 @@ def test_mixed_round_ranks_match_oracle(tt, ctx, seed0, tol):
     ctx.sync()
     assert x.ranks() == nt.ranks(want)
     assert fro_rel(nt.full(x.to_cores()), nt.full(want)) < 1e-5
+
+
+@pytest.mark.parametrize("prec,dtype,bound", [("mixed", "f32", 2e-6), ("mixed", "f64", 1e-10), ("fp64", "f64", 1e-10)])
+def test_step_leaves_angular_cores_right_orthonormal(tt, ctx, prec, dtype, bound):
+    """A rounded state keeps its angular cores right-orthonormal (Sec. 3.1: the R->L sweep leaves
+    C_k <- V_k^T); in the mixed path the phi core's columns come from FP32 Jacobi vectors that the
+    Newton-Schulz steps (FP32, then FP64) make orthonormal, so every bound here is the storage
+    precision's."""
+    wl = plane_config1(nx=12, ny=10, G=5, ntheta=4, nphi=8, rmax=8, tol=1e-6)
+    plan = tt.Plan(ctx, wl)
+    x = tt.initial_state(plan, [wl.rmax, wl.rmax], dtype)
+    worst = []
+    for _ in range(4):
+        tt.tt_step(ctx, plan, x, wl.tol, wl.rmax, prec)
+        ctx.sync()
+        C = x.to_cores()
+        th = C[1].reshape(C[1].shape[0], -1)
+        ph = C[2].reshape(C[2].shape[0], -1)
+        worst.append(max(np.abs(th @ th.T - np.eye(th.shape[0])).max(),
+                         np.abs(ph @ ph.T - np.eye(ph.shape[0])).max()))
+    assert x.ranks()[2] > 1, x.ranks()
+    assert max(worst) <= bound, worst
