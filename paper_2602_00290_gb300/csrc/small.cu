@@ -233,32 +233,13 @@ __device__ void cgs2_warp_staged(int nv, int k, int rowmod, int rowlive, double*
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(32) k_orthonormalise_warp(int nv, int ldv, double* __restrict__ Vg,
-                                                            const int* kptr, int rowmod, const int* rowlive_ptr) {
-  __shared__ double V[32 * 33];  // row i at V[i * 33 + c]
-  __shared__ double h[32];
-  const int lane = threadIdx.x;
-  const int k = *kptr;
-  const int rowlive = rowlive_ptr ? *rowlive_ptr : rowmod;
-  for (int idx = lane; idx < nv * ldv; idx += 32) {
-    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
-    V[i * 33 + c] = Vg[idx];
-  }
-  __syncwarp();
-  cgs2_warp_staged(nv, k, rowmod, rowlive, V, h);
-  for (int idx = lane; idx < nv * ldv; idx += 32) {
-    const int i = idx / ldv, c = idx - (idx / ldv) * ldv;
-    Vg[idx] = V[i * 33 + c];
-  }
-}
-
 // The first k columns of V (nv <= 32 rows, k <= ldv <= 32) made orthonormal by Newton-Schulz steps
 // towards the polar factor, V <- V (3 I - V^T V) / 2, when they are already close to
 // orthonormal (the right singular vectors of a Jacobi sweep, normalised in FP64): with
 // e = max |V^T V - I| <= 1e-4 each step takes e to about 1.5 e^2, so one step suffices for e <=
 // 1e-8 (FP64 Jacobi) and two for FP32-accurate columns.  The span of the columns is unchanged and
 // the columns move by O(e).  Other inputs (a vanishing or far from orthogonal column) take the
-// column-by-column Gram-Schmidt of k_orthonormalise_warp, which also replaces dependent columns.
+// column-by-column Gram-Schmidt of cgs2_warp_staged, which also replaces dependent columns.
 // Four warps compute V^T V and the update as small matrix products in shared memory: no
 // dependent chain longer than nv, against the column-by-column chains of Gram-Schmidt.
 __global__ void __launch_bounds__(128) k_orthonormalise_polar(int nv, int ldv, double* __restrict__ Vg,
@@ -371,7 +352,7 @@ __global__ void __launch_bounds__(128) k_orthonormalise_polar(int nv, int ldv, d
 // products instead of the 2 nv k^2 dependent products of Gram-Schmidt.  The columns end
 // orthonormal to FP64 round-off and span a space within the FP32 round-off of span(V), the
 // accuracy V itself has.  Inputs outside the bounds (a vanishing, dependent or far from
-// orthogonal column, a NaN) take the column-by-column Gram-Schmidt of k_orthonormalise_warp on
+// orthogonal column, a NaN) take the column-by-column Gram-Schmidt of cgs2_warp_staged on
 // the original columns, which also replaces dependent columns.
 __global__ void __launch_bounds__(128) k_orthonormalise_polar_mixed(int nv, int ldv, double* __restrict__ Vg,
                                                                     const int* kptr, int rowmod,
