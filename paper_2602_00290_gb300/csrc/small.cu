@@ -66,6 +66,45 @@ __global__ void k_small_gemm(int M, int N, int K, const TA* __restrict__ A, long
   }
 }
 
+// C = A B with the K range split over gridDim.z slices of kslice (a multiple of 16): slice z writes
+// its partial product, unmasked, to part[z] (M x N, row-major); k_small_gemm_sum adds the slices in
+// order.  For products with few output tiles and a long K (W = B0p V1: 10 x 2 tiles, K = 512),
+// where one CTA per tile leaves most SMs idle and each tile's FP64 chain runs on one SM.
+__global__ void k_small_gemm_part(int M, int N, int K, int kslice, const double* __restrict__ A, long sa0, long sa1,
+                                  const double* __restrict__ B, long sb0, long sb1, double* __restrict__ part) {
+  __shared__ double As[16][17];
+  __shared__ double Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.y * 16 + ty;
+  const int j = blockIdx.x * 16 + tx;
+  const int kbeg = blockIdx.z * kslice;
+  const int kend = min(kbeg + kslice, K);
+  double acc = 0.0;
+  for (int k0 = kbeg; k0 < kend; k0 += 16) {
+    const int ka = k0 + tx, kb = k0 + ty;
+    As[ty][tx] = (i < M && ka < kend) ? A[i * sa0 + ka * sa1] : 0.0;
+    const int jb = blockIdx.x * 16 + tx;
+    Bs[ty][tx] = (kb < kend && jb < N) ? B[kb * sb0 + jb * sb1] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) acc += As[ty][kk] * Bs[kk][tx];
+    __syncthreads();
+  }
+  if (i < M && j < N) part[((size_t)blockIdx.z * M + i) * N + j] = acc;
+}
+
+__global__ void k_small_gemm_sum(int M, int N, int nslice, const double* __restrict__ part, double* __restrict__ C,
+                                 long ldc, const int* __restrict__ nlive) {
+  const int nl = nlive ? *nlive : N;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < (long)M * N; idx += (long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / N), j = (int)(idx - (long)i * N);
+    double v = 0.0;
+    if (j < nl)
+      for (int z = 0; z < nslice; ++z) v += part[(size_t)z * M * N + idx];
+    C[i * ldc + j] = v;
+  }
+}
+
 // Rank decision for one bond.  first != 0: this is the first SVD of the right-to-left sweep,
 // which also fixes ||X|| = sqrt(sum sigma^2) and delta = tol ||X|| / sqrt(d-1).  The kept rank
 // is the smallest k >= 1 with sqrt(sum_{j>=k} sigma_j^2) <= delta (tol > 0), or the full rank
@@ -816,26 +855,69 @@ __global__ void __launch_bounds__(1024) k_sort_cols(int nv, int ldv, int K, doub
   for (int c = threadIdx.x; c < K; c += blockDim.x) sig[rank_of[c]] = sg[c];
 }
 
-// tail = max(0, fro2 - sum_{j<K} sig_j^2): the energy of A outside its K leading singular pairs
-// *tail = max(0, ||A||_F^2 - sum_j sig_j^2) with ||A||_F^2 over `count` entries of A: the energy
-// beyond the K refined singular values (one CTA).
-__global__ void k_tail_from_frob(long count, const double* __restrict__ A, int K, const double* __restrict__ sig,
-                                 double* __restrict__ fro2, double* __restrict__ tail) {
+// *tail = max(0, ||A||_F^2 - sum_{j<K} sig_j^2): the energy of A outside its K leading singular
+// pairs, with ||A||_F^2 over `count` entries of A, from partial sums: k_sumsq_parts writes
+// gridDim.x partial sums of squares over a fixed grid-stride partition of A, k_tail_from_parts adds
+// them in order (one SM's FP64 pipe took ~20 us for the 82k entries of the bench's bond-1 matrix
+// in one CTA).
+__global__ void k_sumsq_parts(long count, const double* __restrict__ A, double* __restrict__ parts) {
   __shared__ double red[33];
   double s = 0.0;
-  for (long i = threadIdx.x; i < count; i += blockDim.x) s += A[i] * A[i];
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
+    s += A[i] * A[i];
   s = block_sum(s, red);
-  if (threadIdx.x == 0) {
-    *fro2 = s;
-    double s2 = 0.0;
-    for (int j = K - 1; j >= 0; --j) s2 += sig[j] * sig[j];
-    const double t = s - s2;
-    *tail = t > 0.0 ? t : 0.0;
+  if (threadIdx.x == 0) parts[blockIdx.x] = s;
+}
+__global__ void k_tail_from_parts(int nparts, const double* __restrict__ parts, int K, const double* __restrict__ sig,
+                                  double* __restrict__ fro2, double* __restrict__ tail) {
+  if (threadIdx.x || blockIdx.x) return;
+  double s = 0.0;
+  for (int b = 0; b < nparts; ++b) s += parts[b];
+  *fro2 = s;
+  double s2 = 0.0;
+  for (int j = K - 1; j >= 0; --j) s2 += sig[j] * sig[j];
+  const double t = s - s2;
+  *tail = t > 0.0 ? t : 0.0;
+}
+constexpr int kTailParts = 32;
+
+// k_sort_cols in two launches for tall V: the rank of each of the first K values of sig (decreasing,
+// ties by index) into rank_of and sig sorted, in one CTA; then every row of V permuted in place
+// through shared memory, kPermRows rows a CTA (one CTA moving the whole matrix took ~20 us).
+__global__ void __launch_bounds__(1024) k_sort_keys(int K, double* __restrict__ sig, int* __restrict__ rank_of) {
+  __shared__ double sg[1024];
+  for (int c = threadIdx.x; c < K; c += blockDim.x) sg[c] = sig[c];
+  __syncthreads();
+  for (int c = threadIdx.x; c < K; c += blockDim.x) {
+    const double v = rank_key(sg[c]);
+    int r = 0;
+    for (int q = 0; q < K; ++q) {
+      const double w = rank_key(sg[q]);
+      r += (w > v) || (w == v && q < c);
+    }
+    rank_of[c] = r;
+    sig[r] = sg[c];
+  }
+}
+constexpr int kPermRows = 4;
+__global__ void __launch_bounds__(256) k_permute_cols(int nv, int ldv, int K, const int* __restrict__ rank_of,
+                                                      double* __restrict__ V) {
+  __shared__ double buf[kPermRows * 1024];
+  const int row0 = blockIdx.x * kPermRows;
+  const int nr = min(kPermRows, nv - row0);
+  for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
+    const int r = idx / K, c = idx - (idx / K) * K;
+    buf[idx] = V[(size_t)(row0 + r) * ldv + c];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nr * K; idx += blockDim.x) {
+    const int r = idx / K, c = idx - (idx / K) * K;
+    V[(size_t)(row0 + r) * ldv + rank_of[c]] = buf[idx];
   }
 }
 
 // Energy beyond the first K of n sorted singular values that are accurate to FP64 (the squared
-// tail, like k_tail_from_frob, but without the cancellation of ||A||^2 - sum sigma^2).
+// tail, like k_tail_from_parts, but without the cancellation of ||A||^2 - sum sigma^2).
 __global__ void k_tail_from_sigma(int n, int K, const double* __restrict__ sig, double* __restrict__ tail) {
   if (threadIdx.x || blockIdx.x) return;
   double s2 = 0.0;
@@ -1705,6 +1787,31 @@ void small_gemm(cudaStream_t s, int M, int N, int K, const TA* A, long sa0, long
                                             nullptr, nullptr); count_launch();
 }
 
+// small_gemm (FP64, no column scaling) with K split over up to kMaxKSlices slices when the output
+// has fewer tiles than half the SMs; part holds kMaxKSlices M N doubles (small_gemm_ksplit_elems).
+constexpr int kMaxKSlices = 16;
+static size_t small_gemm_ksplit_elems(int M, int N) { return (size_t)kMaxKSlices * M * N; }
+static void small_gemm_ksplit(cudaStream_t s, int num_sms, int M, int N, int K, const double* A, long sa0, long sa1,
+                              const double* B, long sb0, long sb1, double* C, long ldc, const int* nlive,
+                              double* part) {
+  const int tiles = ((N + 15) / 16) * ((M + 15) / 16);
+  int ns = (num_sms / 2) / (tiles > 0 ? tiles : 1);
+  if (ns > kMaxKSlices) ns = kMaxKSlices;
+  const int kmin = 64;  // at least four 16-wide chunks a slice
+  if (ns > (K + kmin - 1) / kmin) ns = (K + kmin - 1) / kmin;
+  if (ns <= 1) {
+    small_gemm<double, double>(s, M, N, K, A, sa0, sa1, B, sb0, sb1, C, ldc, nlive, nullptr);
+    return;
+  }
+  int kslice = (K + ns - 1) / ns;
+  kslice = (kslice + 15) / 16 * 16;
+  ns = (K + kslice - 1) / kslice;
+  dim3 grid((N + 15) / 16, (M + 15) / 16, ns);
+  k_small_gemm_part<<<grid, 256, 0, s>>>(M, N, K, kslice, A, sa0, sa1, B, sb0, sb1, part); count_launch();
+  const long tot = (long)M * N;
+  k_small_gemm_sum<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, ns, part, C, ldc, nlive); count_launch();
+}
+
 // A B -> C and A2 B -> C2 in one launch (same shape, strides and B).
 template <typename TA, typename TB>
 void small_gemm_pair(cudaStream_t s, int M, int N, int K, const TA* A, const TA* A2, long sa0, long sa1, const TB* B,
@@ -1991,9 +2098,11 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   double* sig1 = ws.take<double>(Kr);
   double* P1s = ws.take<double>((size_t)nv * R);
   double* fro1 = ws.take<double>(1);
+  double* fparts = ws.take<double>(kTailParts);
+  int* rank1 = ws.take<int>(R);
   double* tailK = ws.take<double>(1);
-  double* tmpK = ws.take<double>((size_t)nv * Kr);
   double* V1 = ws.take<double>((size_t)nv * K1);
+  double* wpart = ws.take<double>(small_gemm_ksplit_elems(R, K1));
   double *U1 = nullptr, *P1 = nullptr;
   st = svd_right_pre<F64>(s, num_sms, SrcCols<double>{Y2, nv}, nv, R, ws, &U1, &P1, sigc1, perm1, j.ctrl,
                           j.coop_grid_max);
@@ -2010,15 +2119,17 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   if (F64) {  // the FP64 Jacobi singular values resolve the whole tail
     k_tail_from_sigma<<<1, 32, 0, s>>>(R, Kr, sigc1, tailK); count_launch();
   } else {
-    k_tail_from_frob<<<1, 1024, 0, s>>>((long)R * nv, Y2, Kr, sig1, fro1, tailK); count_launch();
+    k_sumsq_parts<<<kTailParts, 256, 0, s>>>((long)R * nv, Y2, fparts); count_launch();
+    k_tail_from_parts<<<1, 32, 0, s>>>(kTailParts, fparts, Kr, sig1, fro1, tailK); count_launch();
   }
-  k_sort_cols<<<1, 1024, 0, s>>>(nv, R, Kr, sig1, P1s, tmpK); count_launch();
+  k_sort_keys<<<1, 1024, 0, s>>>(Kr, sig1, rank1); count_launch();
+  k_permute_cols<<<(nv + kPermRows - 1) / kPermRows, 256, 0, s>>>(nv, R, Kr, rank1, P1s); count_launch();
   k_decide<<<1, 32, 0, s>>>(sig1, Kr, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
                             nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, tailK); count_launch();
   // V1 <- the leading K1 columns of P1s, with the zero ones replaced by independent unit vectors
   k_fix_zero_columns<<<1, 1024, 0, s>>>(nv, K1, V1, sig1, &j.ctrl->k[0], K2, &j.ctrl->k[1], P1s, R); count_launch();
   k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2); count_launch();
-  small_gemm<double, double>(s, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], nullptr);
+  small_gemm_ksplit(s, num_sms, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], wpart);
   small_gemm<double, double>(s, K1 * n1, n2, K2, j.core1, K2, 1, j.core2, n2, 1, j.Bnew, n2, nullptr, nullptr);
   k_vj<<<K1, 128, 0, s>>>(K1, nang, j.Bnew, j.domega, j.vJ); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
