@@ -859,25 +859,35 @@ __global__ void __launch_bounds__(1024) k_sort_cols(int nv, int ldv, int K, doub
 // pairs, with ||A||_F^2 over `count` entries of A, from partial sums: k_sumsq_parts writes
 // gridDim.x partial sums of squares over a fixed grid-stride partition of A, k_tail_from_parts adds
 // them in order (one SM's FP64 pipe took ~20 us for the 82k entries of the bench's bond-1 matrix
-// in one CTA).
-__global__ void k_sumsq_parts(long count, const double* __restrict__ A, double* __restrict__ parts) {
+// in one CTA).  With concurrent problems (batches) one CTA does both, in one launch: parts = nullptr
+// and a single CTA write fro2 and the tail directly.
+__device__ __forceinline__ void tail_finish(double s, int K, const double* __restrict__ sig,
+                                            double* __restrict__ fro2, double* __restrict__ tail) {
+  *fro2 = s;
+  double s2 = 0.0;
+  for (int j = K - 1; j >= 0; --j) s2 += sig[j] * sig[j];
+  const double t = s - s2;
+  *tail = t > 0.0 ? t : 0.0;
+}
+__global__ void k_sumsq_parts(long count, const double* __restrict__ A, double* __restrict__ parts, int K,
+                              const double* __restrict__ sig, double* __restrict__ fro2, double* __restrict__ tail) {
   __shared__ double red[33];
   double s = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x)
     s += A[i] * A[i];
   s = block_sum(s, red);
-  if (threadIdx.x == 0) parts[blockIdx.x] = s;
+  if (threadIdx.x != 0) return;
+  if (parts)
+    parts[blockIdx.x] = s;
+  else
+    tail_finish(s, K, sig, fro2, tail);
 }
 __global__ void k_tail_from_parts(int nparts, const double* __restrict__ parts, int K, const double* __restrict__ sig,
                                   double* __restrict__ fro2, double* __restrict__ tail) {
   if (threadIdx.x || blockIdx.x) return;
   double s = 0.0;
   for (int b = 0; b < nparts; ++b) s += parts[b];
-  *fro2 = s;
-  double s2 = 0.0;
-  for (int j = K - 1; j >= 0; --j) s2 += sig[j] * sig[j];
-  const double t = s - s2;
-  *tail = t > 0.0 ? t : 0.0;
+  tail_finish(s, K, sig, fro2, tail);
 }
 constexpr int kTailParts = 32;
 
@@ -2100,6 +2110,10 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   double* fro1 = ws.take<double>(1);
   double* fparts = ws.take<double>(kTailParts);
   int* rank1 = ws.take<int>(R);
+  double* tmpK = ws.take<double>((size_t)nv * Kr);
+  // concurrent problems (batch views, one-CTA cooperative launches): the GPU is already full, so
+  // the bond-1 tail, column sort and W product take the forms with the fewest launches and CTAs
+  const bool few_launches = (j.coop_grid_max == 1);
   double* tailK = ws.take<double>(1);
   double* V1 = ws.take<double>((size_t)nv * K1);
   double* wpart = ws.take<double>(small_gemm_ksplit_elems(R, K1));
@@ -2119,17 +2133,26 @@ static tt_status small_round_mixed3(cudaStream_t s, int num_sms, const SmallJob&
   if (F64) {  // the FP64 Jacobi singular values resolve the whole tail
     k_tail_from_sigma<<<1, 32, 0, s>>>(R, Kr, sigc1, tailK); count_launch();
   } else {
-    k_sumsq_parts<<<kTailParts, 256, 0, s>>>((long)R * nv, Y2, fparts); count_launch();
-    k_tail_from_parts<<<1, 32, 0, s>>>(kTailParts, fparts, Kr, sig1, fro1, tailK); count_launch();
+    if (few_launches) {
+      k_sumsq_parts<<<1, 1024, 0, s>>>((long)R * nv, Y2, nullptr, Kr, sig1, fro1, tailK); count_launch();
+    } else {
+      k_sumsq_parts<<<kTailParts, 256, 0, s>>>((long)R * nv, Y2, fparts, 0, nullptr, nullptr, nullptr);
+      count_launch();
+      k_tail_from_parts<<<1, 32, 0, s>>>(kTailParts, fparts, Kr, sig1, fro1, tailK); count_launch();
+    }
   }
-  k_sort_keys<<<1, 1024, 0, s>>>(Kr, sig1, rank1); count_launch();
-  k_permute_cols<<<(nv + kPermRows - 1) / kPermRows, 256, 0, s>>>(nv, R, Kr, rank1, P1s); count_launch();
+  if (few_launches) {
+    k_sort_cols<<<1, 1024, 0, s>>>(nv, R, Kr, sig1, P1s, tmpK); count_launch();
+  } else {
+    k_sort_keys<<<1, 1024, 0, s>>>(Kr, sig1, rank1); count_launch();
+    k_permute_cols<<<(nv + kPermRows - 1) / kPermRows, 256, 0, s>>>(nv, R, Kr, rank1, P1s); count_launch();
+  }
   k_decide<<<1, 32, 0, s>>>(sig1, Kr, 0, 3, j.tol, j.rmax, K1, j.nrowsZ, j.lp.r_ptr, j.lp.nblk, j.lp.nextra, 1,
                             nullptr, 0, 0, &j.ctrl->k[1], n1, 0, j.ctrl, 0, tailK); count_launch();
   // V1 <- the leading K1 columns of P1s, with the zero ones replaced by independent unit vectors
   k_fix_zero_columns<<<1, 1024, 0, s>>>(nv, K1, V1, sig1, &j.ctrl->k[0], K2, &j.ctrl->k[1], P1s, R); count_launch();
   k_write_cores3<<<64, 256, 0, s>>>(n1, n2, K1, K2, V1, V2, j.ctrl, j.core1, j.core2); count_launch();
-  small_gemm_ksplit(s, num_sms, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], wpart);
+  small_gemm_ksplit(s, few_launches ? 0 : num_sms, R, K1, nv, B0p, nv, 1, V1, K1, 1, j.W, K1, &j.ctrl->k[0], wpart);
   small_gemm<double, double>(s, K1 * n1, n2, K2, j.core1, K2, 1, j.core2, n2, 1, j.Bnew, n2, nullptr, nullptr);
   k_vj<<<K1, 128, 0, s>>>(K1, nang, j.Bnew, j.domega, j.vJ); count_launch();
   return cudaGetLastError() == cudaSuccess ? TT_OK : TT_ERR_CUDA;
