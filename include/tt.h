@@ -209,7 +209,7 @@ tt_status tt_context_set_sketch(tt_context *ctx, const double *omega_dev, int32_
  * A variant that cannot take the shape runs variant 0.  The variant picks the leaf kernel; the
  * merge tree over the leaves' R factors runs four lanes per column in every variant when
  * 4 ncap <= 1024.  leaves = cap on the TSQR leaves: <= 0 gives the default wave (2 CTAs per SM for
- * FP64, 3 for FP32); larger caps are clamped to 4 per SM.  The choice changes the order of
+ * FP64, 3 for FP32); larger caps are clamped to 6 per SM.  The choice changes the order of
  * rounding errors only.  ncap <= 0 clears every entry.  tt_context_get_tsqr reports what a pass
  * of ncap columns would run.  The paper has no counterpart: these are launch-shape choices. */
 tt_status tt_context_set_tsqr(tt_context *ctx, tt_precision prec, int32_t ncap, int32_t variant, int32_t leaves);

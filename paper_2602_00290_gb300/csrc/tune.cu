@@ -123,12 +123,15 @@ tt_status tt_autotune(tt_context* ctx, const tt_plan* plan, const tt_tensor* I, 
   const int wave = default_wave(ctx, es);
   const int most = ttk::kTsqrMaxLeavesPerSm * ctx->num_sms;
   // leaf caps tried per variant (multiples of half the SM count): up to one default wave for
-  // the column and row-split kernels, up to four CTAs per SM for the dense column kernels
+  // the column kernels, up to kTsqrMaxLeavesPerSm CTAs per SM for the row-split and dense column
+  // kernels (measured: the 33-column row-split source leaf, six CTAs per SM, takes 0.39 ms at 912
+  // leaves against 0.63 ms at 456)
   auto leaf_opts = [&](int v) {
     std::vector<int> o;
-    for (int m : {1, 2, 3, 4, 6, 8}) {
+    for (int m : {1, 2, 3, 4, 6, 8, 12}) {
       const int l = m * ctx->num_sms / 2;
-      const int hi = (v == ttk::kTsqrColumnDense) ? most : (v == ttk::kTsqrBlocked) ? ctx->num_sms : wave;
+      const bool wide = (v == ttk::kTsqrColumnDense || v == ttk::kTsqrRowSplit);
+      const int hi = wide ? most : (v == ttk::kTsqrBlocked) ? ctx->num_sms : wave;
       const int lo = (v == ttk::kTsqrColumnDense) ? ctx->num_sms : 8;
       if (l >= lo && l <= hi) o.push_back(l);
     }

@@ -17,8 +17,10 @@ namespace ttk {
 enum TsqrVariant : int { kTsqrColumn = 0, kTsqrRowSplit = 1, kTsqrColumnDense = 2, kTsqrBlocked = 3,
                          kTsqrVariants = 4 };
 
-// Most leaves a tuned entry may ask for, per SM (workspace is sized for the entry in effect).
-constexpr int kTsqrMaxLeavesPerSm = 4;
+// Most leaves a tuned entry may ask for, per SM (workspace is sized for the entry in effect; the
+// leaf launch itself stays within the CTAs its kernel keeps resident).  Narrow passes fit six:
+// the row-split leaf of the 33-column source sum keeps six CTAs per SM.
+constexpr int kTsqrMaxLeavesPerSm = 6;
 
 struct TsqrCfg {
   int variant;

@@ -134,8 +134,8 @@ def test_get_tsqr_defaults_and_clear(tt, ctx):
     ctx.set_tsqr("mixed", 41, "rowsplit", 10)
     assert ctx.get_tsqr("mixed", 41) == ("rowsplit", 10)
     assert ctx.get_tsqr("fp64", 41) == ("column", 2 * nsm)
-    ctx.set_tsqr("mixed", 41, "rowsplit", 10 ** 6)  # above four per SM: clamped
-    assert ctx.get_tsqr("mixed", 41) == ("rowsplit", 4 * nsm)
+    ctx.set_tsqr("mixed", 41, "rowsplit", 10 ** 6)  # above six per SM: clamped
+    assert ctx.get_tsqr("mixed", 41) == ("rowsplit", 6 * nsm)
     ctx.set_tsqr("mixed", 300, "rowsplit", 0)  # 4 x 300 lanes > 1024: column kernels run
     assert ctx.get_tsqr("mixed", 300) == ("column", 3 * nsm)
     ctx.set_tsqr("mixed", 200, "column", 0)  # 224 threads: column kernels

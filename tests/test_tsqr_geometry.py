@@ -159,7 +159,8 @@ SHAPES = [
 
 @pytest.mark.parametrize("prec,ncap,nrows", SHAPES)
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
-@pytest.mark.parametrize("num_sms,max_leaves", [(152, 0), (152, 608), (152, 456), (152, 8), (7, 0), (3, 5)])
+@pytest.mark.parametrize("num_sms,max_leaves", [(152, 0), (152, 912), (152, 608), (152, 456), (152, 8), (7, 0),
+                                                (3, 5)])
 def test_tsqr_geometry_stays_inside_its_buffers(tt, prec, ncap, nrows, variant, num_sms, max_leaves):
     g0 = tt.tsqr_geometry(prec, variant, ncap, nrows, num_sms, 1, max_leaves)
     most = SMEM_PER_SM // (g0["leaf_smem"] + 1024)  # resident CTAs the leaf's shared memory admits
